@@ -1,0 +1,107 @@
+"""CryptoTrain-P linear layer on the oracle (test infrastructure).
+
+Section 3.2: offline, the client draws masks r^x, r^w, encrypts them and the
+server computes [r^x r^w] by CCMul (with relinearisation); online, the server
+computes c = [x](w - r^w) + [w](x - r^x) + [r^x r^w] by two CPMuls and CCAdds
+and p = (x - r^x)(w - r^w) by PPMul; the client recovers Dec(c) - p = x w.
+With channel groups the products are summed over the G groups of an output.
+
+Reading: masks are uniform over all N coefficients of R_t (the paper's
+"R^n" is undefined).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import he, packing
+
+
+@dataclass
+class LayerRun:
+    plan: packing.Plan
+    keys: he.Keys
+    x_polys: np.ndarray      # [T*G][N]
+    w_polys: np.ndarray      # [M*G][N]
+    r_x: np.ndarray
+    r_w: np.ndarray
+    ct_x: np.ndarray
+    ct_w: np.ndarray
+    ct_rx: np.ndarray
+    ct_rw: np.ndarray
+    rr: np.ndarray           # [M*T][2][L][N] precomputed [r^x r^w]
+    out: np.ndarray          # [M*T][2][L][N] online result c
+    p: np.ndarray            # [M*T][N] PPMul result
+    y: np.ndarray            # decoded [M, Ho, Wo]
+
+
+def precompute_pairs(plan):
+    """CCMul pairs (rx index, rw index), G consecutive pairs per output m*T+t."""
+    pairs = []
+    for m in range(plan.M):
+        for t in range(plan.T):
+            for g in range(plan.G):
+                pairs.append((t * plan.G + g, m * plan.G + g))
+    return pairs
+
+
+def online_terms(plan):
+    """CPMul terms over ct = [ct_x ; ct_w] and pt = [(w - r^w) ; (x - r^x)]."""
+    TG, MG = plan.T * plan.G, plan.M * plan.G
+    terms = []
+    for m in range(plan.M):
+        for t in range(plan.T):
+            tl = []
+            for g in range(plan.G):
+                tl.append((t * plan.G + g, m * plan.G + g))
+                tl.append((TG + m * plan.G + g, MG + t * plan.G + g))
+            terms.append(tl)
+    return terms
+
+
+def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
+    """x: [C,H,W] ints, w: [M,C,h,h] ints; seeds: workloads.ProtocolSeeds."""
+    t = P.t
+    if keys is None:
+        keys = he.keygen(P, seeds.keys, True)
+    xp = packing.encode_input(plan, x, t).reshape(-1, P.N)
+    wp = packing.encode_kernel(plan, w, t).reshape(-1, P.N)
+    r_x = he.sample_masks(P, seeds.mask_x, xp.shape[0])
+    r_w = he.sample_masks(P, seeds.mask_w, wp.shape[0])
+    ct_x = he.encrypt(P, keys, xp, seeds.enc_x)
+    ct_w = he.encrypt(P, keys, wp, seeds.enc_w)
+    ct_rx = he.encrypt(P, keys, r_x, seeds.enc_rx)
+    ct_rw = he.encrypt(P, keys, r_w, seeds.enc_rw)
+    # offline: [r^x r^w] summed over channel groups
+    rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan), plan.G)
+    # online
+    tt = np.uint64(t)
+    wm = (wp + (tt - r_w)) % tt
+    xm = (xp + (tt - r_x)) % tt
+    ct_all = np.concatenate([ct_x, ct_w])
+    pt_all = np.concatenate([wm, xm])
+    out = he.cpmul_terms(P, ct_all, pt_all, online_terms(plan), add=rr)
+    p = he.ppmul_terms(P, xm, wm, packing.product_terms(plan))
+    dec = he.decrypt(P, keys, out)
+    z = (dec + (tt - p)) % tt
+    y = packing.decode(plan, z.reshape(plan.M, plan.T, P.N), t)
+    return LayerRun(plan, keys, xp, wp, r_x, r_w, ct_x, ct_w, ct_rx, ct_rw, rr, out, p, y)
+
+
+def conv_reference(x, w, pad):
+    """Direct integer cross-correlation (what a CNN layer computes), used as
+    the brute-force check of the whole protocol: y[m,a,b] = sum_{c,k,l}
+    x[c, a+k-pad, b+l-pad] w[m,c,k,l]."""
+    x = np.asarray(x, dtype=np.int64)
+    w = np.asarray(w, dtype=np.int64)
+    C, H, W = x.shape
+    M, _, h, _ = w.shape
+    xp = np.zeros((C, H + 2 * pad, W + 2 * pad), dtype=np.int64)
+    xp[:, pad:pad + H, pad:pad + W] = x
+    Ho, Wo = H + 2 * pad - h + 1, W + 2 * pad - h + 1
+    y = np.zeros((M, Ho, Wo), dtype=np.int64)
+    for k in range(h):
+        for l in range(h):
+            y += np.einsum("mc,cab->mab", w[:, :, k, l], xp[:, k:k + Ho, l:l + Wo])
+    return y

@@ -1,0 +1,178 @@
+"""Pins of the oracle's BFV layer against homomorphic identities, key
+relations and big-integer brute force on tiny rings (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import he
+from tests.bruteforce import centred, crt, negacyclic_int, negacyclic_mod, round_tq
+
+
+def small_params(N=16, bits=(50, 50, 50, 50), t=65537):
+    return he.Params(N, he.gen_primes(N, list(bits)), t)
+
+
+def rns_to_int(P, poly):
+    """[L][N] residues -> list of N integers in [0, q)."""
+    return [crt([int(poly[i][k]) for i in range(P.L)], P.q) for k in range(P.N)]
+
+
+def test_keygen_relations():
+    P = small_params(32)
+    K = he.keygen(P, 5, True)
+    s = [int(v) for v in K.sk]
+    assert set(s) <= {-1, 0, 1}
+    Q = P.Q
+    b, a = rns_to_int(P, K.pk[0]), rns_to_int(P, K.pk[1])
+    # b + a s = -e, e a small CBD error
+    e = [centred((bb + v) % Q, Q) for bb, v in zip(b, negacyclic_int(a, s))]
+    assert max(abs(v) for v in e) <= 21 and any(e)
+    s2 = negacyclic_int(s, s)
+    for j in range(P.ell):
+        r0, r1 = rns_to_int(P, K.rlk[j][0]), rns_to_int(P, K.rlk[j][1])
+        # rlk_j0 + rlk_j1 s - 2^(16 j) s^2 = -e_j
+        ej = [centred((x + y - (1 << (16 * j)) * z) % Q, Q) for x, y, z in zip(r0, negacyclic_int(r1, s), s2)]
+        assert max(abs(v) for v in ej) <= 21
+
+
+@pytest.mark.parametrize("N,bits,t", [(16, (36, 36, 36), 65537), (64, (50,) * 4, 1032193), (4096, (36,) * 3, 65537)])
+def test_encrypt_decrypt_roundtrip(N, bits, t):
+    P = he.Params(N, he.gen_primes(N, list(bits)), t)
+    K = he.keygen(P, 9, False)
+    rng = np.random.default_rng(N)
+    m = rng.integers(0, t, (3, N), dtype=np.uint64)
+    ct = he.encrypt(P, K, m, 77)
+    assert np.array_equal(he.decrypt(P, K, ct), m)
+    # fresh noise |e1 + e u + e2 s| is far below Delta/2
+    assert he.noise_bits(P, K, ct[0], m[0]) < 20
+
+
+def test_decrypt_rounding_boundaries():
+    # ct = (x, 0) decrypts to floor((t x + floor(q/2)) / q) mod t
+    P = small_params(16, (36, 36, 36), 65537)
+    K = he.keygen(P, 1, False)
+    Q, t = P.Q, P.t
+    xs = [0, 1, Q - 1, Q // 2, Q // 2 + 1, Q // (2 * t), Q // (2 * t) + 1, (Q // t) * 5 + Q // (2 * t)]
+    for x in xs:
+        ct = np.zeros((2, P.L, P.N), dtype=np.uint64)
+        for i, qi in enumerate(P.q):
+            ct[0, i, 3] = x % qi
+        m = he.decrypt(P, K, ct)[0]
+        assert int(m[3]) == ((t * x + Q // 2) // Q) % t
+        assert int(m[0]) == 0
+
+
+def test_cpmul_ccadd_identity():
+    P = small_params(64, (50,) * 4, 1032193)
+    K = he.keygen(P, 3, False)
+    rng = np.random.default_rng(4)
+    t = P.t
+    m = rng.integers(0, t, (3, P.N), dtype=np.uint64)
+    pt = rng.integers(0, t, (2, P.N), dtype=np.uint64)
+    ct = he.encrypt(P, K, m, 8)
+    # out0 = ct0 * pt0 + ct1 * pt1 ; out1 = ct2 * pt0 + add(=ct0)
+    out = he.cpmul_terms(P, ct, pt, [[(0, 0), (1, 1)], [(2, 0)]],
+                         add=np.stack([np.zeros_like(ct[0]), ct[0]]))
+    dec = he.decrypt(P, K, out)
+    want0 = [(x + y) % t for x, y in zip(negacyclic_mod(m[0], pt[0], t), negacyclic_mod(m[1], pt[1], t))]
+    want1 = [(x + int(y)) % t for x, y in zip(negacyclic_mod(m[2], pt[0], t), m[0])]
+    assert [int(v) for v in dec[0]] == want0
+    assert [int(v) for v in dec[1]] == want1
+
+
+def test_cpmul_centred_lift_of_plaintext():
+    # pt = t-1 is the constant -1: ct * pt must decrypt to -m and the
+    # ciphertext must equal the negation of ct (centred lift, not t-1)
+    P = small_params(16, (36, 36, 36), 65537)
+    K = he.keygen(P, 3, False)
+    m = np.arange(16, dtype=np.uint64)
+    ct = he.encrypt(P, K, m, 2)
+    pt = np.zeros((1, 16), dtype=np.uint64)
+    pt[0, 0] = P.t - 1
+    out = he.cpmul_terms(P, ct, pt, [[(0, 0)]])
+    for i, qi in enumerate(P.q):
+        assert np.array_equal(out[0, :, i], (np.uint64(qi) - ct[0, :, i]) % np.uint64(qi))
+
+
+def ccmul_bruteforce(P, K, a, b, group_pairs):
+    """Exact CCMul of the definition with Python integers and schoolbook products."""
+    Q, t = P.Q, P.t
+    N, L = P.N, P.L
+    d = [[0] * N for _ in range(3)]
+    for (ca, cb) in group_pairs:
+        a0 = [centred(v, Q) for v in rns_to_int(P, ca[0])]
+        a1 = [centred(v, Q) for v in rns_to_int(P, ca[1])]
+        b0 = [centred(v, Q) for v in rns_to_int(P, cb[0])]
+        b1 = [centred(v, Q) for v in rns_to_int(P, cb[1])]
+        for k, v in enumerate(negacyclic_int(a0, b0)):
+            d[0][k] += v
+        for k, (v, w) in enumerate(zip(negacyclic_int(a0, b1), negacyclic_int(a1, b0))):
+            d[1][k] += v + w
+        for k, v in enumerate(negacyclic_int(a1, b1)):
+            d[2][k] += v
+    r = [[round_tq(v, t, Q) % Q for v in dj] for dj in d]
+    c0, c1 = r[0][:], r[1][:]
+    B = 1 << P.base_log2
+    for j in range(P.ell):
+        dig = [(v >> (P.base_log2 * j)) % B for v in r[2]]
+        k0 = rns_to_int(P, K.rlk[j][0])
+        k1 = rns_to_int(P, K.rlk[j][1])
+        for k, v in enumerate(negacyclic_int(dig, k0)):
+            c0[k] = (c0[k] + v) % Q
+        for k, v in enumerate(negacyclic_int(dig, k1)):
+            c1[k] = (c1[k] + v) % Q
+    out = np.zeros((2, L, N), dtype=np.uint64)
+    for i, qi in enumerate(P.q):
+        out[0, i] = [v % qi for v in c0]
+        out[1, i] = [v % qi for v in c1]
+    return out
+
+
+@pytest.mark.parametrize("bits,t", [((36, 36, 36), 65537), ((50,) * 4, 1032193), ((60, 60), 17)])
+def test_ccmul_bits_equal_bruteforce(bits, t):
+    P = he.Params(8, he.gen_primes(8, list(bits)), t)
+    K = he.keygen(P, 21, True)
+    rng = np.random.default_rng(2)
+    m = rng.integers(0, t, (4, 8), dtype=np.uint64)
+    ct = he.encrypt(P, K, m, 5)
+    got = he.ccmul(P, K, ct, ct, [(0, 1), (2, 3)], group=2)
+    want = ccmul_bruteforce(P, K, ct, ct, [(ct[0], ct[1]), (ct[2], ct[3])])
+    assert np.array_equal(got[0], want)
+    got1 = he.ccmul(P, K, ct, ct, [(1, 3)], group=1)
+    assert np.array_equal(got1[0], ccmul_bruteforce(P, K, ct, ct, [(ct[1], ct[3])]))
+
+
+@pytest.mark.parametrize("N,bits,t", [(64, (50,) * 4, 1032193), (1024, (36,) * 3, 65537)])
+def test_ccmul_decrypts_to_product(N, bits, t):
+    P = he.Params(N, he.gen_primes(N, list(bits)), t)
+    K = he.keygen(P, 4, True)
+    rng = np.random.default_rng(N + 1)
+    m = rng.integers(0, t, (4, N), dtype=np.uint64)
+    ct = he.encrypt(P, K, m, 6)
+    out = he.ccmul(P, K, ct[:2], ct[2:], [(0, 0), (1, 1)], group=2)
+    dec = he.decrypt(P, K, out)[0]
+    want = [(x + y) % t for x, y in zip(negacyclic_mod(m[0], m[2], t), negacyclic_mod(m[1], m[3], t))]
+    assert [int(v) for v in dec] == want
+
+
+def test_round_scalar_against_floor_division():
+    P = small_params(16, (50,) * 4, 1032193)
+    Q, t = P.Q, P.t
+    rng = np.random.default_rng(7)
+    vals = [0, 1, -1, Q, -Q, Q // 2, -(Q // 2), Q * Q, -(Q * Q) + 12345]
+    vals += [int(rng.integers(1, 2 ** 62)) * int(rng.integers(1, 2 ** 62)) * (1 if i % 2 else -1) * Q // 7
+             for i in range(20)]
+    for v in vals:
+        want = round_tq(v, t, Q)
+        assert he.round_scalar(P, v) == [want % qi for qi in P.q]
+
+
+def test_ppmul_equals_schoolbook_mod_t():
+    N = 64
+    for t in (65537, 1032193, 1099511480321, 255):
+        P = he.Params(N, he.gen_primes(N, [50]), t)
+        rng = np.random.default_rng(t % 1000)
+        a = rng.integers(0, t, (2, N), dtype=np.uint64)
+        b = rng.integers(0, t, (2, N), dtype=np.uint64)
+        got = he.ppmul_terms(P, a, b, [[(0, 0), (1, 1)]])[0]
+        want = [(x + y) % t for x, y in zip(negacyclic_mod(a[0], b[0], t), negacyclic_mod(a[1], b[1], t))]
+        assert [int(v) for v in got] == want

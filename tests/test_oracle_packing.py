@@ -1,0 +1,176 @@
+"""Pins of the oracle's packing: the toy example of Fig. 7, Eq. 1-2 taken
+literally, brute-force convolution through polynomial products for both
+encodings and every padding, and the protocol identity of Section 3.2."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import he, packing, protocol
+from paper_2409_16675_gb300 import workloads as wl
+from tests.bruteforce import negacyclic_int
+from tests.conftest import read_golden
+
+
+def deg(poly):
+    nz = np.nonzero(np.asarray(poly))[0]
+    return int(nz[-1]) if len(nz) else -1
+
+
+def test_toy_example_fig7():
+    g = read_golden("toy_example_fig7.txt")
+    H, W, h, pad = (int(g[k][0]) for k in ("H", "W", "h", "pad"))
+    x = np.array([[[3, 5], [7, 11]]])
+    w = np.array([[[[2, 13], [17, 19]]]])
+    # unpartitioned packing (a ring large enough to hold everything)
+    pc = packing.make_plan("conv", 64, 1, H, W, 1, h, pad)
+    assert pc.T == 1 and pc.G == 1
+    xa = packing.encode_input(pc, x, 1 << 20)[0, 0]
+    wa = packing.encode_kernel(pc, w, 1 << 20)[0, 0]
+    assert deg(xa) == int(g["conv_deg_x"][0]) and deg(wa) == int(g["conv_deg_w"][0])
+    used = sorted(k for (k, a, b) in packing.output_slots(pc, 0))
+    span = range(min(used), max(used) + 1)
+    assert sorted(set(span) - set(used)) == [int(v) for v in g["conv_unused"]]
+    pr = packing.make_plan("corr", 64, 1, H, W, 1, h, pad)
+    assert pr.O == max(W, H) + h - 1 == 3
+    xb = packing.encode_input(pr, x, 1 << 20)[0, 0]
+    wb = packing.encode_kernel(pr, w, 1 << 20)[0, 0]
+    assert deg(xb) == int(g["corr_deg_x"][0]) and deg(wb) == int(g["corr_deg_w"][0])
+    assert sorted(k for (k, a, b) in packing.output_slots(pr, 0)) == [int(v) for v in g["corr_used"]]
+    # multiplication counts with the degree capped (capacity = cap + 1 coefficients)
+    cap = int(g["degree_cap"][0]) + 1
+    pc9 = packing.make_plan("conv", cap, 1, H, W, 1, h, pad)
+    pr9 = packing.make_plan("corr", cap, 1, H, W, 1, h, pad)
+    assert pc9.G * pc9.T == int(g["conv_products"][0])
+    assert pr9.G * pr9.T == int(g["corr_products"][0])
+    y = protocol.conv_reference(x, w, pad)
+    for p in (pc, pr, pc9, pr9):
+        got = np.zeros_like(y)
+        xs = packing.encode_input(p, x, 1 << 40)
+        ws = packing.encode_kernel(p, w, 1 << 40)
+        for t in range(p.T):
+            acc = [0] * p.N
+            for gg in range(p.G):
+                prod = negacyclic_int([int(v) for v in xs[t, gg]], [int(v) for v in ws[0, gg]])
+                acc = [u + v for u, v in zip(acc, prod)]
+            for (k, a, b) in packing.output_slots(p, t):
+                got[0, a, b] = acc[k]
+        assert np.array_equal(got, y)
+
+
+def test_eq1_eq2_literal_single_channel():
+    # Eq. 1: x^[iO+j] = x[i,j]; Eq. 2: w^[(h-i-1)O + (h-j-1)] = w[i,j]; O = max(W,H)+h-1
+    H, W, h = 5, 7, 3
+    rng = np.random.default_rng(0)
+    x = rng.integers(1, 9, (1, H, W))
+    w = rng.integers(1, 9, (1, 1, h, h))
+    p = packing.make_plan("corr", 1024, 1, H, W, 1, h, h - 1)
+    assert p.T == 1 and p.O == max(W, H) + h - 1
+    xa = packing.encode_input(p, x, 1000)[0, 0]
+    wa = packing.encode_kernel(p, w, 1000)[0, 0]
+    for i in range(H):
+        for j in range(W):
+            assert xa[i * p.O + j] == x[0, i, j]
+    for i in range(h):
+        for j in range(h):
+            assert wa[(h - i - 1) * p.O + (h - j - 1)] == w[0, 0, i, j]
+    assert np.count_nonzero(xa) == H * W and np.count_nonzero(wa) == h * h
+
+
+def shapes():
+    rng = np.random.default_rng(42)
+    out = []
+    for _ in range(14):
+        h = int(rng.choice([1, 2, 3, 5]))
+        C = int(rng.integers(1, 5))
+        H = int(rng.integers(h, 12))
+        W = int(rng.integers(h, 12))
+        pad = int(rng.integers(0, h))
+        N = int(rng.choice([64, 128, 256, 512]))
+        out.append((N, C, H, W, 2, h, pad))
+    out += [(64, 3, 8, 8, 2, 3, 1), (128, 1, 9, 5, 2, 5, 4), (64, 2, 4, 11, 1, 2, 0), (256, 4, 1, 1, 3, 1, 0)]
+    return out
+
+
+@pytest.mark.parametrize("enc", ["conv", "corr"])
+@pytest.mark.parametrize("shape", shapes())
+def test_packed_products_equal_bruteforce_conv(enc, shape):
+    N, C, H, W, M, h, pad = shape
+    try:
+        p = packing.make_plan(enc, N, C, H, W, M, h, pad)
+    except ValueError:
+        pytest.skip("shape does not fit this ring at all")
+    rng = np.random.default_rng(sum(shape))
+    x = rng.integers(0, 256, (C, H, W))
+    w = rng.integers(-8, 8, (M, C, h, h))
+    t = 1 << 40
+    xs = packing.encode_input(p, x, t)
+    ws = packing.encode_kernel(p, w, t)
+    prod = np.zeros((M, p.T, N), dtype=np.uint64)
+    for m in range(M):
+        for tt in range(p.T):
+            acc = [0] * N
+            for g in range(p.G):
+                pr = negacyclic_int([int(v) for v in xs[tt, g]], [int(v) for v in ws[m, g]])
+                acc = [a + b for a, b in zip(acc, pr)]
+            prod[m, tt] = [v % t for v in acc]
+    y = packing.decode(p, prod, t)
+    assert np.array_equal(y, protocol.conv_reference(x, w, pad))
+    # every output is decoded exactly once
+    seen = [(a, b) for tt in range(p.T) for (_, a, b) in packing.output_slots(p, tt)]
+    assert len(seen) == len(set(seen)) == p.Ho * p.Wo
+
+
+def test_plan_search_prefers_fewest_products():
+    # exhaustive check on small cases: no feasible window gives fewer products
+    for (N, C, H, W, h, pad) in [(64, 2, 6, 6, 3, 1), (128, 3, 9, 7, 3, 2), (256, 1, 15, 15, 5, 2)]:
+        pr = packing.plan_correlated(N, C, H, W, 1, h, pad)
+        Ho, Wo = H + 2 * pad - h + 1, W + 2 * pad - h + 1
+        for th, tw in itertools.product(range(1, Ho + 1), range(1, Wo + 1)):
+            tiles = packing._corr_tiles(H, W, h, pad, th, tw)
+            O, S, geo = packing._corr_geometry(tiles, h, pad)
+            if packing._corr_fits(1, S, geo, N):
+                assert pr.G * pr.T <= C * len(tiles)
+
+
+def test_complexity_identity_section33():
+    # N1 - N2 = floor((h+1)/2) H + floor((h-1)/2) h for the paper's N1, N2
+    # (documentation check of the paper's algebra, not of the oracle)
+    for H in range(1, 80):
+        for h in range(1, 12):
+            N1 = ((h - 1) // 2 + H - 1) * (H + h - 1) + H + (h - 1) // 2
+            N2 = (H + h - 1) * (H - 1)
+            assert N1 - N2 == ((h + 1) // 2) * H + ((h - 1) // 2) * h
+
+
+def test_fig8_sweep_correlated_never_needs_more_products():
+    """Fig. 8 (multiplication counts, padded 5x5 conv with C = M = 3, inputs
+    8..64, then kernels at 64x64).  The figure is missing from the source and
+    its 4x / 5.1x ratios are not reproduced by the plans here; what holds is
+    that the correlated plan never needs more products than the conventional
+    one.  The computed counts are recorded in the design doc."""
+    for N in (4096, 8192):
+        for H in (8, 16, 32, 64):
+            a = packing.make_plan("conv", N, 3, H, H, 3, 5, 2)
+            b = packing.make_plan("corr", N, 3, H, H, 3, 5, 2)
+            assert b.G * b.T <= a.G * a.T
+        for h in (3, 5, 7):
+            a = packing.make_plan("conv", N, 3, 64, 64, 3, h, h // 2)
+            b = packing.make_plan("corr", N, 3, 64, 64, 3, h, h // 2)
+            assert b.G * b.T <= a.G * a.T
+
+
+@pytest.mark.parametrize("enc,pad", [("conv", 0), ("corr", 1), ("corr", 2), ("conv", 2)])
+def test_protocol_identity_decodes_to_conv(enc, pad):
+    spec = wl.RingSpec(1024, (36, 36, 36), 65537)
+    P = he.Params.from_spec(spec)
+    plan = packing.make_plan(enc, P.N, 3, 10, 9, 2, 3, pad)
+    x = wl.activations(3, (3, 10, 9))
+    w = wl.weights(4, (2, 3, 3, 3))
+    run = protocol.run_layer(P, plan, x, w, wl.protocol_seeds(11))
+    assert np.array_equal(run.y, protocol.conv_reference(x, w, pad))
+    # Dec(c) - p = x^ w^ in R_t for every output polynomial
+    dec = he.decrypt(P, run.keys, run.out)
+    xw = he.ppmul_terms(P, run.x_polys, run.w_polys, packing.product_terms(plan))
+    tt = np.uint64(P.t)
+    assert np.array_equal((dec + tt - run.p) % tt, xw)
