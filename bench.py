@@ -1,0 +1,295 @@
+"""Benchmark: encrypted CryptoTrain-P conv layers per second on GB300.
+
+Workload (one step): a batch of B images through the 3x32x32 -> 16-channel
+3x3 same-padded conv layer, correlated encoding, ring N = 8192 with four
+50-bit RNS limbs and t = 1032193.  A step is one pass of the whole hot path:
+encode x and w, draw the masks, encrypt x, w and the masks, the offline
+CCMul-Precompute ([r^x r^w] with relinearisation), the online fused CPMul +
+CCAdd, PPMul, decryption and decoding.  Keys are generated once, before the
+timed region (they stay resident on the device).
+
+value: layers (images) per second over all ranks; e2e: the same through the
+public API with the input tensors copied from pinned host memory and the
+decoded output copied back inside the timed region.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload.  Under torchrun every rank runs its own batch (weak scaling,
+no data-path collective); only the timing uses collectives.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Encrypted conv layers/s & NTT HBM GB/s (% of peak) vs plain launch; p50/p99 latency"
+UNIT = "layers/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        mx = max((float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def cpu_oracle_layers(seconds_budget: float, steps: int = 1):
+    """Time the CPU oracle on one image of the layer, restricted to the first
+    m output channels so that `steps` samples fit the budget; returns
+    (layers/s equivalent, description, threads)."""
+    import numpy as np  # noqa: F401
+    from oracle import he, packing, protocol
+    from paper_2409_16675_gb300 import workloads as wl
+
+    w = wl.CONV_MID
+    s = w.shape
+    P = he.Params.from_spec(w.ring)
+    keys = he.keygen(P, 1, True)
+    # one output channel first, to size the sample
+    m_sel = 1
+    x, k = wl.layer_inputs(w, 1)
+    plan = packing.make_plan(w.encoding, P.N, s.C, s.H, s.W, m_sel, s.h, s.pad)
+    t0 = time.perf_counter()
+    protocol.run_layer(P, plan, x[0], k[:m_sel], wl.protocol_seeds(w.seed), keys=keys)
+    per_channel = time.perf_counter() - t0
+    m_sel = int(max(1, min(s.M, seconds_budget / max(steps, 1) / per_channel)))
+    plan = packing.make_plan(w.encoding, P.N, s.C, s.H, s.W, m_sel, s.h, s.pad)
+    times = []
+    for i in range(steps):
+        t0 = time.perf_counter()
+        protocol.run_layer(P, plan, x[0], k[:m_sel], wl.protocol_seeds(w.seed + i), keys=keys)
+        times.append(time.perf_counter() - t0)
+    per_layer = (sum(times) / len(times)) * s.M / m_sel
+    desc = ("one 3x32x32 image, %d of the %d output channels per sample (whole CryptoTrain-P layer: "
+            "encode, masks, 4 encryptions, CCMul-Precompute, CPMul, PPMul, decrypt, decode), "
+            "scaled to a full layer; keygen excluded" % (m_sel, s.M))
+    return 1.0 / per_layer, desc, times
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_2409_16675_gb300 import workloads as wl
+    budget = 150.0
+    val, desc, times = cpu_oracle_layers(budget, max(1, args.steps))
+    w = wl.CONV_MID
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "batch": 1, "N": w.ring.N, "L": w.ring.L, "t": w.ring.t,
+                       "encoding": w.encoding},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
+
+    w = wl.CONV_MID
+    s = w.shape
+    B = args.batch
+    ctx = layer.Context(w.ring, device=local)
+    keys = layer.Keys(ctx, w.seed * 7 + 1 + 1000 * rank, True)
+    plan = layer.Plan(ctx, s, w.encoding)
+    pl = layer.PLayer(ctx, keys, plan, B)
+    x_h, k_h = wl.layer_inputs(w, B)
+    x_h = x_h.copy()
+    x_h[0, 0, 0, 0] = rank % 256
+    x = torch.from_numpy(x_h).cuda()
+    k = torch.from_numpy(k_h).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        return pl.step(x, k, wl.protocol_seeds(w.seed + 17 * i + 100003 * rank))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    nv.he_trace_enable(ctx.h, True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    nv.he_trace_enable(ctx.h, False)
+    trace = nv.he_trace_read(ctx.h)
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * B * args.steps / (ms / 1000.0)
+
+    # ---- end to end through the API with host buffers
+    xp = torch.from_numpy(x_h).pin_memory()
+    kp = torch.from_numpy(k_h).pin_memory()
+    yp = torch.empty(pl.buf.y.shape, dtype=torch.int64).pin_memory()
+    xd, kd = torch.empty_like(x), torch.empty_like(k)
+
+    def e2e_step(i):
+        xd.copy_(xp, non_blocking=True)
+        kd.copy_(kp, non_blocking=True)
+        y = pl.step(xd, kd, wl.protocol_seeds(w.seed + 31 * i + 100003 * rank))
+        yp.copy_(y, non_blocking=True)
+
+    for i in range(max(1, args.warmup)):
+        e2e_step(i)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        e2e_step(1000 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ems = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([ems], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e_value = ws * B * args.steps / (ems / 1000.0)
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    # ---- roofline of the dominant kernel family
+    peak, peak_kind = peaks()
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    name, (launches, tot_ms, byt, mm) = dom
+    achieved = byt / (tot_ms / 1000.0) / 1e9
+    roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+            "avg_launch_us": 1000.0 * tot_ms / launches,
+            "modmul_rate_T_per_s": mm / (tot_ms / 1000.0) / 1e12}
+    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(u[1] for u in trace.values()),
+                   "GB/s": v[2] / (v[1] / 1000.0) / 1e9 if v[1] else None} for k, v in trace.items()}
+    launches_total = sum(v[0] for v in trace.values())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": w.name, "batch": B, "N": w.ring.N, "L": w.ring.L, "t": w.ring.t,
+                       "encoding": w.encoding, "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (working set of one step > 129 MB)"},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_h.nbytes + k_h.nbytes),
+                    "d2h_bytes_per_step": int(yp.numel() * 8)},
+            "gpu_launches": int(launches_total),
+            "roofline": roof,
+            "kernels": kernels}
+    if not args.no_cpu_baseline and ws == 1:
+        val, desc, _ = cpu_oracle_layers(20.0, 1)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * cryptotrain.h -- C ABI of the GB300 library for the homomorphic linear
+ * layers of CryptoTrain (arXiv 2409.16675): RLWE/BFV ciphertext x plaintext
+ * polynomial convolution (CPMul + CCAdd) in the conventional row-major and the
+ * correlated polynomial encodings, the offline CCMul-Precompute path
+ * (ciphertext x ciphertext tensor product, exact rescaling,
+ * relinearisation), PPMul, encryption and decryption.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: HE_OK (0) or a negative HE_ERR_* code.  A failing call
+ *    leaves a message retrievable with he_last_error().  No call aborts the
+ *    process.
+ *  - Handles (he_ctx, he_keys, he_plan) are owned by the library and freed by
+ *    the matching *_destroy call.
+ *  - Data buffers are caller-owned DEVICE pointers (cudaMalloc / PyTorch
+ *    tensors) unless a parameter says "host"; the library never frees them.
+ *    All are dense, C-contiguous, 8-byte aligned.
+ *  - Every compute call is asynchronous on the given cudaStream_t (NULL = the
+ *    legacy default stream).  A context owns one scratch workspace: calls on
+ *    one context must be issued from one host thread and, if they use
+ *    different streams, be ordered by the caller.  Workspace growth
+ *    synchronises the device, so make one warm-up call before capturing a
+ *    CUDA graph.
+ *  - Layouts (coefficient form, the only form that crosses this boundary):
+ *      ciphertext  uint64 [2][L][N], limb i in [0, q_i)
+ *      plaintext   uint64 [N] in [0, t)
+ *      secret key  int64  [N] in {-1, 0, 1}
+ *      public key  uint64 [2][L][N] = (b, a), b = -(a s + e)
+ *      relin key   uint64 [ell][2][L][N], rlk_j = (-(a_j s + e_j) + 2^(base*j) s^2, a_j)
+ *  - All arithmetic is exact integer arithmetic; results are bit-identical
+ *    to the CPU oracle for the same seeds.
+ */
+#ifndef CRYPTOTRAIN_H
+#define CRYPTOTRAIN_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HE_OK 0
+#define HE_ERR_INVALID_ARG -1
+#define HE_ERR_UNSUPPORTED_PARAMS -2
+#define HE_ERR_PLAN_DOES_NOT_FIT -3
+#define HE_ERR_OOM -4
+#define HE_ERR_BUDGET_EXCEEDED -5
+#define HE_ERR_TIMEOUT -6
+#define HE_ERR_CUDA -7
+
+#define HE_MAX_LIMBS 16
+
+/* encodings (Section 3.3) */
+#define HE_ENC_CONVENTIONAL 0 /* row-major packing of the zero-padded input (left half of Fig. 7) */
+#define HE_ENC_CORRELATED 1   /* Eq. 1 and Eq. 2: x^[iO+j] = x[i,j], w^[(h-i-1)O+(h-j-1)] = w[i,j] */
+
+/* roles of a tensor in an encoding */
+#define HE_ROLE_INPUT 0  /* activations x [batch][C][H][W] */
+#define HE_ROLE_KERNEL 1 /* weights     w [M][C][h][h]     */
+
+/* tensor element types */
+#define HE_DTYPE_U8 0
+#define HE_DTYPE_I8 1
+#define HE_DTYPE_I64 2
+
+/* key export selectors */
+#define HE_KEY_SK 0
+#define HE_KEY_PK 1
+#define HE_KEY_RLK 2
+
+/*
+ * Ring parameters.  Section 2 (Notations) fixes the ring A_{N,p} =
+ * Z_p[x]/(x^N+1) with N a power of two; the paper states no values, so the
+ * caller chooses them.
+ *   N            ring degree, a power of two in [1024, 16384]
+ *   L            number of RNS limbs of q, 1..HE_MAX_LIMBS
+ *   q[]          explicit limb primes (each prime, = 1 mod 2N, < 2^61,
+ *                distinct); if q[0] == 0 they are generated from prime_bits
+ *   prime_bits[] per-limb bit size b in [20, 61]: the largest unused prime
+ *                below 2^b that is = 1 mod 2N, limbs in the given order
+ *   t            plaintext modulus, 2 <= t < 2^61, coprime to every q_i.
+ *                PPMul needs t prime and t = 1 mod 2N.
+ *   base_log2    relinearisation digit size in bits, 1..32 (0 -> 16)
+ *   eta          centred-binomial error parameter, 1..32 (0 -> 21)
+ *   max_ccmul_group  largest number of tensor products summed into one CCMul
+ *                output (sizes the auxiliary basis; 0 -> 1024)
+ *   device       CUDA device ordinal
+ */
+typedef struct he_params {
+    int32_t N;
+    int32_t L;
+    int32_t prime_bits[HE_MAX_LIMBS];
+    uint64_t q[HE_MAX_LIMBS];
+    uint64_t t;
+    int32_t base_log2;
+    int32_t eta;
+    int32_t max_ccmul_group;
+    int32_t device;
+} he_params;
+
+/* Read-only description of a context (filled by he_ctx_query). */
+typedef struct he_ctx_info {
+    int32_t N, L;
+    uint64_t q[HE_MAX_LIMBS];
+    uint64_t t;
+    int32_t ell;         /* relinearisation digits = ceil(bitlen(q) / base_log2) */
+    int32_t n_aux;       /* auxiliary primes of the CCMul basis */
+    uint64_t aux[24];
+    int32_t ppmul_ok;    /* 1 if t supports he_ppmul_* */
+} he_ctx_info;
+
+/* Convolution shape (stride 1, square kernel, zero padding pad <= h-1). */
+typedef struct he_conv_shape {
+    int32_t C, H, W; /* input channels and spatial size */
+    int32_t M;       /* output channels */
+    int32_t h;       /* kernel size */
+    int32_t pad;     /* zero padding on each side */
+} he_conv_shape;
+
+/* Plan summary (filled by he_plan_query). */
+typedef struct he_plan_info {
+    int32_t encoding;
+    int32_t Cn, G;      /* channels per polynomial, channel groups */
+    int32_t th, tw;     /* output tile size */
+    int32_t Th, Tw, T;  /* tiles per image (T = Th * Tw) */
+    int32_t Hn, Wn, Ooff; /* conventional window and kernel offset */
+    int32_t O, S;       /* correlated row stride and channel stride */
+    int32_t Ho, Wo;
+} he_plan_info;
+
+typedef struct he_ctx he_ctx;
+typedef struct he_keys he_keys;
+typedef struct he_plan he_plan;
+
+/* he_setup: validate params, search the primes, build NTT / CRT tables on
+ * `device`, and return a new context in *ctx.  Errors: INVALID_ARG,
+ * UNSUPPORTED_PARAMS (no such primes, N out of range), CUDA, OOM. */
+int he_setup(const he_params *params, he_ctx **ctx);
+int he_ctx_destroy(he_ctx *ctx);
+int he_ctx_query(const he_ctx *ctx, he_ctx_info *info);
+/* Copy the last error message of ctx (NULL ctx: of the last he_setup) into
+ * buf (host, len bytes, always NUL-terminated). */
+int he_last_error(const he_ctx *ctx, char *buf, int len);
+
+/* he_keygen (Section 2, HE; the relinearisation key is what CCMul needs,
+ * Fig. 3(b)): ternary s, pk = (-(a s + e), a), and if with_relin the ell
+ * relinearisation keys, all drawn from the ChaCha20 streams of `seed`.  Keys
+ * stay resident on the device. */
+int he_keygen(he_ctx *ctx, uint64_t seed, int with_relin, he_keys **keys, cudaStream_t stream);
+int he_keys_destroy(he_keys *keys);
+/* Copy a key in coefficient form into device buffer dst (layouts above). */
+int he_keys_export(he_ctx *ctx, const he_keys *keys, int which, void *dst, cudaStream_t stream);
+
+/* he_encrypt, eps(p, pk) of Section 2: pt [n][N] in [0,t) -> ct [n][2][L][N];
+ * ct_k = (b u + e1 + Delta m, a u + e2), Delta = floor(q/t), u ternary and
+ * e1, e2 CBD drawn from the streams (seed, k).  Values of pt >= t are
+ * reduced mod t. */
+int he_encrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *pt, int n, uint64_t seed, uint64_t *ct,
+               cudaStream_t stream);
+/* he_decrypt, sigma(c, sk) of Section 2: m = floor((t [c0 + c1 s]_q +
+ * floor(q/2)) / q) mod t, exactly.  ct [n][2][L][N] -> pt [n][N]. */
+int he_decrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t stream);
+/* Uniform masks mod t (Section 3.2, preprocessing: r^x, r^w): out [n][N],
+ * polynomial k from stream (seed, k). */
+int he_sample_masks(he_ctx *ctx, uint64_t seed, int n, uint64_t *out, cudaStream_t stream);
+/* Elementwise (a - b) mod t over n values (the shares x - r^x, w - r^w). */
+int he_pt_sub(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int64_t n, uint64_t *out, cudaStream_t stream);
+
+/* he_conv_plan: window search of Section 3.3 for `encoding`; fails with
+ * PLAN_DOES_NOT_FIT when no window fits the ring. */
+int he_conv_plan(he_ctx *ctx, const he_conv_shape *shape, int encoding, he_plan **plan);
+int he_plan_destroy(he_plan *plan);
+int he_plan_query(const he_plan *plan, he_plan_info *info);
+
+/* Encoders (Section 3.3).  role INPUT: tensor [batch][C][H][W] -> polys
+ * [batch][T][G][N]; role KERNEL: tensor [M][C][h][h] -> polys [M][G][N]
+ * (batch ignored).  Values are reduced into [0, t).  The plan's encoding
+ * must match the entry point. */
+int he_encode_conventional(he_ctx *ctx, const he_plan *plan, int role, const void *tensor, int dtype, int batch,
+                           uint64_t *polys, cudaStream_t stream);
+int he_encode_correlated(he_ctx *ctx, const he_plan *plan, int role, const void *tensor, int dtype, int batch,
+                         uint64_t *polys, cudaStream_t stream);
+
+/* he_cpmul_conv: CPMul + CCAdd over a plan (Fig. 3(c); Section 3.2 online):
+ *   out[b][m][t] = sum_g ct_x[b][t][g] * pt_w[m][g]
+ *                + sum_g ct_w[m][g]    * pt_x[b][t][g]
+ *                + ct_add[b][m][t]
+ * Each family is skipped when its ciphertext pointer is NULL (at least one
+ * must be given); ct_add may be NULL.  Plaintexts in [0,t) are centre-lifted.
+ * Shapes: ct_x [batch][T][G][2][L][N], pt_w [M][G][N], ct_w [M][G][2][L][N],
+ * pt_x [batch][T][G][N], ct_add / ct_out [batch][M][T][2][L][N].
+ * Runs as one batched forward NTT and one fused MAC -> inverse NTT -> add. */
+int he_cpmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *ct_x, const uint64_t *pt_w,
+                  const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add, uint64_t *ct_out,
+                  cudaStream_t stream);
+
+/* he_ccmul_precompute: CCMul with relinearisation (Section 2, Motivation;
+ * Section 3.2 preprocessing).  Output o sums the tensor products of pairs
+ * [o*group, (o+1)*group): d0 = sum a0 b0, d1 = sum a0 b1 + a1 b0, d2 = sum
+ * a1 b1 of the centred lifts (exact integers), d_j <- floor((t d_j +
+ * floor(q/2)) / q) mod q, (c0, c1) = (d0, d1) + sum_j D_j rlk_j with D_j the
+ * base-2^base_log2 digits of d2.  ct_a [n_a][2][L][N], ct_b [n_b][2][L][N];
+ * pair_a, pair_b: HOST int32 [n_pairs] indices; out [n_pairs/group][2][L][N].
+ * Needs keys made with_relin.  group <= max_ccmul_group. */
+int he_ccmul_precompute(he_ctx *ctx, const he_keys *keys, const uint64_t *ct_a, int n_a, const uint64_t *ct_b,
+                        int n_b, const int32_t *pair_a, const int32_t *pair_b, int n_pairs, int group,
+                        uint64_t *ct_out, cudaStream_t stream);
+/* The same over a plan: out[b][m][t] = sum_g [r^x][b][t][g] (x) [r^w][m][g]
+ * (the precomputed [r^x r^w] of Section 3.2).  ct_rx [batch][T][G][2][L][N],
+ * ct_rw [M][G][2][L][N], out [batch][M][T][2][L][N]. */
+int he_ccmul_conv_precompute(he_ctx *ctx, const he_keys *keys, const he_plan *plan, int batch,
+                             const uint64_t *ct_rx, const uint64_t *ct_rw, uint64_t *ct_out, cudaStream_t stream);
+
+/* he_ppmul_conv: PPMul of Section 3.2, p[b][m][t] = sum_g pt_x[b][t][g] *
+ * pt_w[m][g] in Z_t[x]/(x^N+1).  pt_x [batch][T][G][N], pt_w [M][G][N],
+ * out [batch][M][T][N].  UNSUPPORTED_PARAMS if t is not an NTT prime. */
+int he_ppmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt_x, const uint64_t *pt_w,
+                  uint64_t *out, cudaStream_t stream);
+
+/* he_decode (Section 3.3, output positions of each encoding): out[b][m][a][c]
+ * = centred((pt - sub)[b][m][tile(a,c)][coef(a,c)] mod t) as int64, centred
+ * means v > (t-1)/2 -> v - t.  pt, sub [batch][M][T][N] (sub may be NULL);
+ * out [batch][M][Ho][Wo]. */
+int he_decode(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt, const uint64_t *sub, int64_t *out,
+              cudaStream_t stream);
+
+/* Launch tracing (profiling aid, not part of the paper's method).  While
+ * enabled, every kernel launch of the context is bracketed by two CUDA events
+ * on its stream and tagged with the kernel family name and its algorithmic
+ * bytes (each distinct input polynomial read once, each output written
+ * once) and 64-bit modular products.  he_trace_read synchronises the device,
+ * folds the recorded launches into one entry per kernel family, and clears
+ * the record.  Tracing adds two event records per launch. */
+typedef struct he_trace_entry {
+    char name[32];
+    int64_t launches;
+    double total_ms;     /* sum of event-measured launch durations */
+    double bytes;        /* algorithmic bytes, summed over launches */
+    double modmuls;      /* 64-bit modular products, summed over launches */
+} he_trace_entry;
+int he_trace_enable(he_ctx *ctx, int on);
+int he_trace_read(he_ctx *ctx, he_trace_entry *out, int max_entries, int *n_entries);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -36,36 +36,56 @@ class LayerRun:
     y: np.ndarray            # decoded [M, Ho, Wo]
 
 
-def precompute_pairs(plan):
-    """CCMul pairs (rx index, rw index), G consecutive pairs per output m*T+t."""
+def precompute_pairs(plan, batch=1):
+    """CCMul pairs (rx index, rw index), G consecutive pairs per output
+    (b, m, t) in that order; rx index (b*T + t)*G + g, rw index m*G + g."""
     pairs = []
-    for m in range(plan.M):
-        for t in range(plan.T):
-            for g in range(plan.G):
-                pairs.append((t * plan.G + g, m * plan.G + g))
+    for b in range(batch):
+        for m in range(plan.M):
+            for t in range(plan.T):
+                for g in range(plan.G):
+                    pairs.append(((b * plan.T + t) * plan.G + g, m * plan.G + g))
     return pairs
 
 
-def online_terms(plan):
-    """CPMul terms over ct = [ct_x ; ct_w] and pt = [(w - r^w) ; (x - r^x)]."""
+def online_terms(plan, batch=1):
+    """CPMul terms over ct = [ct_x ; ct_w] and pt = [(w - r^w) ; (x - r^x)],
+    output order (b, m, t)."""
     TG, MG = plan.T * plan.G, plan.M * plan.G
     terms = []
-    for m in range(plan.M):
-        for t in range(plan.T):
-            tl = []
-            for g in range(plan.G):
-                tl.append((t * plan.G + g, m * plan.G + g))
-                tl.append((TG + m * plan.G + g, MG + t * plan.G + g))
-            terms.append(tl)
+    for b in range(batch):
+        for m in range(plan.M):
+            for t in range(plan.T):
+                tl = []
+                for g in range(plan.G):
+                    xi = (b * plan.T + t) * plan.G + g
+                    tl.append((xi, m * plan.G + g))
+                    tl.append((batch * TG + m * plan.G + g, MG + xi))
+                terms.append(tl)
+    return terms
+
+
+def ppmul_terms(plan, batch=1):
+    terms = []
+    for b in range(batch):
+        for m in range(plan.M):
+            for t in range(plan.T):
+                terms.append([((b * plan.T + t) * plan.G + g, m * plan.G + g) for g in range(plan.G)])
     return terms
 
 
 def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
-    """x: [C,H,W] ints, w: [M,C,h,h] ints; seeds: workloads.ProtocolSeeds."""
+    """x: [C,H,W] or [B,C,H,W] ints, w: [M,C,h,h] ints; seeds:
+    workloads.ProtocolSeeds.  Every random object of the batch is drawn from
+    one stream per kind, object index = position in the flattened batch."""
     t = P.t
+    x = np.asarray(x)
+    if x.ndim == 3:
+        x = x[None]
+    B = x.shape[0]
     if keys is None:
         keys = he.keygen(P, seeds.keys, True)
-    xp = packing.encode_input(plan, x, t).reshape(-1, P.N)
+    xp = np.concatenate([packing.encode_input(plan, x[b], t).reshape(-1, P.N) for b in range(B)])
     wp = packing.encode_kernel(plan, w, t).reshape(-1, P.N)
     r_x = he.sample_masks(P, seeds.mask_x, xp.shape[0])
     r_w = he.sample_masks(P, seeds.mask_w, wp.shape[0])
@@ -74,18 +94,21 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
     ct_rx = he.encrypt(P, keys, r_x, seeds.enc_rx)
     ct_rw = he.encrypt(P, keys, r_w, seeds.enc_rw)
     # offline: [r^x r^w] summed over channel groups
-    rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan), plan.G)
+    rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan, B), plan.G)
     # online
     tt = np.uint64(t)
     wm = (wp + (tt - r_w)) % tt
     xm = (xp + (tt - r_x)) % tt
     ct_all = np.concatenate([ct_x, ct_w])
     pt_all = np.concatenate([wm, xm])
-    out = he.cpmul_terms(P, ct_all, pt_all, online_terms(plan), add=rr)
-    p = he.ppmul_terms(P, xm, wm, packing.product_terms(plan))
+    out = he.cpmul_terms(P, ct_all, pt_all, online_terms(plan, B), add=rr)
+    p = he.ppmul_terms(P, xm, wm, ppmul_terms(plan, B))
     dec = he.decrypt(P, keys, out)
     z = (dec + (tt - p)) % tt
-    y = packing.decode(plan, z.reshape(plan.M, plan.T, P.N), t)
+    zz = z.reshape(B, plan.M, plan.T, P.N)
+    y = np.stack([packing.decode(plan, zz[b], t) for b in range(B)])
+    if B == 1:
+        y = y[0]
     return LayerRun(plan, keys, xp, wp, r_x, r_w, ct_x, ct_w, ct_rx, ct_rw, rr, out, p, y)
 
 

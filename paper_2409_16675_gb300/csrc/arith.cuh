@@ -1,0 +1,158 @@
+// arith.cuh -- device arithmetic: Shoup / Harvey modular products, lazy
+// butterflies, multi-word CRT, ChaCha20.
+//
+// Modular products follow V. Shoup's precomputed-quotient method as used for
+// NTTs by D. Harvey, "Faster arithmetic for number-theoretic transforms"
+// (J. Symbolic Computation, 2014): for w < q < 2^62 and w' = floor(w 2^64 / q),
+// a*w - floor(a w' / 2^64)*q lies in [0, 2q) for every 64-bit a.
+#pragma once
+#include "internal.h"
+
+namespace he {
+
+__device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
+    u64 qh = __umul64hi(a, ws);
+    return a * w - qh * q;  // [0, 2q)
+}
+__device__ __forceinline__ u64 red1(u64 a, u64 q) { return a >= q ? a - q : a; }
+__device__ __forceinline__ u64 addm(u64 a, u64 b, u64 q) { return red1(a + b, q); }   // a,b < q
+__device__ __forceinline__ u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+// full product a*b mod q for a,b < q via the 128-bit value
+__device__ __forceinline__ void mul128(u64 a, u64 b, u64 &lo, u64 &hi) {
+    lo = a * b;
+    hi = __umul64hi(a, b);
+}
+// (hi 2^64 + lo) mod q, fully reduced, any hi, lo < 2^64
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const ModDev &M) {
+    u64 a = shoup(hi, M.r64, M.r64s, M.q);   // hi * 2^64 mod q, [0, 2q)
+    u64 b = shoup(lo, 1, M.one_s, M.q);      // lo mod q, [0, 2q)
+    u64 r = a + b;                           // [0, 4q)
+    r = r >= M.twoq ? r - M.twoq : r;
+    return red1(r, M.q);
+}
+// a (< 2^64) mod q given r64-style constants, fully reduced
+__device__ __forceinline__ u64 reduce64(u64 a, u64 q, u64 one_s) { return red1(shoup(a, 1, one_s, q), q); }
+
+// ---------------------------------------------------------------- multi-word
+// Little-endian arrays of 64-bit words, compile-time capacity MW, runtime
+// used length W <= MW.  Loops are unrolled to MW with guards so the arrays
+// stay in registers.
+
+// X = sum_i y_i hat_i then reduced into [0, M); returns the number of M
+// subtracted (the CRT overflow count v).
+template <int MW>
+__device__ __forceinline__ int crt_compose(const CrtDev &B, const u64 *y, u64 (&X)[MW]) {
+#pragma unroll
+    for (int k = 0; k < MW; k++) X[k] = 0;
+    for (int i = 0; i < B.n; i++) {
+        u64 carry = 0;
+#pragma unroll
+        for (int k = 0; k < MW; k++) {
+            if (k < B.W) {
+                u64 lo, hi;
+                mul128(y[i], B.hat[i][k], lo, hi);
+                u64 s = X[k] + lo;
+                hi += (s < lo);
+                s += carry;
+                hi += (s < carry);
+                X[k] = s;
+                carry = hi;
+            }
+        }
+    }
+    int v = 0;
+    for (int it = 0; it < B.n; it++) {
+        // X >= M ?
+        bool ge = true, decided = false;
+#pragma unroll
+        for (int k = MW - 1; k >= 0; k--) {
+            if (k < B.W && !decided && X[k] != B.M[k]) { ge = X[k] > B.M[k]; decided = true; }
+        }
+        if (!ge) break;
+        u64 br = 0;
+#pragma unroll
+        for (int k = 0; k < MW; k++) {
+            if (k < B.W) {
+                u64 d = X[k] - B.M[k];
+                u64 b1 = X[k] < B.M[k];
+                u64 d2 = d - br;
+                u64 b2 = d < br;
+                X[k] = d2;
+                br = b1 | b2;
+            }
+        }
+        v++;
+    }
+    return v;
+}
+
+// residues r_i (< m_i) -> y_i = r_i * inv_i mod m_i
+__device__ __forceinline__ u64 crt_y(const CrtDev &B, int i, u64 r) {
+    return red1(shoup(r, B.inv[i], B.invs[i], B.m[i]), B.m[i]);
+}
+
+template <int MW>
+__device__ __forceinline__ bool mw_greater(const u64 (&X)[MW], const u64 *Y, int W) {
+    bool gt = false, decided = false;
+#pragma unroll
+    for (int k = MW - 1; k >= 0; k--) {
+        if (k < W && !decided && X[k] != Y[k]) { gt = X[k] > Y[k]; decided = true; }
+    }
+    return gt;
+}
+
+// X mod p by Horner over 64-bit words: r <- r 2^64 + w
+template <int MW>
+__device__ __forceinline__ u64 mw_mod(const u64 (&X)[MW], int W, u64 p, u64 r64, u64 r64s, u64 one_s) {
+    u64 r = 0;
+#pragma unroll
+    for (int k = MW - 1; k >= 0; k--) {
+        if (k < W) {
+            u64 a = shoup(r, r64, r64s, p);        // r 2^64 mod p, [0, 2p)
+            u64 b = shoup(X[k], 1, one_s, p);      // [0, 2p)
+            u64 s = a + b;                         // [0, 4p)
+            s = s >= 2 * p ? s - 2 * p : s;
+            r = red1(s, p);
+        }
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- ChaCha20
+// Block function of RFC 8439 (section 2.3): 20 rounds over the 4x4 state of
+// constants, 256-bit key, 32-bit counter and 96-bit nonce, then the input
+// state added back.
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+#define HE_QR(a, b, c, d)                                        \
+    a += b; d ^= a; d = rotl(d, 16); c += d; b ^= c; b = rotl(b, 12); \
+    a += b; d ^= a; d = rotl(d, 8);  c += d; b ^= c; b = rotl(b, 7);
+
+// Stream of 64-bit words of (seed, tag, idx, limb): key = (seed lo, seed hi,
+// 0 x 6), nonce = (tag, idx, limb), block counter = word / 8; word w is state
+// words 2(w%8) (low half) and 2(w%8)+1 (high half).
+__device__ __forceinline__ void chacha_block8(uint64_t seed, uint32_t tag, uint32_t idx, uint32_t limb,
+                                              uint32_t counter, u64 (&out)[8]) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t x0 = 0x61707865u, x1 = 0x3320646eu, x2 = 0x79622d32u, x3 = 0x6b206574u;
+    uint32_t x4 = k0, x5 = k1, x6 = 0, x7 = 0, x8 = 0, x9 = 0, x10 = 0, x11 = 0;
+    uint32_t x12 = counter, x13 = tag, x14 = idx, x15 = limb;
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+        HE_QR(x0, x4, x8, x12) HE_QR(x1, x5, x9, x13) HE_QR(x2, x6, x10, x14) HE_QR(x3, x7, x11, x15)
+        HE_QR(x0, x5, x10, x15) HE_QR(x1, x6, x11, x12) HE_QR(x2, x7, x8, x13) HE_QR(x3, x4, x9, x14)
+    }
+    x0 += 0x61707865u; x1 += 0x3320646eu; x2 += 0x79622d32u; x3 += 0x6b206574u;
+    x4 += k0; x5 += k1;
+    x12 += counter; x13 += tag; x14 += idx; x15 += limb;
+    out[0] = (u64)x0 | ((u64)x1 << 32);
+    out[1] = (u64)x2 | ((u64)x3 << 32);
+    out[2] = (u64)x4 | ((u64)x5 << 32);
+    out[3] = (u64)x6 | ((u64)x7 << 32);
+    out[4] = (u64)x8 | ((u64)x9 << 32);
+    out[5] = (u64)x10 | ((u64)x11 << 32);
+    out[6] = (u64)x12 | ((u64)x13 << 32);
+    out[7] = (u64)x14 | ((u64)x15 << 32);
+}
+#undef HE_QR
+
+}  // namespace he

@@ -1,0 +1,341 @@
+// exact.cu -- per-coefficient kernels that need all RNS limbs at once:
+// sampling, the exact base extension Q -> Q u B, the exact BFV rescaling
+// floor((t d + floor(q/2)) / q) with digit decomposition, exact decryption,
+// and the encoding / decoding gathers.
+//
+// Exactness: every value is rebuilt as a multi-word integer by CRT (sum of
+// y_i * (M/m_i), then the overflow multiples of M subtracted), so no step is
+// an approximation.  The rescaling uses the identity
+//   floor((t d + h) / q) = (t d + h - r) / q,  r = [t d + h]_q, h = floor(q/2),
+// whose right side is an exact division, evaluated modulo each auxiliary
+// prime and brought back to Q by a second exact CRT (the quotient is smaller
+// than B/2 by construction of B).
+#include "arith.cuh"
+
+namespace he {
+
+// ---------------------------------------------------------------- sampling
+__global__ void k_sample(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_limbs, int N, void *out,
+                         long long total_blocks, const ModDev *__restrict__ mods, const ExactDev *__restrict__ E,
+                         int eta) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total_blocks) return;
+    if (kind == SAMPLE_UNIFORM_Q) {
+        // 4 coefficients per ChaCha block (two words each)
+        const int per = N / 4;
+        const int b = (int)(gid % per);
+        const long long ol = gid / per;
+        const int limb = (int)(ol % n_limbs);
+        const long long obj = ol / n_limbs;
+        u64 w[8];
+        chacha_block8(seed, tag, idx0 + (uint32_t)obj, (uint32_t)limb, (uint32_t)b, w);
+        const ModDev M = mods[limb];
+        u64 *o = (u64 *)out + (obj * n_limbs + limb) * N + 4 * b;
+#pragma unroll
+        for (int j = 0; j < 4; j++) o[j] = reduce128(w[2 * j], w[2 * j + 1], M);
+        return;
+    }
+    const int per = N / 8;
+    const int b = (int)(gid % per);
+    const long long obj = gid / per;
+    u64 w[8];
+    chacha_block8(seed, tag, idx0 + (uint32_t)obj, 0u, (uint32_t)b, w);
+    if (kind == SAMPLE_UNIFORM_T) {
+        u64 *o = (u64 *)out + obj * N + 8 * b;
+#pragma unroll
+        for (int j = 0; j < 8; j++) o[j] = reduce64(w[j], E->t, E->one_ts);
+        return;
+    }
+    int8_t r[8];
+    if (kind == SAMPLE_TERNARY) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) r[j] = (int8_t)((int)__umul64hi(w[j], 3ull) - 1);
+    } else {
+        const u64 mask = (eta >= 64) ? ~0ull : ((1ull << eta) - 1);
+#pragma unroll
+        for (int j = 0; j < 8; j++) r[j] = (int8_t)(__popcll(w[j] & mask) - __popcll((w[j] >> eta) & mask));
+    }
+    int8_t *o = (int8_t *)out + obj * N + 8 * b;
+    u64 packed = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) packed |= (u64)(uint8_t)r[j] << (8 * j);
+    *(u64 *)o = packed;
+}
+
+int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_obj, int n_limbs,
+                  void *out, cudaStream_t st) {
+    const int N = c->N;
+    long long total = kind == SAMPLE_UNIFORM_Q ? (long long)n_obj * n_limbs * (N / 4) : (long long)n_obj * (N / 8);
+    if (!total) return HE_OK;
+    TraceScope ts(c, st, "sample", kind == SAMPLE_UNIFORM_Q ? 32.0 * total : (kind == SAMPLE_UNIFORM_T ? 64.0 * total : 8.0 * total), 0);
+    k_sample<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(kind, seed, tag, idx0, n_limbs, N, out, total,
+                                                               c->d_mods, c->d_exact, c->P.eta);
+    return cuda_check(c, cudaGetLastError(), "k_sample");
+}
+
+// ---------------------------------------------------------------- exact CRT kernels
+// centred lift of each coefficient (residues mod Q) to the auxiliary primes
+template <int MW>
+__global__ void k_base_extend(const u64 *__restrict__ src, long long n_polys, int L, int K, int N,
+                              u64 *__restrict__ dst, const ModDev *__restrict__ mods, const ExactDev *__restrict__ E) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n_polys * N) return;
+    const int x = (int)(gid % N);
+    const long long p = gid / N;
+    const CrtDev &Q = E->Q;
+    u64 y[MAXP];
+    for (int i = 0; i < L; i++) y[i] = crt_y(Q, i, src[(p * L + i) * N + x]);
+    u64 X[MW];
+    crt_compose<MW>(Q, y, X);
+    const bool neg = mw_greater<MW>(X, Q.Mhalf, Q.W);
+    for (int j = 0; j < K; j++) {
+        const ModDev &M = mods[L + j];
+        u64 a = mw_mod<MW>(X, Q.W, M.q, M.r64, M.r64s, M.one_s);
+        if (neg) a = subm(a, E->Q_b[j], M.q);
+        dst[(p * K + j) * N + x] = a;
+    }
+}
+
+// d: [n_out][3][L+K][N] exact tensor products (coefficient form).
+// dq: [n_out][2][L][N] rescaled d0, d1; digits: [n_out][ell][N] of rescaled d2.
+template <int MW>
+__global__ void k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K, int N, int ell, int base_log2,
+                              u64 *__restrict__ dq, uint32_t *__restrict__ digits, const ModDev *__restrict__ mods,
+                              const ExactDev *__restrict__ E) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)n_out * 3 * N) return;
+    const int x = (int)(gid % N);
+    const int j = (int)((gid / N) % 3);
+    const long long o = gid / (3LL * N);
+    const int LK = L + K;
+    const u64 *src = d + ((o * 3 + j) * LK) * N + x;
+    const CrtDev &Q = E->Q, &B = E->B;
+    u64 y[MAXP];
+    // r = [t d + floor(q/2)]_q  (residues, then exact integer)
+    for (int i = 0; i < L; i++) {
+        const u64 qi = mods[i].q;
+        const u64 td = red1(shoup(src[(long long)i * N], E->t_q[i], E->t_qs[i], qi), qi);
+        y[i] = crt_y(Q, i, addm(td, E->Qhalf_q[i], qi));
+    }
+    u64 R[MW];
+    crt_compose<MW>(Q, y, R);
+    // F = (t d + h - r) / q modulo each aux prime
+    for (int k = 0; k < K; k++) {
+        const ModDev &M = mods[L + k];
+        const u64 b = M.q;
+        const u64 rb = mw_mod<MW>(R, Q.W, b, M.r64, M.r64s, M.one_s);
+        const u64 td = red1(shoup(src[(long long)(L + k) * N], E->t_b[k], E->t_bs[k], b), b);
+        const u64 num = subm(addm(td, E->Qhalf_b[k], b), rb, b);
+        y[k] = crt_y(B, k, red1(shoup(num, E->Qinv_b[k], E->Qinv_bs[k], b), b));
+    }
+    u64 F[MW];
+    crt_compose<MW>(B, y, F);
+    const bool neg = mw_greater<MW>(F, B.Mhalf, B.W);
+    u64 f[MAXP];
+    for (int i = 0; i < L; i++) {
+        const ModDev &M = mods[i];
+        u64 a = mw_mod<MW>(F, B.W, M.q, M.r64, M.r64s, M.one_s);
+        f[i] = neg ? subm(a, E->B_q[i], M.q) : a;
+    }
+    if (j < 2) {
+        u64 *out = dq + ((o * 2 + j) * L) * N + x;
+        for (int i = 0; i < L; i++) out[(long long)i * N] = f[i];
+        return;
+    }
+    // digits of [F]_q in [0, q)
+    for (int i = 0; i < L; i++) y[i] = crt_y(Q, i, f[i]);
+    u64 X[MW];
+    crt_compose<MW>(Q, y, X);
+    const u64 dmask = base_log2 >= 64 ? ~0ull : ((1ull << base_log2) - 1);
+    uint32_t *dg = digits + (o * ell) * N + x;
+    for (int dd = 0; dd < ell; dd++) {
+        const int bit = dd * base_log2;
+        const int w = bit >> 6, sh = bit & 63;
+        u64 v = 0;
+#pragma unroll
+        for (int k = 0; k < MW; k++) {
+            if (k == w) v = X[k] >> sh;
+            if (k == w + 1 && sh + base_log2 > 64) v |= X[k] << (64 - sh);
+        }
+        dg[(long long)dd * N] = (uint32_t)(v & dmask);
+    }
+}
+
+// x: [n][L][N] = c0 + c1 s; m = floor((t x + floor(q/2)) / q) mod t
+//    = (floor(q/2) - [t x + floor(q/2)]_q) * q^-1 mod t
+template <int MW>
+__global__ void k_decrypt_exact(const u64 *__restrict__ xs, int n, int L, int N, u64 *__restrict__ m,
+                                const ModDev *__restrict__ mods, const ExactDev *__restrict__ E) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)n * N) return;
+    const int x = (int)(gid % N);
+    const long long k = gid / N;
+    const CrtDev &Q = E->Q;
+    u64 y[MAXP];
+    for (int i = 0; i < L; i++) {
+        const u64 qi = mods[i].q;
+        const u64 tx = red1(shoup(xs[(k * L + i) * N + x], E->t_q[i], E->t_qs[i], qi), qi);
+        y[i] = crt_y(Q, i, addm(tx, E->Qhalf_q[i], qi));
+    }
+    u64 R[MW];
+    crt_compose<MW>(Q, y, R);
+    const u64 t = E->t;
+    const u64 rt = mw_mod<MW>(R, Q.W, t, E->r64_t, E->r64_ts, E->one_ts);
+    m[k * N + x] = red1(shoup(subm(E->Qhalf_t, rt, t), E->Qinv_t, E->Qinv_ts, t), t);
+}
+
+static int mw_of(he_ctx *c) {
+    const int W = c->h_exact.Q.W > c->h_exact.B.W ? c->h_exact.Q.W : c->h_exact.B.W;
+    return W <= 6 ? 6 : (W <= 10 ? 10 : 18);
+}
+
+int launch_base_extend(he_ctx *c, const u64 *src, long long n_polys, u64 *dst_aux, cudaStream_t st) {
+    const long long total = n_polys * c->N;
+    if (!total) return HE_OK;
+    const unsigned g = (unsigned)((total + 127) / 128);
+    TraceScope ts(c, st, "base_extend", 8.0 * total * (c->L + c->K), 0);
+    switch (mw_of(c)) {
+    case 6: k_base_extend<6><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
+    case 10: k_base_extend<10><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
+    default: k_base_extend<18><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
+    }
+    return cuda_check(c, cudaGetLastError(), "k_base_extend");
+}
+
+int launch_scale_round(he_ctx *c, const u64 *d, int n_out, u64 *dq, uint32_t *digits, cudaStream_t st) {
+    const long long total = (long long)n_out * 3 * c->N;
+    if (!total) return HE_OK;
+    const unsigned g = (unsigned)((total + 127) / 128);
+    const int b = c->P.base_log2;
+    TraceScope ts(c, st, "scale_round", 8.0 * total * (c->L + c->K) + 8.0 * n_out * 2 * c->L * c->N +
+                  4.0 * n_out * c->ell * c->N, 0);
+    switch (mw_of(c)) {
+    case 6: k_scale_round<6><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
+    case 10: k_scale_round<10><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
+    default: k_scale_round<18><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
+    }
+    return cuda_check(c, cudaGetLastError(), "k_scale_round");
+}
+
+int launch_decrypt_exact(he_ctx *c, const u64 *x, int n, u64 *m, cudaStream_t st) {
+    const long long total = (long long)n * c->N;
+    if (!total) return HE_OK;
+    const unsigned g = (unsigned)((total + 127) / 128);
+    TraceScope ts(c, st, "decrypt_exact", 8.0 * total * (c->L + 1), 0);
+    switch (mw_of(c)) {
+    case 6: k_decrypt_exact<6><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
+    case 10: k_decrypt_exact<10><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
+    default: k_decrypt_exact<18><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
+    }
+    return cuda_check(c, cudaGetLastError(), "k_decrypt_exact");
+}
+
+// ---------------------------------------------------------------- encode / decode
+__device__ __forceinline__ u64 to_t(const void *tensor, int dtype, long long i, u64 t) {
+    long long v;
+    if (dtype == HE_DTYPE_U8) v = ((const uint8_t *)tensor)[i];
+    else if (dtype == HE_DTYPE_I8) v = ((const int8_t *)tensor)[i];
+    else v = ((const long long *)tensor)[i];
+    if (v >= 0) return (u64)v % t;
+    const u64 r = (u64)(-(v + 1)) % t;  // -(v+1) >= 0, no overflow
+    return t - 1 - r;
+}
+
+// input role: out[(b*out_batch_polys + p)*N + x] = x_b[map[p*N + x]] mod t
+__global__ void k_encode_input(const int32_t *__restrict__ map, int n_polys, int N, const void *tensor, int dtype,
+                               long long tensor_stride, int batch, long long out_batch_polys, u64 *__restrict__ out,
+                               u64 t) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = (long long)n_polys * N;
+    if (gid >= per * batch) return;
+    const long long b = gid / per;
+    const long long r = gid - b * per;
+    const int idx = map[r];
+    out[b * out_batch_polys * N + r] = idx >= 0 ? to_t(tensor, dtype, b * tensor_stride + idx, t) : 0;
+}
+
+// kernel role: out[(m*G + g)*N + x] = w[m*per_m + map[g*N + x]] mod t
+__global__ void k_encode_kernel(const int32_t *__restrict__ map, int G, int M, int N, const void *tensor, int dtype,
+                                long long per_m, u64 *__restrict__ out, u64 t) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per = (long long)G * N;
+    if (gid >= per * M) return;
+    const long long m = gid / per;
+    const long long r = gid - m * per;
+    const int idx = map[r];
+    out[gid] = idx >= 0 ? to_t(tensor, dtype, m * per_m + idx, t) : 0;
+}
+
+// out[(b*M + m)*HW + i] = centred((pt - sub)[((b*M + m)*T)*N + map[i]] mod t)
+__global__ void k_decode(const int32_t *__restrict__ map, int HW, int M, int T, int N, int batch,
+                         const u64 *__restrict__ pt, const u64 *__restrict__ sub, long long *__restrict__ out, u64 t) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)batch * M * HW) return;
+    const int i = (int)(gid % HW);
+    const long long bm = gid / HW;
+    const long long src = bm * T * N + map[i];
+    u64 v = pt[src];
+    v = v >= t ? v % t : v;
+    if (sub) {
+        u64 s = sub[src];
+        s = s >= t ? s % t : s;
+        v = v >= s ? v - s : v + t - s;
+    }
+    out[gid] = v > (t - 1) / 2 ? (long long)v - (long long)t : (long long)v;
+}
+
+__global__ void k_pt_sub(const u64 *__restrict__ a, const u64 *__restrict__ b, long long n, u64 *__restrict__ out,
+                         u64 t) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n) return;
+    u64 x = a[gid], y = b[gid];
+    x = x >= t ? x % t : x;
+    y = y >= t ? y % t : y;
+    out[gid] = x >= y ? x - y : x + t - y;
+}
+
+__global__ void k_copy_sk(const int8_t *__restrict__ s8, long long *__restrict__ sk, int N) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < N) sk[gid] = s8[gid];
+}
+
+int launch_encode(he_ctx *c, const int32_t *map, int n_polys, int map_polys, const void *tensor, int dtype,
+                  long long tensor_stride, int batch, long long out_batch_polys, u64 *out, cudaStream_t st) {
+    (void)map_polys;
+    const long long total = (long long)n_polys * c->N * batch;
+    if (!total) return HE_OK;
+    k_encode_input<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, n_polys, c->N, tensor, dtype, tensor_stride,
+                                                                     batch, out_batch_polys, out, c->P.t);
+    return cuda_check(c, cudaGetLastError(), "k_encode_input");
+}
+
+int launch_encode_kernel(he_ctx *c, const int32_t *map, int G, int M, const void *tensor, int dtype, long long per_m,
+                         u64 *out, cudaStream_t st) {
+    const long long total = (long long)G * M * c->N;
+    if (!total) return HE_OK;
+    k_encode_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, G, M, c->N, tensor, dtype, per_m, out,
+                                                                      c->P.t);
+    return cuda_check(c, cudaGetLastError(), "k_encode_kernel");
+}
+
+int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int T, int batch, const u64 *pt, const u64 *sub,
+                  int64_t *out, cudaStream_t st) {
+    const long long total = (long long)batch * M * HW;
+    if (!total) return HE_OK;
+    k_decode<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, HW, M, T, c->N, batch, pt, sub,
+                                                               (long long *)out, c->P.t);
+    return cuda_check(c, cudaGetLastError(), "k_decode");
+}
+
+int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, cudaStream_t st) {
+    if (!n) return HE_OK;
+    k_pt_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, b, n, out, c->P.t);
+    return cuda_check(c, cudaGetLastError(), "k_pt_sub");
+}
+
+int launch_copy_sk(he_ctx *c, const int8_t *s8, u64 *sk, cudaStream_t st) {
+    k_copy_sk<<<(c->N + 255) / 256, 256, 0, st>>>(s8, (long long *)sk, c->N);
+    return cuda_check(c, cudaGetLastError(), "k_copy_sk");
+}
+
+}  // namespace he

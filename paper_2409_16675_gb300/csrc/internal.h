@@ -1,0 +1,197 @@
+// internal.h -- structures shared by the host code and the kernels of the
+// GB300 homomorphic linear-layer library.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <unordered_map>
+#include <cuda_runtime.h>
+
+#include "../../include/cryptotrain.h"
+
+typedef uint64_t u64;
+
+namespace he {
+
+constexpr int MAX_MODS = 48;   // Q limbs + aux limbs + t
+constexpr int MAXP = 24;       // primes of one CRT basis
+constexpr int MAXW = 18;       // 64-bit words of a CRT sum (< n * M)
+
+// One NTT-friendly modulus: constants for Shoup products and its twiddles.
+// Twiddle index convention: entry 2^s + i is the factor of group i at stage s
+// of the merged-twist negacyclic transform (psi^bitrev), inverse table holds
+// psi^-bitrev.
+struct ModDev {
+    u64 q, twoq;
+    u64 r64, r64s;     // 2^64 mod q, Shoup companion
+    u64 one_s;         // floor(2^64 / q): Shoup companion of 1
+    u64 ninv, ninvs;   // N^-1 mod q
+    const u64 *fw, *fws, *iw, *iws;
+};
+
+// A CRT basis {m_i}: M = prod m_i, hat_i = M / m_i, inv_i = hat_i^-1 mod m_i.
+struct CrtDev {
+    int n, W;                 // primes, words used by sums
+    u64 m[MAXP];
+    u64 inv[MAXP], invs[MAXP];
+    u64 hat[MAXP][MAXW];
+    u64 M[MAXW];
+    u64 Mhalf[MAXW];          // floor(M / 2)
+};
+
+// Everything the exact kernels need in one device block.
+struct ExactDev {
+    CrtDev Q;                 // coefficient modulus basis
+    CrtDev B;                 // auxiliary basis for the tensor product
+    // per aux prime b_j: Q mod b_j, floor(Q/2) mod b_j, Q^-1 mod b_j (+Shoup), t mod b_j (+Shoup)
+    u64 Q_b[MAXP], Qhalf_b[MAXP], Qinv_b[MAXP], Qinv_bs[MAXP], t_b[MAXP], t_bs[MAXP];
+    // per q_i: B mod q_i, floor(Q/2) mod q_i, t mod q_i (+Shoup), Delta mod q_i (+Shoup)
+    u64 B_q[MAXP], Qhalf_q[MAXP], t_q[MAXP], t_qs[MAXP], delta_q[MAXP], delta_qs[MAXP];
+    // decryption: floor(Q/2) mod t, Q^-1 mod t (+Shoup w.r.t. t), 2^64 mod t (+Shoup), floor(2^64/t)
+    u64 t, Qhalf_t, Qinv_t, Qinv_ts, r64_t, r64_ts, one_ts;
+};
+
+}  // namespace he
+
+struct he_ctx {
+    he_params P;
+    int N = 0, logN = 0, L = 0, K = 0;   // K auxiliary primes
+    int n_mods = 0;                       // L + K (+1 if the t modulus is available)
+    int t_mod = -1;                       // index of the t modulus in the table, -1 if PPMul unsupported
+    int ell = 0;
+    std::vector<u64> q, aux;
+    // device tables
+    he::ModDev *d_mods = nullptr;       // [n_mods]
+    he::ExactDev *d_exact = nullptr;
+    std::vector<void *> allocs;          // twiddle tables etc.
+    // host copies
+    std::vector<he::ModDev> h_mods;
+    he::ExactDev h_exact;
+    // workspace
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    // small host->device tables cached by content
+    std::unordered_map<std::string, void *> table_cache;
+    std::string err;
+    // launch tracing
+    bool trace = false;
+    struct TraceRec { const char *name; cudaEvent_t a, b; double bytes, modmuls; };
+    std::vector<TraceRec> trace_recs;
+};
+
+struct he_keys {
+    int L = 0, ell = 0, N = 0;
+    u64 *sk = nullptr;       // int64 [N] (stored in u64 words)
+    u64 *s_ntt = nullptr;    // [L][N] NTT form
+    u64 *pk = nullptr;       // [2][L][N] coefficient form
+    u64 *pk_ntt = nullptr;   // [2][L][N]
+    u64 *rlk = nullptr;      // [ell][2][L][N] coefficient form (or null)
+    u64 *rlk_ntt = nullptr;  // [ell][2][L][N]
+};
+
+struct he_plan {
+    he_conv_shape s;
+    he_plan_info info;
+    int N = 0;
+    // tiles: a0,a1,b0,b1,r0,r1,s0,s1 per tile
+    std::vector<int> tiles;
+    // device index maps
+    int32_t *in_map = nullptr;   // [T*G][N] -> index into one image [C][H][W], -1 = zero
+    int32_t *ker_map = nullptr;  // [G][N]   -> index into w[m] ([C][h][h]), -1 = zero
+    int32_t *out_map = nullptr;  // [Ho*Wo]  -> t*N + coefficient
+    // host copies for tests of the plan
+    std::vector<int32_t> h_in_map, h_ker_map, h_out_map;
+};
+
+namespace he {
+
+// launch tracing: bracket a launch with events when the context traces
+struct TraceScope {
+    he_ctx *c;
+    cudaStream_t st;
+    int idx = -1;
+    TraceScope(he_ctx *c, cudaStream_t st, const char *name, double bytes, double modmuls);
+    ~TraceScope();
+};
+
+// host helpers (capi.cu / params.cpp / plan.cpp)
+int fail(he_ctx *c, int code, const std::string &msg);
+int cuda_check(he_ctx *c, cudaError_t e, const char *what);
+int build_tables(he_ctx *c, std::string &err);
+int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std::string &err);
+
+// ---------------------------------------------------------------- launchers
+// Forward NTT of n_polys polynomials over n_limbs consecutive moduli starting
+// at mod_base.  Source kinds:
+enum SrcKind {
+    SRC_RNS = 0,     // u64 residues: src + p*src_stride + limb*N (limbs < split), src2 for limbs >= split
+    SRC_T_LIFT = 1,  // u64 values in [0,t) (>= t reduced), centred lift: src + p*src_stride
+    SRC_I8 = 2,      // int8 small signed values: src + p*src_stride
+    SRC_U32 = 3,     // uint32 small unsigned values (< every modulus): src + p*src_stride
+    SRC_T_RAW = 4,   // u64 values taken mod the modulus (used for the t modulus)
+};
+struct FwdJob {
+    const void *src;
+    const void *src2;       // second source for limbs >= split (SRC_RNS only)
+    long long src_stride;   // elements between polynomials
+    long long src2_stride;
+    int split;              // limbs < split read from src
+    int kind;
+    u64 t;                  // for SRC_T_LIFT
+    u64 *dst;               // NTT form [p][n_limbs][N] with dst_stride elements between polys
+    long long dst_stride;
+    int n_polys, n_limbs, mod_base;
+};
+int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st);
+
+// Fused multiply-accumulate in the NTT domain followed by the inverse NTT and
+// an epilogue.  Output o, limb l:
+//   v = INTT( sum_{k in [ptr[o], ptr[o+1])} A[(ta[k]+l)*N ...] * B[(tb[k]+l)*N ...] )
+// Epilogue (natural order, coefficient x):
+//   r = v (+ add[o*add_stride + l*N + x]) (+ err8[o*err_stride + x])
+//       (+ delta_l * msg[o*msg_stride + x] mod t) (+ g_l * s2[l*N + x]),
+//   negated first if `negate` (r = -(v + err) + ...).
+struct MacJob {
+    const u64 *A, *B;
+    const int32_t *ptr, *ta, *tb;
+    u64 *out;
+    long long out_stride;
+    const u64 *add;
+    long long add_stride;
+    const int8_t *err;          // small error added (after negation rule)
+    long long err_stride;
+    const u64 *msg;             // plaintext, Delta * msg added to outputs o with o % msg_div == 0
+    long long msg_stride;       // message index o / msg_div
+    int msg_div;
+    const ExactDev *E;          // Delta and t for msg
+    const u64 *s2;              // s^2 coefficient form [L][N] times gmul (relin keys)
+    const u64 *gmul;            // [n_limbs] multipliers for s2 (device)
+    int negate;
+    int n_out, n_limbs, mod_base;
+    // for tracing: distinct A and B polynomials referenced, total terms
+    int n_dist_a, n_dist_b, n_terms;
+};
+int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st);
+
+// sampling (ChaCha20 streams): kinds
+enum SampleKind { SAMPLE_TERNARY = 0, SAMPLE_CBD = 1, SAMPLE_UNIFORM_Q = 2, SAMPLE_UNIFORM_T = 3 };
+// n_obj objects, object k uses stream (seed, tag, idx0 + k, limb); for
+// SAMPLE_UNIFORM_Q every object has n_limbs limbs (limb field = limb index),
+// output u64 [k][limb][N]; ternary / CBD output int8 [k][N]; uniform t u64 [k][N].
+int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_obj, int n_limbs,
+                  void *out, cudaStream_t st);
+
+int launch_base_extend(he_ctx *c, const u64 *src, long long n_polys, u64 *dst_aux, cudaStream_t st);
+int launch_scale_round(he_ctx *c, const u64 *d, int n_out, u64 *dq, uint32_t *digits, cudaStream_t st);
+int launch_decrypt_exact(he_ctx *c, const u64 *x, int n, u64 *m, cudaStream_t st);
+int launch_encode(he_ctx *c, const int32_t *map, int n_polys, int map_polys, const void *tensor, int dtype,
+                  long long tensor_stride, int batch, long long out_batch_polys, u64 *out, cudaStream_t st);
+int launch_encode_kernel(he_ctx *c, const int32_t *map, int G, int M, const void *tensor, int dtype,
+                         long long per_m, u64 *out, cudaStream_t st);
+int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int T, int batch, const u64 *pt, const u64 *sub,
+                  int64_t *out, cudaStream_t st);
+int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, cudaStream_t st);
+int launch_copy_sk(he_ctx *c, const int8_t *s8, u64 *sk, cudaStream_t st);
+
+}  // namespace he

@@ -1,0 +1,332 @@
+// params.cpp -- host-side parameter generation for a context: limb primes,
+// auxiliary primes of the tensor-product basis, NTT twiddle tables, and the
+// CRT / rescaling constants used by the exact kernels.  Runs once per
+// he_setup; everything it computes is uploaded to the device.
+#include <cstring>
+#include <algorithm>
+
+#include "internal.h"
+
+namespace he {
+
+typedef unsigned __int128 u128;
+
+static u64 mulmod(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+static u64 powmod(u64 a, u64 e, u64 m) {
+    u64 r = 1 % m;
+    a %= m;
+    while (e) {
+        if (e & 1) r = mulmod(r, a, m);
+        a = mulmod(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+// modular inverse by the extended Euclidean algorithm; 0 if none
+static u64 invmod(u64 a, u64 m) {
+    __int128 t = 0, nt = 1, r = m, nr = a % m;
+    while (nr) {
+        __int128 qq = r / nr, tmp;
+        tmp = t - qq * nt; t = nt; nt = tmp;
+        tmp = r - qq * nr; r = nr; nr = tmp;
+    }
+    if (r != 1) return 0;
+    if (t < 0) t += m;
+    return (u64)t;
+}
+// strong probable-prime test to the first 12 prime bases: deterministic for
+// all 64-bit inputs
+static bool is_prime(u64 n) {
+    if (n < 2) return false;
+    static const u64 small[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (u64 p : small) {
+        if (n % p == 0) return n == p;
+    }
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) { d >>= 1; s++; }
+    for (u64 a : small) {
+        u64 x = powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int r = 1; r < s && witness; r++) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+static u64 shoup_c(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+// ---------------------------------------------------------------- multi-word
+struct Big {
+    std::vector<u64> w;  // little endian
+    static Big of(u64 v) { Big b; b.w.push_back(v); return b; }
+    void trim() { while (w.size() > 1 && w.back() == 0) w.pop_back(); }
+    Big mul(u64 m) const {
+        Big r;
+        u64 carry = 0;
+        for (u64 x : w) {
+            u128 p = (u128)x * m + carry;
+            r.w.push_back((u64)p);
+            carry = (u64)(p >> 64);
+        }
+        r.w.push_back(carry);
+        r.trim();
+        return r;
+    }
+    // quotient by a single word, remainder in *rem
+    Big div(u64 d, u64 *rem) const {
+        Big r;
+        r.w.assign(w.size(), 0);
+        u128 cur = 0;
+        for (size_t i = w.size(); i-- > 0;) {
+            cur = (cur << 64) | w[i];
+            r.w[i] = (u64)(cur / d);
+            cur %= d;
+        }
+        if (rem) *rem = (u64)cur;
+        r.trim();
+        return r;
+    }
+    u64 mod(u64 d) const { u64 r; div(d, &r); return r; }
+    Big shr1() const {
+        Big r = *this;
+        for (size_t i = 0; i < r.w.size(); i++) {
+            r.w[i] >>= 1;
+            if (i + 1 < r.w.size()) r.w[i] |= r.w[i + 1] << 63;
+        }
+        r.trim();
+        return r;
+    }
+    int bits() const {
+        for (size_t i = w.size(); i-- > 0;)
+            if (w[i]) return (int)(64 * i) + 64 - __builtin_clzll(w[i]);
+        return 0;
+    }
+};
+
+static Big product(const std::vector<u64> &m) {
+    Big b = Big::of(1);
+    for (u64 x : m) b = b.mul(x);
+    return b;
+}
+
+static bool fill_crt(CrtDev &C, const std::vector<u64> &m, std::string &err) {
+    if ((int)m.size() > MAXP) { err = "too many primes in one CRT basis"; return false; }
+    memset(&C, 0, sizeof C);
+    C.n = (int)m.size();
+    Big M = product(m);
+    int nb = 0;
+    while ((1 << nb) < C.n) nb++;
+    C.W = (M.bits() + nb + 63) / 64;
+    if (C.W < 1) C.W = 1;
+    if (C.W > MAXW) { err = "modulus too large"; return false; }
+    for (int i = 0; i < C.n; i++) {
+        C.m[i] = m[i];
+        u64 r;
+        Big hat = M.div(m[i], &r);
+        for (size_t k = 0; k < hat.w.size() && (int)k < MAXW; k++) C.hat[i][k] = hat.w[k];
+        C.inv[i] = invmod(hat.mod(m[i]), m[i]);
+        C.invs[i] = shoup_c(C.inv[i], m[i]);
+    }
+    for (size_t k = 0; k < M.w.size() && (int)k < MAXW; k++) C.M[k] = M.w[k];
+    Big h = M.shr1();
+    for (size_t k = 0; k < h.w.size() && (int)k < MAXW; k++) C.Mhalf[k] = h.w[k];
+    return true;
+}
+
+static int bitrev(int x, int n) {
+    int r = 0;
+    for (int i = 0; i < n; i++) r |= ((x >> i) & 1) << (n - 1 - i);
+    return r;
+}
+
+// a primitive 2N-th root of unity mod q (q prime, q = 1 mod 2N)
+static u64 root_2n(u64 q, int N) {
+    for (u64 g = 2; g < 1000000; g++) {
+        u64 psi = powmod(g, (q - 1) / (2 * (u64)N), q);
+        if (powmod(psi, (u64)N, q) == q - 1) return psi;
+    }
+    return 0;
+}
+
+static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
+    const int N = c->N, logN = c->logN;
+    u64 psi = root_2n(q, N);
+    if (!psi) { err = "no primitive 2N-th root"; return false; }
+    u64 psiinv = invmod(psi, q);
+    std::vector<u64> tab(4 * (size_t)N);
+    u64 *fw = tab.data(), *fws = fw + N, *iw = fws + N, *iws = iw + N;
+    // powers psi^e for e in [0, N)
+    std::vector<u64> pw(N), ipw(N);
+    pw[0] = ipw[0] = 1;
+    for (int e = 1; e < N; e++) { pw[e] = mulmod(pw[e - 1], psi, q); ipw[e] = mulmod(ipw[e - 1], psiinv, q); }
+    for (int k = 0; k < N; k++) {
+        int e = bitrev(k, logN);
+        fw[k] = pw[e]; fws[k] = shoup_c(fw[k], q);
+        iw[k] = ipw[e]; iws[k] = shoup_c(iw[k], q);
+    }
+    void *d = nullptr;
+    if (cudaMalloc(&d, tab.size() * 8) != cudaSuccess) { err = "cudaMalloc twiddles"; return false; }
+    c->allocs.push_back(d);
+    if (cudaMemcpy(d, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) { err = "upload twiddles"; return false; }
+    ModDev M;
+    memset(&M, 0, sizeof M);
+    M.q = q;
+    M.twoq = 2 * q;
+    M.r64 = (u64)(((u128)1 << 64) % q);
+    M.r64s = shoup_c(M.r64, q);
+    M.one_s = (u64)(((u128)1 << 64) / q);
+    M.ninv = invmod((u64)N, q);
+    M.ninvs = shoup_c(M.ninv, q);
+    M.fw = (const u64 *)d;
+    M.fws = M.fw + N;
+    M.iw = M.fws + N;
+    M.iws = M.iw + N;
+    c->h_mods.push_back(M);
+    return true;
+}
+
+// largest unused prime below 2^bits with p = 1 mod 2N
+static u64 next_prime_below(int bits, int N, const std::vector<u64> &used) {
+    const u64 step = 2 * (u64)N;
+    u64 p = (((u64)1 << bits) - 2) / step * step + 1;
+    for (; p > step; p -= step) {
+        if (std::find(used.begin(), used.end(), p) != used.end()) continue;
+        if (is_prime(p)) return p;
+    }
+    return 0;
+}
+
+int build_tables(he_ctx *c, std::string &err) {
+    he_params &P = c->P;
+    const int N = P.N;
+    if (N < 1024 || N > 16384 || (N & (N - 1))) { err = "N must be a power of two in [1024, 16384]"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    if (P.L < 1 || P.L > HE_MAX_LIMBS) { err = "L out of range"; return HE_ERR_INVALID_ARG; }
+    if (P.t < 2 || P.t >= ((u64)1 << 61)) { err = "t out of range"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    if (P.base_log2 == 0) P.base_log2 = 16;
+    if (P.eta == 0) P.eta = 21;
+    if (P.max_ccmul_group == 0) P.max_ccmul_group = 64;
+    if (P.base_log2 < 1 || P.base_log2 > 32) { err = "base_log2 out of range"; return HE_ERR_INVALID_ARG; }
+    if (P.eta < 1 || P.eta > 32) { err = "eta out of range"; return HE_ERR_INVALID_ARG; }
+    if (P.max_ccmul_group < 1) { err = "max_ccmul_group out of range"; return HE_ERR_INVALID_ARG; }
+    c->N = N;
+    c->logN = 0;
+    while ((1 << c->logN) < N) c->logN++;
+    c->L = P.L;
+    // limb primes
+    c->q.clear();
+    const bool explicit_q = P.q[0] != 0;
+    for (int i = 0; i < P.L; i++) {
+        u64 q = explicit_q ? P.q[i] : 0;
+        if (explicit_q) {
+            if (!is_prime(q) || q % (2 * (u64)N) != 1 || q >= ((u64)1 << 61) ||
+                std::find(c->q.begin(), c->q.end(), q) != c->q.end()) {
+                err = "explicit q must be distinct primes < 2^61 with q = 1 mod 2N";
+                return HE_ERR_UNSUPPORTED_PARAMS;
+            }
+        } else {
+            if (P.prime_bits[i] < 20 || P.prime_bits[i] > 61) { err = "prime_bits out of [20, 61]"; return HE_ERR_UNSUPPORTED_PARAMS; }
+            q = next_prime_below(P.prime_bits[i], N, c->q);
+            if (!q) { err = "no prime of that size"; return HE_ERR_UNSUPPORTED_PARAMS; }
+        }
+        c->q.push_back(q);
+        P.q[i] = q;
+    }
+    for (u64 q : c->q)
+        if (std::__gcd(q, (u64)P.t) != 1) { err = "t must be coprime to q"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    Big Q = product(c->q);
+    c->ell = (Q.bits() + P.base_log2 - 1) / P.base_log2;
+    // auxiliary basis: 61-bit primes until B > group * N * t * Q * 2
+    int gbits = 0;
+    while ((1LL << gbits) < P.max_ccmul_group) gbits++;
+    const int need = gbits + c->logN + Big::of(P.t).bits() + Q.bits() + 1;
+    std::vector<u64> used = c->q;
+    c->aux.clear();
+    while (true) {
+        Big B = product(c->aux);
+        if (!c->aux.empty() && B.bits() - 1 >= need) break;
+        u64 p = next_prime_below(61, N, used);
+        if (!p) { err = "aux primes exhausted"; return HE_ERR_UNSUPPORTED_PARAMS; }
+        used.push_back(p);
+        c->aux.push_back(p);
+        if ((int)c->aux.size() > 24) { err = "aux basis too large"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    }
+    if (std::find(c->q.begin(), c->q.end(), P.t) != c->q.end()) { err = "t equals a limb prime"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    c->K = (int)c->aux.size();
+    c->h_mods.clear();
+    for (u64 q : c->q)
+        if (!add_modulus(c, q, err)) return HE_ERR_CUDA;
+    for (u64 q : c->aux)
+        if (!add_modulus(c, q, err)) return HE_ERR_CUDA;
+    c->t_mod = -1;
+    if (is_prime(P.t) && P.t % (2 * (u64)N) == 1) {
+        if (!add_modulus(c, P.t, err)) return HE_ERR_CUDA;
+        c->t_mod = c->L + c->K;
+    }
+    c->n_mods = (int)c->h_mods.size();
+    if (c->n_mods > MAX_MODS) { err = "too many moduli"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    // exact-kernel constants
+    ExactDev &E = c->h_exact;
+    memset(&E, 0, sizeof E);
+    if (!fill_crt(E.Q, c->q, err) || !fill_crt(E.B, c->aux, err)) return HE_ERR_UNSUPPORTED_PARAMS;
+    Big Qh = Q.shr1();
+    Big Bp = product(c->aux);
+    const u64 t = P.t;
+    u64 rem;
+    Big delta = Q.div(t, &rem);
+    for (int j = 0; j < c->K; j++) {
+        const u64 b = c->aux[j];
+        E.Q_b[j] = Q.mod(b);
+        E.Qhalf_b[j] = Qh.mod(b);
+        E.Qinv_b[j] = invmod(E.Q_b[j], b);
+        E.Qinv_bs[j] = shoup_c(E.Qinv_b[j], b);
+        E.t_b[j] = t % b;
+        E.t_bs[j] = shoup_c(E.t_b[j], b);
+    }
+    for (int i = 0; i < c->L; i++) {
+        const u64 q = c->q[i];
+        E.B_q[i] = Bp.mod(q);
+        E.Qhalf_q[i] = Qh.mod(q);
+        E.t_q[i] = t % q;
+        E.t_qs[i] = shoup_c(E.t_q[i], q);
+        E.delta_q[i] = delta.mod(q);
+        E.delta_qs[i] = shoup_c(E.delta_q[i], q);
+    }
+    E.t = t;
+    E.Qhalf_t = Qh.mod(t);
+    E.Qinv_t = invmod(Q.mod(t), t);
+    if (!E.Qinv_t && t > 1) { err = "q not invertible mod t"; return HE_ERR_UNSUPPORTED_PARAMS; }
+    E.Qinv_ts = shoup_c(E.Qinv_t, t);
+    E.r64_t = (u64)(((u128)1 << 64) % t);
+    E.r64_ts = shoup_c(E.r64_t, t);
+    E.one_ts = (u64)(((u128)1 << 64) / t);
+    // upload
+    if (cudaMalloc((void **)&c->d_mods, sizeof(ModDev) * c->n_mods) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_exact, sizeof(ExactDev)) != cudaSuccess) {
+        err = "cudaMalloc tables";
+        return HE_ERR_OOM;
+    }
+    if (cudaMemcpy(c->d_mods, c->h_mods.data(), sizeof(ModDev) * c->n_mods, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_exact, &E, sizeof(ExactDev), cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "upload tables";
+        return HE_ERR_CUDA;
+    }
+    return HE_OK;
+}
+
+// 2^(base*j) mod q_i with Shoup companions, [ell][L][2]
+std::vector<u64> relin_multipliers(const he_ctx *c) {
+    std::vector<u64> g((size_t)c->ell * c->L * 2);
+    for (int j = 0; j < c->ell; j++)
+        for (int i = 0; i < c->L; i++) {
+            u64 v = powmod(2, (u64)c->P.base_log2 * (u64)j, c->q[i]);
+            g[((size_t)j * c->L + i) * 2] = v;
+            g[((size_t)j * c->L + i) * 2 + 1] = shoup_c(v, c->q[i]);
+        }
+    return g;
+}
+
+}  // namespace he

@@ -1,0 +1,220 @@
+// plan.cpp -- window search and index maps for the two convolution packings
+// of Section 3.3.
+//
+// Conventional (row-major, the packing the paper builds on; left half of
+// Fig. 7): the input is zero-padded to H' x W' and cut into square windows of
+// side s (clipped to the padded image) holding C_n channels at stride H_n W_n;
+// the kernel is stored reversed at offset O = (C_n-1) H_n W_n + (h-1) W_n + h-1
+// and output (a, b) of a window is coefficient O + a W_n + b.
+//
+// Correlated (Eq. 1 and Eq. 2): per channel x^[i O + j] = x[i, j] and
+// w^[(h-1-k) O + (h-1-l)] = w[k, l] with O = max(W_w, H_w) + h - 1 over the
+// unpadded window; C_n channels are placed at stride S (kernel channels in
+// reverse order) where S is the smallest stride that keeps cross-channel terms
+// off the requested outputs; C_n is the largest count for which the requested
+// outputs stay below N and no wrapped (x^N = -1) term lands on them.
+//
+// Window choice: minimise the number of input polynomials per image G*T
+// (= polynomial products per output channel), then G, then prefer the larger
+// window.  The paper's objective is printed with floors and W_w + h - 1 in a
+// denominator; this is the reading used everywhere in the library.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "internal.h"
+
+namespace he {
+
+struct Tile { int a0, a1, b0, b1, r0, r1, s0, s1; };
+
+static bool conv_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
+    const int Hp = s.H + 2 * s.pad, Wp = s.W + 2 * s.pad;
+    const int Ho = Hp - s.h + 1, Wo = Wp - s.h + 1;
+    long long best[4] = {LLONG_MAX, 0, 0, 0};
+    bool found = false;
+    for (int G = 1; G <= s.C; G++) {
+        const int Cn = (s.C + G - 1) / G;
+        if ((s.C + Cn - 1) / Cn != G) continue;
+        for (int side = s.h; side <= std::max(Hp, Wp); side++) {
+            const int Hn = std::min(side, Hp), Wn = std::min(side, Wp);
+            if ((long long)Cn * Hn * Wn > N) continue;
+            const int th = Hn - s.h + 1, tw = Wn - s.h + 1;
+            const int Th = (Ho + th - 1) / th, Tw = (Wo + tw - 1) / tw;
+            long long key[4] = {(long long)G * Th * Tw, G, -Hn, -Wn};
+            if (!found || std::lexicographical_compare(key, key + 4, best, best + 4)) {
+                std::copy(key, key + 4, best);
+                found = true;
+                I.Cn = Cn; I.G = G; I.Hn = Hn; I.Wn = Wn; I.th = th; I.tw = tw; I.Th = Th; I.Tw = Tw;
+            }
+        }
+    }
+    if (!found) return false;
+    I.T = I.Th * I.Tw;
+    I.Ooff = (I.Cn - 1) * I.Hn * I.Wn + (s.h - 1) * I.Wn + s.h - 1;
+    tiles.clear();
+    for (int ti = 0; ti < I.Th; ti++)
+        for (int tj = 0; tj < I.Tw; tj++) {
+            const int a0 = ti * I.th, b0 = tj * I.tw;
+            tiles.push_back({a0, std::min(Ho, a0 + I.th), b0, std::min(Wo, b0 + I.tw), a0, a0 + I.Hn, b0, b0 + I.Wn});
+        }
+    return true;
+}
+
+static void corr_tiles(const he_conv_shape &s, int th, int tw, std::vector<Tile> &tiles) {
+    const int Ho = s.H + 2 * s.pad - s.h + 1, Wo = s.W + 2 * s.pad - s.h + 1;
+    tiles.clear();
+    for (int a0 = 0; a0 < Ho; a0 += th)
+        for (int b0 = 0; b0 < Wo; b0 += tw) {
+            const int a1 = std::min(Ho, a0 + th), b1 = std::min(Wo, b0 + tw);
+            tiles.push_back({a0, a1, b0, b1, std::max(0, a0 - s.pad), std::min(s.H, a1 - s.pad + s.h - 1),
+                             std::max(0, b0 - s.pad), std::min(s.W, b1 - s.pad + s.h - 1)});
+        }
+}
+
+struct Geo { long long rlo, rhi, D1; };
+
+static void corr_geometry(const he_conv_shape &s, const std::vector<Tile> &tiles, long long &O, long long &S,
+                          std::vector<Geo> &g) {
+    int Hm = 0, Wm = 0;
+    for (const Tile &t : tiles) { Hm = std::max(Hm, t.r1 - t.r0); Wm = std::max(Wm, t.s1 - t.s0); }
+    O = std::max(Hm, Wm) + s.h - 1;
+    g.clear();
+    S = 0;
+    for (const Tile &t : tiles) {
+        const long long ulo = t.a0 - s.pad - t.r0 + s.h - 1, uhi = t.a1 - 1 - s.pad - t.r0 + s.h - 1;
+        const long long vlo = t.b0 - s.pad - t.s0 + s.h - 1, vhi = t.b1 - 1 - s.pad - t.s0 + s.h - 1;
+        Geo e{ulo * O + vlo, uhi * O + vhi, (long long)(t.r1 - t.r0 + s.h - 2) * O + (t.s1 - t.s0 + s.h - 2)};
+        S = std::max(S, std::max(e.rhi, e.D1 - e.rlo));
+        g.push_back(e);
+    }
+    S += 1;
+}
+
+static bool corr_fits(long long c, long long S, const std::vector<Geo> &g, long long N) {
+    for (const Geo &e : g) {
+        if ((c - 1) * S + e.rhi >= N) return false;
+        const long long D = 2 * (c - 1) * S + e.D1;
+        if (!(D < N || D - N < (c - 1) * S + e.rlo)) return false;
+    }
+    return true;
+}
+
+static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
+    const int Ho = s.H + 2 * s.pad - s.h + 1, Wo = s.W + 2 * s.pad - s.h + 1;
+    long long best[4] = {LLONG_MAX, 0, 0, 0};
+    bool found = false;
+    std::vector<Tile> tl;
+    std::vector<Geo> g;
+    for (int th = 1; th <= Ho; th++)
+        for (int tw = 1; tw <= Wo; tw++) {
+            corr_tiles(s, th, tw, tl);
+            long long O, S;
+            corr_geometry(s, tl, O, S, g);
+            if (!corr_fits(1, S, g, N)) continue;
+            int cmax = 1;
+            while (cmax < s.C && corr_fits(cmax + 1, S, g, N)) cmax++;
+            const int G = (s.C + cmax - 1) / cmax;
+            const int Cn = (s.C + G - 1) / G;
+            long long key[4] = {(long long)G * (long long)tl.size(), G, -th, -tw};
+            if (!found || std::lexicographical_compare(key, key + 4, best, best + 4)) {
+                std::copy(key, key + 4, best);
+                found = true;
+                I.Cn = Cn; I.G = G; I.th = th; I.tw = tw; I.O = (int)O; I.S = (int)S;
+                I.Th = (Ho + th - 1) / th; I.Tw = (Wo + tw - 1) / tw;
+                tiles = tl;
+            }
+        }
+    if (!found) return false;
+    I.T = I.Th * I.Tw;
+    return true;
+}
+
+int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std::string &err) {
+    if (s.C < 1 || s.H < 1 || s.W < 1 || s.M < 1 || s.h < 1 || s.pad < 0 || s.pad > s.h - 1 ||
+        s.H + 2 * s.pad - s.h + 1 < 1 || s.W + 2 * s.pad - s.h + 1 < 1) {
+        err = "bad convolution shape";
+        return HE_ERR_INVALID_ARG;
+    }
+    if (encoding != HE_ENC_CONVENTIONAL && encoding != HE_ENC_CORRELATED) { err = "bad encoding"; return HE_ERR_INVALID_ARG; }
+    const int N = c->N;
+    he_plan_info I;
+    memset(&I, 0, sizeof I);
+    I.encoding = encoding;
+    I.Ho = s.H + 2 * s.pad - s.h + 1;
+    I.Wo = s.W + 2 * s.pad - s.h + 1;
+    std::vector<Tile> tiles;
+    const bool ok = encoding == HE_ENC_CONVENTIONAL ? conv_search(N, s, I, tiles) : corr_search(N, s, I, tiles);
+    if (!ok) { err = "no partition window fits the ring"; return HE_ERR_PLAN_DOES_NOT_FIT; }
+    p->s = s;
+    p->info = I;
+    p->N = N;
+    p->tiles.clear();
+    for (const Tile &t : tiles) {
+        int v[8] = {t.a0, t.a1, t.b0, t.b1, t.r0, t.r1, t.s0, t.s1};
+        p->tiles.insert(p->tiles.end(), v, v + 8);
+    }
+    // index maps
+    const int T = I.T, G = I.G, Cn = I.Cn;
+    p->h_in_map.assign((size_t)T * G * N, -1);
+    p->h_ker_map.assign((size_t)G * N, -1);
+    p->h_out_map.assign((size_t)I.Ho * I.Wo, -1);
+    for (int ti = 0; ti < T; ti++) {
+        const Tile &t = tiles[ti];
+        for (int g = 0; g < G; g++) {
+            int32_t *m = p->h_in_map.data() + ((size_t)ti * G + g) * N;
+            for (int cl = 0; cl < Cn; cl++) {
+                const int ch = g * Cn + cl;
+                if (ch >= s.C) break;
+                if (encoding == HE_ENC_CONVENTIONAL) {
+                    for (int i = 0; i < I.Hn; i++)
+                        for (int j = 0; j < I.Wn; j++) {
+                            const int r = t.r0 + i - s.pad, q = t.s0 + j - s.pad;
+                            if (r >= 0 && r < s.H && q >= 0 && q < s.W)
+                                m[cl * I.Hn * I.Wn + i * I.Wn + j] = (ch * s.H + r) * s.W + q;
+                        }
+                } else {
+                    for (int i = t.r0; i < t.r1; i++)
+                        for (int j = t.s0; j < t.s1; j++)
+                            m[(long long)cl * I.S + (long long)(i - t.r0) * I.O + (j - t.s0)] = (ch * s.H + i) * s.W + j;
+                }
+            }
+        }
+        for (int a = t.a0; a < t.a1; a++)
+            for (int b = t.b0; b < t.b1; b++) {
+                long long coef;
+                if (encoding == HE_ENC_CONVENTIONAL) coef = I.Ooff + (long long)(a - t.a0) * I.Wn + (b - t.b0);
+                else {
+                    const long long u = a - s.pad - t.r0 + s.h - 1, v = b - s.pad - t.s0 + s.h - 1;
+                    coef = (long long)(Cn - 1) * I.S + u * I.O + v;
+                }
+                p->h_out_map[(size_t)a * I.Wo + b] = (int32_t)(ti * N + coef);
+            }
+    }
+    for (int g = 0; g < G; g++) {
+        int32_t *m = p->h_ker_map.data() + (size_t)g * N;
+        for (int cl = 0; cl < Cn; cl++) {
+            const int ch = g * Cn + cl;
+            if (ch >= s.C) break;
+            for (int k = 0; k < s.h; k++)
+                for (int l = 0; l < s.h; l++) {
+                    long long coef = encoding == HE_ENC_CONVENTIONAL
+                        ? (long long)I.Ooff - (long long)cl * I.Hn * I.Wn - (long long)k * I.Wn - l
+                        : (long long)(Cn - 1 - cl) * I.S + (long long)(s.h - 1 - k) * I.O + (s.h - 1 - l);
+                    m[coef] = (ch * s.h + k) * s.h + l;
+                }
+        }
+    }
+    // upload
+    auto up = [&](const std::vector<int32_t> &h, int32_t **d) -> bool {
+        if (cudaMalloc((void **)d, h.size() * 4) != cudaSuccess) return false;
+        return cudaMemcpy(*d, h.data(), h.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up(p->h_in_map, &p->in_map) || !up(p->h_ker_map, &p->ker_map) || !up(p->h_out_map, &p->out_map)) {
+        err = "upload plan maps";
+        return HE_ERR_OOM;
+    }
+    return HE_OK;
+}
+
+}  // namespace he

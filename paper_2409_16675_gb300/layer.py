@@ -1,0 +1,160 @@
+"""CryptoTrain-P homomorphic linear layer on the GPU, composed from the C ABI.
+
+Section 3.2: offline, [r^x r^w] is computed by CCMul with relinearisation;
+online, c = [x](w - r^w) + [w](x - r^x) + [r^x r^w] (two CPMuls and CCAdds in
+one fused launch), p = (x - r^x)(w - r^w) (PPMul), and the client recovers
+Dec(c) - p = x w, decoded to the convolution output.  Every step is a call
+into libcryptotrain.so; this module only allocates buffers and sequences the
+calls.
+
+Batch convention: a batch of B images shares the weights and their mask r^w;
+every random object of one kind is drawn from one seed with object index equal
+to its position in the flattened batch.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import native as nv
+from .workloads import RingSpec, ConvShape, ProtocolSeeds
+
+ENC = {"conv": nv.HE_ENC_CONVENTIONAL, "corr": nv.HE_ENC_CORRELATED}
+
+
+class Context:
+    """A he_ctx for one ring."""
+
+    def __init__(self, spec: RingSpec, device: int = 0, max_ccmul_group: int = 64):
+        self.spec = spec
+        self.params = nv.make_params(spec.N, prime_bits=spec.prime_bits, t=spec.t, base_log2=spec.base_log2,
+                                     eta=spec.eta, max_ccmul_group=max_ccmul_group, device=device)
+        self.h = nv.he_setup(self.params)
+        self.info = nv.he_ctx_query(self.h)
+        self.N, self.L, self.t = spec.N, spec.L, spec.t
+        self.q = [self.info.q[i] for i in range(self.L)]
+        self.ell = self.info.ell
+        self.device = torch.device("cuda", device)
+
+    def close(self):
+        if self.h:
+            nv.he_ctx_destroy(self.h)
+            self.h = None
+
+    def u64(self, *shape):
+        return torch.empty(shape, dtype=torch.uint64, device=self.device)
+
+    def ct(self, n):
+        return self.u64(n, 2, self.L, self.N)
+
+
+class Keys:
+    def __init__(self, ctx: Context, seed: int, with_relin: bool = True):
+        self.ctx = ctx
+        self.h = nv.he_keygen(ctx.h, seed, with_relin)
+
+    def export(self, which):
+        c = self.ctx
+        shape = {nv.HE_KEY_SK: (c.N,), nv.HE_KEY_PK: (2, c.L, c.N), nv.HE_KEY_RLK: (c.ell, 2, c.L, c.N)}[which]
+        out = torch.empty(shape, dtype=torch.int64 if which == nv.HE_KEY_SK else torch.uint64, device=c.device)
+        nv.he_keys_export(c.h, self.h, which, out)
+        return out
+
+    def close(self):
+        if self.h:
+            nv.he_keys_destroy(self.h)
+            self.h = None
+
+
+class Plan:
+    def __init__(self, ctx: Context, shape: ConvShape, encoding: str):
+        self.ctx, self.shape, self.encoding = ctx, shape, encoding
+        self.h = nv.he_conv_plan(ctx.h, shape.C, shape.H, shape.W, shape.M, shape.h, shape.pad, ENC[encoding])
+        self.info = nv.he_plan_query(self.h)
+        self.T, self.G = self.info.T, self.info.G
+
+    def encode_input(self, x, batch, out):
+        f = nv.he_encode_conventional if self.encoding == "conv" else nv.he_encode_correlated
+        f(self.ctx.h, self.h, nv.HE_ROLE_INPUT, x, batch, out)
+
+    def encode_kernel(self, w, out):
+        f = nv.he_encode_conventional if self.encoding == "conv" else nv.he_encode_correlated
+        f(self.ctx.h, self.h, nv.HE_ROLE_KERNEL, w, 1, out)
+
+    def close(self):
+        if self.h:
+            nv.he_plan_destroy(self.h)
+            self.h = None
+
+
+@dataclass
+class LayerBuffers:
+    xp: torch.Tensor
+    wp: torch.Tensor
+    r_x: torch.Tensor
+    r_w: torch.Tensor
+    ct_x: torch.Tensor
+    ct_w: torch.Tensor
+    ct_rx: torch.Tensor
+    ct_rw: torch.Tensor
+    rr: torch.Tensor
+    xm: torch.Tensor
+    wm: torch.Tensor
+    out: torch.Tensor
+    p: torch.Tensor
+    dec: torch.Tensor
+    y: torch.Tensor
+
+
+class PLayer:
+    """One CryptoTrain-P linear layer over a batch of B images."""
+
+    def __init__(self, ctx: Context, keys: Keys, plan: Plan, batch: int):
+        self.ctx, self.keys, self.plan, self.B = ctx, keys, plan, batch
+        c, s = ctx, plan.shape
+        nx, nw, no = batch * plan.T * plan.G, s.M * plan.G, batch * s.M * plan.T
+        self.nx, self.nw, self.no = nx, nw, no
+        self.buf = LayerBuffers(
+            xp=c.u64(nx, c.N), wp=c.u64(nw, c.N), r_x=c.u64(nx, c.N), r_w=c.u64(nw, c.N),
+            ct_x=c.ct(nx), ct_w=c.ct(nw), ct_rx=c.ct(nx), ct_rw=c.ct(nw), rr=c.ct(no),
+            xm=c.u64(nx, c.N), wm=c.u64(nw, c.N), out=c.ct(no), p=c.u64(no, c.N), dec=c.u64(no, c.N),
+            y=torch.empty((batch, s.M, plan.info.Ho, plan.info.Wo), dtype=torch.int64, device=c.device))
+
+    def client_prepare(self, x, w, seeds: ProtocolSeeds):
+        """Client side: encode, draw masks, encrypt x, w and the masks."""
+        c, b = self.ctx, self.buf
+        self.plan.encode_input(x, self.B, b.xp)
+        self.plan.encode_kernel(w, b.wp)
+        nv.he_sample_masks(c.h, seeds.mask_x, self.nx, b.r_x)
+        nv.he_sample_masks(c.h, seeds.mask_w, self.nw, b.r_w)
+        nv.he_encrypt(c.h, self.keys.h, b.xp, self.nx, seeds.enc_x, b.ct_x)
+        nv.he_encrypt(c.h, self.keys.h, b.wp, self.nw, seeds.enc_w, b.ct_w)
+        nv.he_encrypt(c.h, self.keys.h, b.r_x, self.nx, seeds.enc_rx, b.ct_rx)
+        nv.he_encrypt(c.h, self.keys.h, b.r_w, self.nw, seeds.enc_rw, b.ct_rw)
+        nv.he_pt_sub(c.h, b.xp, b.r_x, self.nx * c.N, b.xm)
+        nv.he_pt_sub(c.h, b.wp, b.r_w, self.nw * c.N, b.wm)
+
+    def offline(self):
+        """Server, preprocessing: [r^x r^w] by CCMul + relinearisation."""
+        b = self.buf
+        nv.he_ccmul_conv_precompute(self.ctx.h, self.keys.h, self.plan.h, self.B, b.ct_rx, b.ct_rw, b.rr)
+
+    def online(self):
+        """Server, online: c = [x](w - r^w) + [w](x - r^x) + [r^x r^w]; p = PPMul."""
+        b, c = self.buf, self.ctx
+        nv.he_cpmul_conv(c.h, self.plan.h, self.B, b.ct_x, b.wm, b.ct_w, b.xm, b.rr, b.out)
+        nv.he_ppmul_conv(c.h, self.plan.h, self.B, b.xm, b.wm, b.p)
+
+    def client_finish(self):
+        """Client: Dec(c) - p, decoded to [B, M, Ho, Wo]."""
+        b, c = self.buf, self.ctx
+        nv.he_decrypt(c.h, self.keys.h, b.out, self.no, b.dec)
+        nv.he_decode(c.h, self.plan.h, self.B, b.dec, b.p, b.y)
+        return b.y
+
+    def step(self, x, w, seeds: ProtocolSeeds):
+        self.client_prepare(x, w, seeds)
+        self.offline()
+        self.online()
+        return self.client_finish()

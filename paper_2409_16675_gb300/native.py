@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in include/cryptotrain.h.
+
+Argument marshalling only: every function has the name of its C entry point,
+takes PyTorch CUDA tensors (or None for NULL), passes their device pointers
+and the current CUDA stream, and raises HEError on a negative status.  All
+computation happens in libcryptotrain.so; there is no fallback of any kind:
+importing this module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcryptotrain.so")
+
+HE_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_PARAMS", -3: "PLAN_DOES_NOT_FIT", -4: "OOM",
+          -5: "BUDGET_EXCEEDED", -6: "TIMEOUT", -7: "CUDA"}
+HE_MAX_LIMBS = 16
+HE_ENC_CONVENTIONAL, HE_ENC_CORRELATED = 0, 1
+HE_ROLE_INPUT, HE_ROLE_KERNEL = 0, 1
+HE_DTYPE_U8, HE_DTYPE_I8, HE_DTYPE_I64 = 0, 1, 2
+HE_KEY_SK, HE_KEY_PK, HE_KEY_RLK = 0, 1, 2
+
+
+class HEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class he_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int32), ("prime_bits", ctypes.c_int32 * HE_MAX_LIMBS),
+                ("q", ctypes.c_uint64 * HE_MAX_LIMBS), ("t", ctypes.c_uint64), ("base_log2", ctypes.c_int32),
+                ("eta", ctypes.c_int32), ("max_ccmul_group", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class he_ctx_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int32), ("q", ctypes.c_uint64 * HE_MAX_LIMBS),
+                ("t", ctypes.c_uint64), ("ell", ctypes.c_int32), ("n_aux", ctypes.c_int32),
+                ("aux", ctypes.c_uint64 * 24), ("ppmul_ok", ctypes.c_int32)]
+
+
+class he_conv_shape(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("C", "H", "W", "M", "h", "pad")]
+
+
+class he_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("modmuls", ctypes.c_double)]
+
+
+class he_plan_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("encoding", "Cn", "G", "th", "tw", "Th", "Tw", "T", "Hn", "Wn",
+                                              "Ooff", "O", "S", "Ho", "Wo")]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libcryptotrain.so is not built (run __graft_entry__.build()); "
+                          "there is no fallback implementation")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "he_setup": [ctypes.POINTER(he_params), pp],
+        "he_ctx_destroy": [vp],
+        "he_ctx_query": [vp, ctypes.POINTER(he_ctx_info)],
+        "he_last_error": [vp, ctypes.c_char_p, i32],
+        "he_keygen": [vp, u64, i32, pp, vp],
+        "he_keys_destroy": [vp],
+        "he_keys_export": [vp, vp, i32, vp, vp],
+        "he_encrypt": [vp, vp, vp, i32, u64, vp, vp],
+        "he_decrypt": [vp, vp, vp, i32, vp, vp],
+        "he_sample_masks": [vp, u64, i32, vp, vp],
+        "he_pt_sub": [vp, vp, vp, i64, vp, vp],
+        "he_conv_plan": [vp, ctypes.POINTER(he_conv_shape), i32, pp],
+        "he_plan_destroy": [vp],
+        "he_plan_query": [vp, ctypes.POINTER(he_plan_info)],
+        "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
+        "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
+        "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
+        "he_ccmul_precompute": [vp, vp, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp],
+        "he_ccmul_conv_precompute": [vp, vp, vp, i32, vp, vp, vp, vp],
+        "he_ppmul_conv": [vp, vp, i32, vp, vp, vp, vp],
+        "he_decode": [vp, vp, i32, vp, vp, vp, vp],
+        "he_trace_enable": [vp, i32],
+        "he_trace_read": [vp, ctypes.POINTER(he_trace_entry), i32, ctypes.POINTER(i32)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("device tensor expected")
+        if not t.is_contiguous():
+            raise ValueError("contiguous tensor expected")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def last_error(ctx=None) -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.he_last_error(ctx, buf, 512)
+    return buf.value.decode()
+
+
+def _check(rc, ctx=None):
+    if rc != HE_OK:
+        raise HEError(rc, last_error(ctx))
+
+
+def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=21, max_ccmul_group=64, device=0):
+    p = he_params()
+    p.N = N
+    if q:
+        p.L = len(q)
+        for i, v in enumerate(q):
+            p.q[i] = v
+    else:
+        p.L = len(prime_bits)
+        for i, b in enumerate(prime_bits):
+            p.prime_bits[i] = b
+    p.t, p.base_log2, p.eta, p.max_ccmul_group, p.device = t, base_log2, eta, max_ccmul_group, device
+    return p
+
+
+# ---------------------------------------------------------------- entry points
+def he_setup(params: he_params):
+    h = ctypes.c_void_p()
+    _check(lib.he_setup(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def he_ctx_destroy(ctx):
+    _check(lib.he_ctx_destroy(ctx))
+
+
+def he_ctx_query(ctx) -> he_ctx_info:
+    info = he_ctx_info()
+    _check(lib.he_ctx_query(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+def he_keygen(ctx, seed: int, with_relin: bool = True):
+    h = ctypes.c_void_p()
+    _check(lib.he_keygen(ctx, seed, int(with_relin), ctypes.byref(h), _stream()), ctx)
+    return h
+
+
+def he_keys_destroy(keys):
+    _check(lib.he_keys_destroy(keys))
+
+
+def he_keys_export(ctx, keys, which: int, dst: torch.Tensor):
+    _check(lib.he_keys_export(ctx, keys, which, _ptr(dst), _stream()), ctx)
+
+
+def he_encrypt(ctx, keys, pt: torch.Tensor, n: int, seed: int, ct: torch.Tensor):
+    _check(lib.he_encrypt(ctx, keys, _ptr(pt), n, seed, _ptr(ct), _stream()), ctx)
+
+
+def he_decrypt(ctx, keys, ct: torch.Tensor, n: int, pt: torch.Tensor):
+    _check(lib.he_decrypt(ctx, keys, _ptr(ct), n, _ptr(pt), _stream()), ctx)
+
+
+def he_sample_masks(ctx, seed: int, n: int, out: torch.Tensor):
+    _check(lib.he_sample_masks(ctx, seed, n, _ptr(out), _stream()), ctx)
+
+
+def he_pt_sub(ctx, a, b, n: int, out):
+    _check(lib.he_pt_sub(ctx, _ptr(a), _ptr(b), n, _ptr(out), _stream()), ctx)
+
+
+def he_conv_plan(ctx, C, H, W, M, h, pad, encoding):
+    s = he_conv_shape(C, H, W, M, h, pad)
+    p = ctypes.c_void_p()
+    _check(lib.he_conv_plan(ctx, ctypes.byref(s), encoding, ctypes.byref(p)), ctx)
+    return p
+
+
+def he_plan_destroy(plan):
+    _check(lib.he_plan_destroy(plan))
+
+
+def he_plan_query(plan) -> he_plan_info:
+    info = he_plan_info()
+    _check(lib.he_plan_query(plan, ctypes.byref(info)))
+    return info
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    return {torch.uint8: HE_DTYPE_U8, torch.int8: HE_DTYPE_I8, torch.int64: HE_DTYPE_I64}[t.dtype]
+
+
+def he_encode_conventional(ctx, plan, role, tensor, batch, polys):
+    _check(lib.he_encode_conventional(ctx, plan, role, _ptr(tensor), _dtype_code(tensor), batch, _ptr(polys),
+                                      _stream()), ctx)
+
+
+def he_encode_correlated(ctx, plan, role, tensor, batch, polys):
+    _check(lib.he_encode_correlated(ctx, plan, role, _ptr(tensor), _dtype_code(tensor), batch, _ptr(polys),
+                                    _stream()), ctx)
+
+
+def he_cpmul_conv(ctx, plan, batch, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out):
+    _check(lib.he_cpmul_conv(ctx, plan, batch, _ptr(ct_x), _ptr(pt_w), _ptr(ct_w), _ptr(pt_x), _ptr(ct_add),
+                             _ptr(ct_out), _stream()), ctx)
+
+
+def he_ccmul_precompute(ctx, keys, ct_a, n_a, ct_b, n_b, pairs, group, ct_out):
+    n = len(pairs)
+    pa = (ctypes.c_int32 * max(n, 1))(*[p[0] for p in pairs])
+    pb = (ctypes.c_int32 * max(n, 1))(*[p[1] for p in pairs])
+    _check(lib.he_ccmul_precompute(ctx, keys, _ptr(ct_a), n_a, _ptr(ct_b), n_b, pa, pb, n, group, _ptr(ct_out),
+                                   _stream()), ctx)
+
+
+def he_ccmul_conv_precompute(ctx, keys, plan, batch, ct_rx, ct_rw, ct_out):
+    _check(lib.he_ccmul_conv_precompute(ctx, keys, plan, batch, _ptr(ct_rx), _ptr(ct_rw), _ptr(ct_out), _stream()),
+           ctx)
+
+
+def he_ppmul_conv(ctx, plan, batch, pt_x, pt_w, out):
+    _check(lib.he_ppmul_conv(ctx, plan, batch, _ptr(pt_x), _ptr(pt_w), _ptr(out), _stream()), ctx)
+
+
+def he_decode(ctx, plan, batch, pt, sub, out):
+    _check(lib.he_decode(ctx, plan, batch, _ptr(pt), _ptr(sub), _ptr(out), _stream()), ctx)
+
+
+def he_trace_enable(ctx, on: bool):
+    _check(lib.he_trace_enable(ctx, int(on)), ctx)
+
+
+def he_trace_read(ctx) -> dict:
+    """{kernel family: (launches, total_ms, algorithmic bytes, modular products)}"""
+    arr = (he_trace_entry * 64)()
+    n = ctypes.c_int32()
+    _check(lib.he_trace_read(ctx, arr, 64, ctypes.byref(n)), ctx)
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes, arr[i].modmuls)
+            for i in range(min(n.value, 64))}

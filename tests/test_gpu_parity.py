@@ -1,0 +1,306 @@
+"""GPU parity: every entry point of libcryptotrain.so against the CPU oracle,
+bit for bit (exact integer arithmetic, identical seeds)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import he, packing, protocol  # noqa: E402
+from paper_2409_16675_gb300 import layer, native as nv, workloads as wl  # noqa: E402
+
+RINGS = {
+    "n4096": wl.RING_SMALL,
+    "n8192": wl.RING_MID,
+    "n1024": wl.RingSpec(1024, (40, 45), 65537),
+    "n16384": wl.RingSpec(16384, (60, 60, 55), 65537),
+    "n2048_t40": wl.RingSpec(2048, (50, 50, 50), 1099511480321),
+}
+_CTX = {}
+
+
+def ctx_for(name):
+    if name not in _CTX:
+        c = layer.Context(RINGS[name])
+        _CTX[name] = c
+    return _CTX[name]
+
+
+def oparams(c):
+    return he.Params(c.N, c.q, c.t, c.spec.base_log2, c.spec.eta)
+
+
+def to_np(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("name", list(RINGS))
+def test_primes_match_oracle(name):
+    c = ctx_for(name)
+    assert c.q == he.gen_primes(c.N, list(c.spec.prime_bits))
+    for p in [c.info.aux[j] for j in range(c.info.n_aux)]:
+        assert he.is_prime(p) and p % (2 * c.N) == 1 and p not in c.q
+
+
+@pytest.mark.parametrize("name", ["n4096", "n8192", "n1024", "n16384"])
+def test_keygen_bits(name):
+    c = ctx_for(name)
+    k = layer.Keys(c, 1234, True)
+    ok = he.keygen(oparams(c), 1234, True)
+    assert np.array_equal(to_np(k.export(nv.HE_KEY_SK)), ok.sk)
+    assert np.array_equal(to_np(k.export(nv.HE_KEY_PK)), ok.pk)
+    assert np.array_equal(to_np(k.export(nv.HE_KEY_RLK)), ok.rlk)
+    k.close()
+
+
+@pytest.mark.parametrize("name", list(RINGS))
+def test_encrypt_decrypt_bits(name):
+    c = ctx_for(name)
+    P = oparams(c)
+    k = layer.Keys(c, 77, False)
+    ok = he.keygen(P, 77, False)
+    n = 3
+    m = wl.uniform_mod(5, (n, c.N), c.t)
+    m[0, :5] = [0, 1, c.t - 1, c.t // 2, c.t // 2 + 1]
+    ct = c.ct(n)
+    nv.he_encrypt(c.h, k.h, cuda(m), n, 99, ct)
+    oct_ = he.encrypt(P, ok, m, 99)
+    assert np.array_equal(to_np(ct), oct_)
+    out = c.u64(n, c.N)
+    nv.he_decrypt(c.h, k.h, cuda(oct_), n, out)
+    assert np.array_equal(to_np(out), m)
+    k.close()
+
+
+def test_decrypt_rounding_edges():
+    # ciphertexts (x, 0) with x at the rounding boundaries of floor((t x + q/2)/q)
+    c = ctx_for("n4096")
+    P = oparams(c)
+    k = layer.Keys(c, 3, False)
+    ok = he.keygen(P, 3, False)
+    Q, t = P.Q, P.t
+    xs = [0, 1, Q - 1, Q // 2, Q // 2 + 1, Q // (2 * t), Q // (2 * t) + 1, (Q // t) * 7 + Q // (2 * t) + 1]
+    rng = np.random.default_rng(0)
+    xs += [int(v) for v in rng.integers(0, 2 ** 62, 50)] + [Q - int(v) for v in rng.integers(1, 2 ** 40, 20)]
+    ct = np.zeros((1, 2, P.L, P.N), dtype=np.uint64)
+    for j, x in enumerate(xs):
+        for i, qi in enumerate(P.q):
+            ct[0, 0, i, j] = x % qi
+    out = c.u64(1, c.N)
+    nv.he_decrypt(c.h, k.h, cuda(ct), 1, out)
+    assert np.array_equal(to_np(out), he.decrypt(P, ok, ct))
+    k.close()
+
+
+@pytest.mark.parametrize("name", ["n8192", "n1024", "n16384", "n2048_t40"])
+def test_masks_bits(name):
+    c = ctx_for(name)
+    out = c.u64(4, c.N)
+    nv.he_sample_masks(c.h, 2024, 4, out)
+    assert np.array_equal(to_np(out), he.sample_masks(oparams(c), 2024, 4))
+
+
+SHAPES = [
+    # (C, H, W, M, h, pad) -- several tiles / groups at small N, ragged tails
+    (3, 12, 11, 2, 3, 1),
+    (5, 20, 17, 3, 3, 2),
+    (2, 7, 9, 2, 5, 4),
+    (4, 1, 1, 3, 1, 0),
+    (1, 28, 28, 4, 3, 0),
+]
+
+
+@pytest.mark.parametrize("enc", ["conv", "corr"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_plan_and_encoding_match_oracle(enc, shape):
+    c = ctx_for("n1024")
+    C, H, W, M, h, pad = shape
+    pl = layer.Plan(c, wl.ConvShape(*shape), enc)
+    op = packing.make_plan(enc, c.N, C, H, W, M, h, pad)
+    i = pl.info
+    assert (i.Cn, i.G, i.th, i.tw, i.Th, i.Tw, i.T) == (op.Cn, op.G, op.th, op.tw, op.Th, op.Tw, op.T)
+    if enc == "conv":
+        assert (i.Hn, i.Wn, i.Ooff) == (op.Hn, op.Wn, op.Ooff)
+    else:
+        assert (i.O, i.S) == (op.O, op.S)
+    B = 2
+    x = wl.activations(11, (B, C, H, W))
+    w = wl.weights(12, (M, C, h, h))
+    xp = c.u64(B * op.T * op.G, c.N)
+    wp = c.u64(M * op.G, c.N)
+    pl.encode_input(cuda(x), B, xp)
+    pl.encode_kernel(cuda(w), wp)
+    want_x = np.concatenate([packing.encode_input(op, x[b], c.t).reshape(-1, c.N) for b in range(B)])
+    assert np.array_equal(to_np(xp), want_x)
+    assert np.array_equal(to_np(wp), packing.encode_kernel(op, w, c.t).reshape(-1, c.N))
+    # decode: random polys, with a subtracted operand
+    rng = np.random.default_rng(1)
+    z = rng.integers(0, c.t, (B, M, op.T, c.N), dtype=np.uint64)
+    s = rng.integers(0, c.t, (B, M, op.T, c.N), dtype=np.uint64)
+    y = torch.empty((B, M, op.Ho, op.Wo), dtype=torch.int64, device="cuda")
+    nv.he_decode(c.h, pl.h, B, cuda(z), cuda(s), y)
+    tt = np.uint64(c.t)
+    want = np.stack([packing.decode(op, (z[b] + tt - s[b]) % tt, c.t) for b in range(B)])
+    assert np.array_equal(to_np(y), want)
+    pl.close()
+
+
+@pytest.mark.parametrize("name", ["n1024", "n8192"])
+@pytest.mark.parametrize("families", ["x", "w", "both"])
+def test_cpmul_conv_bits(name, families):
+    c = ctx_for(name)
+    P = oparams(c)
+    k = layer.Keys(c, 5, False)
+    ok = he.keygen(P, 5, False)
+    shape = wl.ConvShape(5, 20, 17, 3, 3, 2) if c.N == 1024 else wl.ConvShape(16, 32, 32, 4, 3, 1)
+    pl = layer.Plan(c, shape, "corr")
+    T, G, M, B = pl.T, pl.G, shape.M, 2
+    nx, nw = B * T * G, M * G
+    rng = np.random.default_rng(3)
+    mx = rng.integers(0, c.t, (nx, c.N), dtype=np.uint64)
+    mw = rng.integers(0, c.t, (nw, c.N), dtype=np.uint64)
+    ptw = rng.integers(0, c.t, (nw, c.N), dtype=np.uint64)
+    ptx = rng.integers(0, c.t, (nx, c.N), dtype=np.uint64)
+    ptw[0, :3] = [c.t - 1, (c.t - 1) // 2, (c.t + 1) // 2]
+    ctx_ = he.encrypt(P, ok, mx, 1)
+    ctw = he.encrypt(P, ok, mw, 2)
+    add = he.encrypt(P, ok, rng.integers(0, c.t, (B * M * T, c.N), dtype=np.uint64), 3)
+    use_x, use_w = families in ("x", "both"), families in ("w", "both")
+    out = c.ct(B * M * T)
+    nv.he_cpmul_conv(c.h, pl.h, B, cuda(ctx_) if use_x else None, cuda(ptw) if use_x else None,
+                     cuda(ctw) if use_w else None, cuda(ptx) if use_w else None, cuda(add), out)
+    terms = []
+    for b in range(B):
+        for m in range(M):
+            for t in range(T):
+                tl = []
+                for g in range(G):
+                    xi = (b * T + t) * G + g
+                    if use_x:
+                        tl.append((xi, m * G + g))
+                    if use_w:
+                        tl.append((nx + m * G + g, nw + xi))
+                terms.append(tl)
+    want = he.cpmul_terms(P, np.concatenate([ctx_, ctw]), np.concatenate([ptw, ptx]), terms, add=add)
+    assert np.array_equal(to_np(out), want)
+    k.close()
+    pl.close()
+
+
+@pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2)])
+def test_ccmul_bits(name, group):
+    c = ctx_for(name)
+    P = oparams(c)
+    k = layer.Keys(c, 8, True)
+    ok = he.keygen(P, 8, True)
+    rng = np.random.default_rng(group)
+    a = he.encrypt(P, ok, rng.integers(0, c.t, (3, c.N), dtype=np.uint64), 4)
+    b = he.encrypt(P, ok, rng.integers(0, c.t, (4, c.N), dtype=np.uint64), 5)
+    pairs = [(0, 1), (2, 3), (1, 0), (2, 2), (0, 0), (1, 3)][: 2 * group]
+    out = c.ct(len(pairs) // group)
+    nv.he_ccmul_precompute(c.h, k.h, cuda(a), 3, cuda(b), 4, pairs, group, out)
+    want = he.ccmul(P, ok, a, b, pairs, group)
+    assert np.array_equal(to_np(out), want)
+    k.close()
+
+
+@pytest.mark.parametrize("name", ["n1024", "n8192", "n2048_t40"])
+def test_ppmul_bits(name):
+    c = ctx_for(name)
+    P = oparams(c)
+    pl = layer.Plan(c, wl.ConvShape(3, 12, 11, 2, 3, 1) if c.N < 4096 else wl.ConvShape(3, 32, 32, 3, 3, 1), "conv")
+    T, G, M, B = pl.T, pl.G, pl.shape.M, 2
+    rng = np.random.default_rng(9)
+    px = rng.integers(0, c.t, (B * T * G, c.N), dtype=np.uint64)
+    pw = rng.integers(0, c.t, (M * G, c.N), dtype=np.uint64)
+    out = c.u64(B * M * T, c.N)
+    nv.he_ppmul_conv(c.h, pl.h, B, cuda(px), cuda(pw), out)
+    terms = [[((b * T + t) * G + g, m * G + g) for g in range(G)] for b in range(B) for m in range(M) for t in range(T)]
+    assert np.array_equal(to_np(out), he.ppmul_terms(P, px, pw, terms))
+    pl.close()
+
+
+def run_layer_both(name, shape, enc, B, seed):
+    c = ctx_for(name)
+    seeds = wl.protocol_seeds(seed)
+    x = wl.activations(seed, (B, shape.C, shape.H, shape.W))
+    w = wl.weights(seed + 1, (shape.M, shape.C, shape.h, shape.h))
+    keys = layer.Keys(c, seeds.keys, True)
+    plan = layer.Plan(c, shape, enc)
+    pl = layer.PLayer(c, keys, plan, B)
+    y = pl.step(cuda(x), cuda(w), seeds)
+    torch.cuda.synchronize()
+    op = packing.make_plan(enc, c.N, shape.C, shape.H, shape.W, shape.M, shape.h, shape.pad)
+    ref = protocol.run_layer(oparams(c), op, x, w, seeds)
+    return c, pl, y, ref, x, w, (keys, plan)
+
+
+@pytest.mark.parametrize("enc", ["conv", "corr"])
+def test_layer_conv_1x28x28_n4096_end_to_end(enc):
+    """The 1x28x28 -> 4 channel 3x3 valid layer at N = 4096, 3 x 36-bit limbs."""
+    c, pl, y, ref, x, w, hs = run_layer_both("n4096", wl.CONV_SMALL.shape, enc, 1, wl.CONV_SMALL.seed)
+    b = pl.buf
+    assert np.array_equal(to_np(b.ct_x), ref.ct_x)
+    assert np.array_equal(to_np(b.ct_rw), ref.ct_rw)
+    assert np.array_equal(to_np(b.rr), ref.rr)
+    assert np.array_equal(to_np(b.out), ref.out)
+    assert np.array_equal(to_np(b.p), ref.p)
+    assert np.array_equal(to_np(y)[0], ref.y)
+    assert np.array_equal(ref.y, protocol.conv_reference(x[0], w, 0))
+    for h in hs:
+        h.close()
+
+
+@pytest.mark.parametrize("enc", ["corr", "conv"])
+def test_layer_conv_3x32x32_n8192_end_to_end(enc):
+    """The 3x32x32 -> 16 channel 3x3 same layer at N = 8192, 4 x 50-bit limbs,
+    20-bit t: offline CCMul-Precompute + online CPMul, full size."""
+    c, pl, y, ref, x, w, hs = run_layer_both("n8192", wl.CONV_MID.shape, enc, 1, wl.CONV_MID.seed)
+    b = pl.buf
+    assert np.array_equal(to_np(b.rr), ref.rr)
+    assert np.array_equal(to_np(b.out), ref.out)
+    assert np.array_equal(to_np(y)[0], ref.y)
+    assert np.array_equal(ref.y, protocol.conv_reference(x[0], w, 1))
+    for h in hs:
+        h.close()
+
+
+def test_layer_batched_ragged_tiles():
+    """batch 3, several tiles and channel groups with ragged tails at N = 1024."""
+    shape = wl.ConvShape(8, 24, 17, 3, 3, 2)
+    c, pl, y, ref, x, w, hs = run_layer_both("n1024", shape, "corr", 3, 41)
+    assert pl.plan.T > 1 and pl.plan.G > 1
+    assert np.array_equal(to_np(pl.buf.out), ref.out)
+    yy = to_np(y)
+    for b in range(3):
+        assert np.array_equal(yy[b], protocol.conv_reference(x[b], w, 2))
+    for h in hs:
+        h.close()
+
+
+def test_errors_are_reported_not_raised_on_device():
+    c = ctx_for("n1024")
+    with pytest.raises(nv.HEError) as e:
+        nv.he_conv_plan(c.h, 64, 64, 64, 2, 3, 1, nv.HE_ENC_CORRELATED)   # cannot fit N = 1024
+    assert e.value.code == -3
+    with pytest.raises(nv.HEError):
+        nv.he_conv_plan(c.h, 3, 8, 8, 2, 3, 3, nv.HE_ENC_CORRELATED)      # pad > h - 1
+    with pytest.raises(nv.HEError):
+        nv.he_setup(nv.make_params(3000, prime_bits=[40], t=65537))       # N not a power of two
+    k = layer.Keys(c, 1, False)
+    a = c.ct(1)
+    with pytest.raises(nv.HEError):
+        nv.he_ccmul_precompute(c.h, k.h, a, 1, a, 1, [(0, 0)], 1, c.ct(1))  # no relin key
+    # zero-sized calls are no-ops
+    nv.he_encrypt(c.h, k.h, c.u64(1, c.N), 0, 1, a)
+    nv.he_decrypt(c.h, k.h, a, 0, c.u64(1, c.N))
+    k.close()
+    torch.cuda.synchronize()
