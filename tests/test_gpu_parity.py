@@ -289,7 +289,7 @@ def test_layer_batched_ragged_tiles():
 def test_errors_are_reported_not_raised_on_device():
     c = ctx_for("n1024")
     with pytest.raises(nv.HEError) as e:
-        nv.he_conv_plan(c.h, 64, 64, 64, 2, 3, 1, nv.HE_ENC_CORRELATED)   # cannot fit N = 1024
+        nv.he_conv_plan(c.h, 1, 40, 40, 2, 40, 0, nv.HE_ENC_CORRELATED)   # a 40x40 kernel cannot fit N = 1024
     assert e.value.code == -3
     with pytest.raises(nv.HEError):
         nv.he_conv_plan(c.h, 3, 8, 8, 2, 3, 3, nv.HE_ENC_CORRELATED)      # pad > h - 1
