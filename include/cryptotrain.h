@@ -195,6 +195,30 @@ int he_cpmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *c
                   const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add, uint64_t *ct_out,
                   cudaStream_t stream);
 
+/* he_cpmul_conv_noalloc: the same computation and argument layout as
+ * he_cpmul_conv, bit-identical results, but the call allocates no device
+ * memory at all: no cudaMalloc, cudaFree or allocating library routine.  It
+ * is meant for callers that cannot allocate at call time: code running while
+ * a stream is being captured into a CUDA graph (cudaMalloc is not allowed
+ * there), serving loops whose device memory is fully reserved up front by
+ * another allocator, and latency-critical paths that must not hit the
+ * synchronisation that cudaMalloc/cudaFree imply.  The paper has no
+ * counterpart; this is a deployment variant of the CPMul convolution.
+ *  - Scratch: a fixed 32 MiB static device array inside the library (held on
+ *    every GPU that loads the library until the process exits).  A call whose
+ *    NTT-form operands and term table need more returns
+ *    HE_ERR_BUDGET_EXCEEDED and does nothing; the config-sized online layer
+ *    (N = 8192, L = 4, 17 input ciphertexts, 16 outputs) needs about 13 MiB.
+ *  - The first call on a device looks up the array's device address once
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and overwrites it (each byte
+ *    read is written earlier in the same call, so no state carries over).
+ *    Calls whose executions overlap on the GPU (different streams, or
+ *    different contexts on the same device) race on it: order them. */
+int he_cpmul_conv_noalloc(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *ct_x, const uint64_t *pt_w,
+                          const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add, uint64_t *ct_out,
+                          cudaStream_t stream);
+
 /* he_ccmul_precompute: CCMul with relinearisation (Section 2, Motivation;
  * Section 3.2 preprocessing).  Output o sums the tensor products of pairs
  * [o*group, (o+1)*group): d0 = sum a0 b0, d1 = sum a0 b1 + a1 b0, d2 = sum

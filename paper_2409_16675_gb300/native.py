@@ -83,6 +83,7 @@ def _load():
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
+        "he_cpmul_conv_noalloc": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
         "he_ccmul_precompute": [vp, vp, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp],
         "he_ccmul_conv_precompute": [vp, vp, vp, i32, vp, vp, vp, vp],
         "he_ppmul_conv": [vp, vp, i32, vp, vp, vp, vp],
@@ -223,6 +224,12 @@ def he_encode_correlated(ctx, plan, role, tensor, batch, polys):
 def he_cpmul_conv(ctx, plan, batch, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out):
     _check(lib.he_cpmul_conv(ctx, plan, batch, _ptr(ct_x), _ptr(pt_w), _ptr(ct_w), _ptr(pt_x), _ptr(ct_add),
                              _ptr(ct_out), _stream()), ctx)
+
+
+def he_cpmul_conv_noalloc(ctx, plan, batch, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out):
+    """he_cpmul_conv without any device allocation (fixed 32 MiB library scratch)."""
+    _check(lib.he_cpmul_conv_noalloc(ctx, plan, batch, _ptr(ct_x), _ptr(pt_w), _ptr(ct_w), _ptr(pt_x),
+                                     _ptr(ct_add), _ptr(ct_out), _stream()), ctx)
 
 
 def he_ccmul_precompute(ctx, keys, ct_a, n_a, ct_b, n_b, pairs, group, ct_out):
