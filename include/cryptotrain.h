@@ -84,7 +84,7 @@ extern "C" {
  *   base_log2    relinearisation digit size in bits, 1..32 (0 -> 16)
  *   eta          centred-binomial error parameter, 1..32 (0 -> 21)
  *   max_ccmul_group  largest number of tensor products summed into one CCMul
- *                output (sizes the auxiliary basis; 0 -> 1024)
+ *                output (sizes the auxiliary basis; 0 -> 64)
  *   device       CUDA device ordinal
  */
 typedef struct he_params {
