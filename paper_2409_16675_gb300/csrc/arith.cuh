@@ -14,6 +14,45 @@ __device__ __forceinline__ u64 shoup(u64 a, u64 w, u64 ws, u64 q) {
     u64 qh = __umul64hi(a, ws);
     return a * w - qh * q;  // [0, 2q)
 }
+// Shoup product built only from 32-bit multiply-accumulates (mul/mad.wide.u32
+// and mad.lo.u32), the cheapest integer-multiply forms of the SM.  The
+// quotient h = a1 s1 + floor((a1 s0 + a0 s1) / 2^32) is floor((a w' - a0 s0)
+// / 2^64), at most 1 below the exact floor(a w' / 2^64); the remainder is
+// a w + h (2^64 - q) mod 2^64.  Result in [0, 3q) for every 64-bit a.
+// nq = 2^64 - q.
+__device__ __forceinline__ u64 shoup3(u64 a, u64 w, u64 ws, u64 nq) {
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, s0, s1, w0, w1, n0, n1, t0, t1, u0, u1, h0, h1, c, l0, l1, z;\n\t"
+        ".reg .u64 t, tl, u, x, h, l;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.wide.u32 t, a0, s1;\n\t"
+        "mov.b64 {t0, t1}, t;\n\t"
+        "cvt.u64.u32 tl, t0;\n\t"
+        "mad.wide.u32 u, a1, s0, tl;\n\t"
+        "mov.b64 {u0, u1}, u;\n\t"
+        "add.cc.u32 c, u1, t1;\n\t"
+        "addc.u32 z, 0, 0;\n\t"
+        "mov.b64 x, {c, z};\n\t"
+        "mad.wide.u32 h, a1, s1, x;\n\t"
+        "mov.b64 {h0, h1}, h;\n\t"
+        "mul.wide.u32 l, a0, w0;\n\t"
+        "mad.wide.u32 l, h0, n0, l;\n\t"
+        "mul.lo.u32 c, a0, w1;\n\t"
+        "mad.lo.u32 c, a1, w0, c;\n\t"
+        "mad.lo.u32 c, h0, n1, c;\n\t"
+        "mad.lo.u32 c, h1, n0, c;\n\t"
+        "mov.b64 {l0, l1}, l;\n\t"
+        "add.u32 l1, l1, c;\n\t"
+        "mov.b64 %0, {l0, l1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(a), "l"(w), "l"(ws), "l"(nq));
+    return r;
+}
 __device__ __forceinline__ u64 red1(u64 a, u64 q) { return a >= q ? a - q : a; }
 __device__ __forceinline__ u64 addm(u64 a, u64 b, u64 q) { return red1(a + b, q); }   // a,b < q
 __device__ __forceinline__ u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
@@ -40,11 +79,13 @@ __device__ __forceinline__ u64 reduce64(u64 a, u64 q, u64 one_s) { return red1(s
 
 // X = sum_i y_i hat_i then reduced into [0, M); returns the number of M
 // subtracted (the CRT overflow count v).
-template <int MW>
-__device__ __forceinline__ int crt_compose(const CrtDev &B, const u64 *y, u64 (&X)[MW]) {
+template <int MW, int NM>
+__device__ __forceinline__ int crt_compose(const CrtDev &B, const u64 (&y)[NM], u64 (&X)[MW]) {
 #pragma unroll
     for (int k = 0; k < MW; k++) X[k] = 0;
-    for (int i = 0; i < B.n; i++) {
+#pragma unroll
+    for (int i = 0; i < NM; i++) {
+        if (i >= B.n) break;
         u64 carry = 0;
 #pragma unroll
         for (int k = 0; k < MW; k++) {
@@ -116,6 +157,44 @@ __device__ __forceinline__ u64 mw_mod(const u64 (&X)[MW], int W, u64 p, u64 r64,
         }
     }
     return r;
+}
+
+// ---------------------------------------------------------------- fast exact base conversion
+// Overflow count v = floor(sum_i y_i / m_i) of a CRT sum from a 58-bit
+// fixed-point estimate S (an underestimate of the true sum by < 1.07 n ulps).
+// Returns false when S's fraction is within 64 ulps of the next integer, the
+// only case in which the estimate could be off; callers then take the exact
+// multi-word path.
+template <int NM>
+__device__ __forceinline__ bool crt_overflow(const ConvDev &C, const u64 (&y)[NM], int n, int &v, u64 &frac) {
+    u64 S = 0;
+#pragma unroll
+    for (int i = 0; i < NM; i++)
+        if (i < n) S += __umul64hi(y[i] << C.sh[i], C.c[i]) >> 5;
+    v = (int)(S >> 58);
+    frac = S & ((1ull << 58) - 1);
+    return frac <= (1ull << 58) - 64;
+}
+// the centring decision X > M/2 is certain when the fraction is not within 64
+// ulps below one half
+__device__ __forceinline__ bool half_certain(u64 frac) {
+    const u64 half = 1ull << 57;
+    return frac >= half || frac + 64 <= half;
+}
+// (sum_i y_i h_i - k M) mod p, fully reduced; h, hs: constants (M/m_i) mod p
+template <int NM>
+__device__ __forceinline__ u64 conv_to(const u64 (&y)[NM], int n, const u64 *h, const u64 *hs, u64 k, u64 Mp, u64 Mps,
+                                       u64 p) {
+    u64 acc = 0;
+    const u64 p2 = 2 * p;
+#pragma unroll
+    for (int i = 0; i < NM; i++)
+        if (i < n) {
+            acc += shoup(y[i], h[i], hs[i], p);
+            acc = acc >= p2 ? acc - p2 : acc;
+        }
+    acc = red1(acc, p);
+    return subm(acc, red1(shoup(k, Mp, Mps, p), p), p);
 }
 
 // ---------------------------------------------------------------- ChaCha20

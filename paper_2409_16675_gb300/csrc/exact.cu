@@ -74,17 +74,36 @@ int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx
 }
 
 // ---------------------------------------------------------------- exact CRT kernels
+// Template parameters: LM, KM bound the runtime limb counts L and K (loops are
+// unrolled to the bound with guards so every array stays in registers); MW
+// bounds the words of a multi-word CRT sum (exact fallback path, digits).
+
 // centred lift of each coefficient (residues mod Q) to the auxiliary primes
-template <int MW>
-__global__ void k_base_extend(const u64 *__restrict__ src, long long n_polys, int L, int K, int N,
-                              u64 *__restrict__ dst, const ModDev *__restrict__ mods, const ExactDev *__restrict__ E) {
+template <int LM, int KM, int MW>
+__global__ void __launch_bounds__(128) k_base_extend(const u64 *__restrict__ src, long long n_polys, int L, int K,
+                                                     int N, u64 *__restrict__ dst, const ModDev *__restrict__ mods,
+                                                     const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= n_polys * N) return;
     const int x = (int)(gid % N);
     const long long p = gid / N;
     const CrtDev &Q = E->Q;
-    u64 y[MAXP];
-    for (int i = 0; i < L; i++) y[i] = crt_y(Q, i, src[(p * L + i) * N + x]);
+    u64 y[LM];
+#pragma unroll
+    for (int i = 0; i < LM; i++)
+        if (i < L) y[i] = crt_y(Q, i, src[(p * L + i) * N + x]);
+    int v;
+    u64 fr;
+    if (crt_overflow<LM>(E->Qc, y, L, v, fr) && half_certain(fr)) {
+        const u64 k = (u64)v + (fr >= (1ull << 57));
+#pragma unroll
+        for (int j = 0; j < KM; j++)
+            if (j < K) {
+                const u64 b = mods[L + j].q;
+                dst[(p * K + j) * N + x] = conv_to<LM>(y, L, E->QhatB[j], E->QhatBs[j], k, E->Q_b[j], E->Q_bs[j], b);
+            }
+        return;
+    }
     u64 X[MW];
     crt_compose<MW>(Q, y, X);
     const bool neg = mw_greater<MW>(X, Q.Mhalf, Q.W);
@@ -98,10 +117,11 @@ __global__ void k_base_extend(const u64 *__restrict__ src, long long n_polys, in
 
 // d: [n_out][3][L+K][N] exact tensor products (coefficient form).
 // dq: [n_out][2][L][N] rescaled d0, d1; digits: [n_out][ell][N] of rescaled d2.
-template <int MW>
-__global__ void k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K, int N, int ell, int base_log2,
-                              u64 *__restrict__ dq, uint32_t *__restrict__ digits, const ModDev *__restrict__ mods,
-                              const ExactDev *__restrict__ E) {
+template <int LM, int KM, int MW>
+__global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K, int N,
+                                                     int ell, int base_log2, u64 *__restrict__ dq,
+                                                     uint32_t *__restrict__ digits, const ModDev *__restrict__ mods,
+                                                     const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_out * 3 * N) return;
     const int x = (int)(gid % N);
@@ -110,95 +130,145 @@ __global__ void k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K
     const int LK = L + K;
     const u64 *src = d + ((o * 3 + j) * LK) * N + x;
     const CrtDev &Q = E->Q, &B = E->B;
-    u64 y[MAXP];
-    // r = [t d + floor(q/2)]_q  (residues, then exact integer)
-    for (int i = 0; i < L; i++) {
-        const u64 qi = mods[i].q;
-        const u64 td = red1(shoup(src[(long long)i * N], E->t_q[i], E->t_qs[i], qi), qi);
-        y[i] = crt_y(Q, i, addm(td, E->Qhalf_q[i], qi));
+    // r = [t d + floor(q/2)]_q as residues y (CRT form)
+    u64 y[LM];
+#pragma unroll
+    for (int i = 0; i < LM; i++)
+        if (i < L) {
+            const u64 qi = mods[i].q;
+            const u64 td = red1(shoup(src[(long long)i * N], E->t_q[i], E->t_qs[i], qi), qi);
+            y[i] = crt_y(Q, i, addm(td, E->Qhalf_q[i], qi));
+        }
+    // r mod b_k
+    u64 rb[KM];
+    int v;
+    u64 fr;
+    if (crt_overflow<LM>(E->Qc, y, L, v, fr)) {
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+            if (k < K)
+                rb[k] = conv_to<LM>(y, L, E->QhatB[k], E->QhatBs[k], (u64)v, E->Q_b[k], E->Q_bs[k], mods[L + k].q);
+    } else {
+        u64 R[MW];
+        crt_compose<MW>(Q, y, R);
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+            if (k < K) {
+                const ModDev &M = mods[L + k];
+                rb[k] = mw_mod<MW>(R, Q.W, M.q, M.r64, M.r64s, M.one_s);
+            }
     }
-    u64 R[MW];
-    crt_compose<MW>(Q, y, R);
-    // F = (t d + h - r) / q modulo each aux prime
-    for (int k = 0; k < K; k++) {
-        const ModDev &M = mods[L + k];
-        const u64 b = M.q;
-        const u64 rb = mw_mod<MW>(R, Q.W, b, M.r64, M.r64s, M.one_s);
-        const u64 td = red1(shoup(src[(long long)(L + k) * N], E->t_b[k], E->t_bs[k], b), b);
-        const u64 num = subm(addm(td, E->Qhalf_b[k], b), rb, b);
-        y[k] = crt_y(B, k, red1(shoup(num, E->Qinv_b[k], E->Qinv_bs[k], b), b));
-    }
-    u64 F[MW];
-    crt_compose<MW>(B, y, F);
-    const bool neg = mw_greater<MW>(F, B.Mhalf, B.W);
-    u64 f[MAXP];
-    for (int i = 0; i < L; i++) {
-        const ModDev &M = mods[i];
-        u64 a = mw_mod<MW>(F, B.W, M.q, M.r64, M.r64s, M.one_s);
-        f[i] = neg ? subm(a, E->B_q[i], M.q) : a;
+    // F = (t d + h - r) / q modulo each aux prime, as residues yb (CRT form over B)
+    u64 yb[KM];
+#pragma unroll
+    for (int k = 0; k < KM; k++)
+        if (k < K) {
+            const u64 b = mods[L + k].q;
+            const u64 td = red1(shoup(src[(long long)(L + k) * N], E->t_b[k], E->t_bs[k], b), b);
+            const u64 num = subm(addm(td, E->Qhalf_b[k], b), rb[k], b);
+            yb[k] = crt_y(B, k, red1(shoup(num, E->Qinv_b[k], E->Qinv_bs[k], b), b));
+        }
+    // centred F mod q_i
+    u64 f[LM];
+    if (crt_overflow<KM>(E->Bc, yb, K, v, fr) && half_certain(fr)) {
+        const u64 k = (u64)v + (fr >= (1ull << 57));
+#pragma unroll
+        for (int i = 0; i < LM; i++)
+            if (i < L) f[i] = conv_to<KM>(yb, K, E->BhatQ[i], E->BhatQs[i], k, E->B_q[i], E->B_qs[i], mods[i].q);
+    } else {
+        u64 F[MW];
+        crt_compose<MW>(B, yb, F);
+        const bool neg = mw_greater<MW>(F, B.Mhalf, B.W);
+#pragma unroll
+        for (int i = 0; i < LM; i++)
+            if (i < L) {
+                const ModDev &M = mods[i];
+                const u64 a = mw_mod<MW>(F, B.W, M.q, M.r64, M.r64s, M.one_s);
+                f[i] = neg ? subm(a, E->B_q[i], M.q) : a;
+            }
     }
     if (j < 2) {
         u64 *out = dq + ((o * 2 + j) * L) * N + x;
-        for (int i = 0; i < L; i++) out[(long long)i * N] = f[i];
+#pragma unroll
+        for (int i = 0; i < LM; i++)
+            if (i < L) out[(long long)i * N] = f[i];
         return;
     }
-    // digits of [F]_q in [0, q)
-    for (int i = 0; i < L; i++) y[i] = crt_y(Q, i, f[i]);
+    // digits of [F]_q in [0, q): exact multi-word value
+#pragma unroll
+    for (int i = 0; i < LM; i++)
+        if (i < L) y[i] = crt_y(Q, i, f[i]);
     u64 X[MW];
     crt_compose<MW>(Q, y, X);
-    const u64 dmask = base_log2 >= 64 ? ~0ull : ((1ull << base_log2) - 1);
+    const u64 dmask = (1ull << base_log2) - 1;
     uint32_t *dg = digits + (o * ell) * N + x;
     for (int dd = 0; dd < ell; dd++) {
         const int bit = dd * base_log2;
         const int w = bit >> 6, sh = bit & 63;
-        u64 v = 0;
+        u64 val = 0;
 #pragma unroll
         for (int k = 0; k < MW; k++) {
-            if (k == w) v = X[k] >> sh;
-            if (k == w + 1 && sh + base_log2 > 64) v |= X[k] << (64 - sh);
+            if (k == w) val = X[k] >> sh;
+            if (k == w + 1 && sh + base_log2 > 64) val |= X[k] << (64 - sh);
         }
-        dg[(long long)dd * N] = (uint32_t)(v & dmask);
+        dg[(long long)dd * N] = (uint32_t)(val & dmask);
     }
 }
 
 // x: [n][L][N] = c0 + c1 s; m = floor((t x + floor(q/2)) / q) mod t
 //    = (floor(q/2) - [t x + floor(q/2)]_q) * q^-1 mod t
-template <int MW>
-__global__ void k_decrypt_exact(const u64 *__restrict__ xs, int n, int L, int N, u64 *__restrict__ m,
-                                const ModDev *__restrict__ mods, const ExactDev *__restrict__ E) {
+template <int LM, int KM, int MW>
+__global__ void __launch_bounds__(128) k_decrypt_exact(const u64 *__restrict__ xs, int n, int L, int N,
+                                                       u64 *__restrict__ m, const ModDev *__restrict__ mods,
+                                                       const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n * N) return;
     const int x = (int)(gid % N);
     const long long k = gid / N;
     const CrtDev &Q = E->Q;
-    u64 y[MAXP];
-    for (int i = 0; i < L; i++) {
-        const u64 qi = mods[i].q;
-        const u64 tx = red1(shoup(xs[(k * L + i) * N + x], E->t_q[i], E->t_qs[i], qi), qi);
-        y[i] = crt_y(Q, i, addm(tx, E->Qhalf_q[i], qi));
-    }
-    u64 R[MW];
-    crt_compose<MW>(Q, y, R);
+    u64 y[LM];
+#pragma unroll
+    for (int i = 0; i < LM; i++)
+        if (i < L) {
+            const u64 qi = mods[i].q;
+            const u64 tx = red1(shoup(xs[(k * L + i) * N + x], E->t_q[i], E->t_qs[i], qi), qi);
+            y[i] = crt_y(Q, i, addm(tx, E->Qhalf_q[i], qi));
+        }
     const u64 t = E->t;
-    const u64 rt = mw_mod<MW>(R, Q.W, t, E->r64_t, E->r64_ts, E->one_ts);
+    u64 rt;
+    int v;
+    u64 fr;
+    if (crt_overflow<LM>(E->Qc, y, L, v, fr)) {
+        rt = conv_to<LM>(y, L, E->Qhat_t, E->Qhat_ts, (u64)v, E->Q_t, E->Q_ts, t);
+    } else {
+        u64 R[MW];
+        crt_compose<MW>(Q, y, R);
+        rt = mw_mod<MW>(R, Q.W, t, E->r64_t, E->r64_ts, E->one_ts);
+    }
     m[k * N + x] = red1(shoup(subm(E->Qhalf_t, rt, t), E->Qinv_t, E->Qinv_ts, t), t);
 }
 
-static int mw_of(he_ctx *c) {
+// kernel size class of a context: limb bounds and multi-word capacity
+static int size_class(he_ctx *c) {
     const int W = c->h_exact.Q.W > c->h_exact.B.W ? c->h_exact.Q.W : c->h_exact.B.W;
-    return W <= 6 ? 6 : (W <= 10 ? 10 : 18);
+    if (c->L <= 4 && c->K <= 4 && W <= 6) return 0;
+    if (c->L <= 8 && c->K <= 8 && W <= 10) return 1;
+    return 2;
 }
+
+#define HE_DISPATCH_EXACT(KER, ...)                                                   \
+    switch (size_class(c)) {                                                           \
+    case 0: KER<4, 4, 6><<<g, 128, 0, st>>>(__VA_ARGS__); break;                      \
+    case 1: KER<8, 8, 10><<<g, 128, 0, st>>>(__VA_ARGS__); break;                     \
+    default: KER<16, 24, 18><<<g, 128, 0, st>>>(__VA_ARGS__); break;                  \
+    }
 
 int launch_base_extend(he_ctx *c, const u64 *src, long long n_polys, u64 *dst_aux, cudaStream_t st) {
     const long long total = n_polys * c->N;
     if (!total) return HE_OK;
     const unsigned g = (unsigned)((total + 127) / 128);
     TraceScope ts(c, st, "base_extend", 8.0 * total * (c->L + c->K), 0);
-    switch (mw_of(c)) {
-    case 6: k_base_extend<6><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
-    case 10: k_base_extend<10><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
-    default: k_base_extend<18><<<g, 128, 0, st>>>(src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact); break;
-    }
+    HE_DISPATCH_EXACT(k_base_extend, src, n_polys, c->L, c->K, c->N, dst_aux, c->d_mods, c->d_exact)
     return cuda_check(c, cudaGetLastError(), "k_base_extend");
 }
 
@@ -209,11 +279,7 @@ int launch_scale_round(he_ctx *c, const u64 *d, int n_out, u64 *dq, uint32_t *di
     const int b = c->P.base_log2;
     TraceScope ts(c, st, "scale_round", 8.0 * total * (c->L + c->K) + 8.0 * n_out * 2 * c->L * c->N +
                   4.0 * n_out * c->ell * c->N, 0);
-    switch (mw_of(c)) {
-    case 6: k_scale_round<6><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
-    case 10: k_scale_round<10><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
-    default: k_scale_round<18><<<g, 128, 0, st>>>(d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact); break;
-    }
+    HE_DISPATCH_EXACT(k_scale_round, d, n_out, c->L, c->K, c->N, c->ell, b, dq, digits, c->d_mods, c->d_exact)
     return cuda_check(c, cudaGetLastError(), "k_scale_round");
 }
 
@@ -222,11 +288,7 @@ int launch_decrypt_exact(he_ctx *c, const u64 *x, int n, u64 *m, cudaStream_t st
     if (!total) return HE_OK;
     const unsigned g = (unsigned)((total + 127) / 128);
     TraceScope ts(c, st, "decrypt_exact", 8.0 * total * (c->L + 1), 0);
-    switch (mw_of(c)) {
-    case 6: k_decrypt_exact<6><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
-    case 10: k_decrypt_exact<10><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
-    default: k_decrypt_exact<18><<<g, 128, 0, st>>>(x, n, c->L, c->N, m, c->d_mods, c->d_exact); break;
-    }
+    HE_DISPATCH_EXACT(k_decrypt_exact, x, n, c->L, c->N, m, c->d_mods, c->d_exact)
     return cuda_check(c, cudaGetLastError(), "k_decrypt_exact");
 }
 

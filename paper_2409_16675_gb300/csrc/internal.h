@@ -18,16 +18,21 @@ constexpr int MAX_MODS = 48;   // Q limbs + aux limbs + t
 constexpr int MAXP = 24;       // primes of one CRT basis
 constexpr int MAXW = 18;       // 64-bit words of a CRT sum (< n * M)
 
-// One NTT-friendly modulus: constants for Shoup products and its twiddles.
-// Twiddle index convention: entry 2^s + i is the factor of group i at stage s
-// of the merged-twist negacyclic transform (psi^bitrev), inverse table holds
-// psi^-bitrev.
+// One NTT-friendly modulus: constants for Shoup products and its tables.
+//   fw[2^s + i]  forward factor of group i at stage s of the merged-twist
+//                negacyclic transform: psi^bitrev(2^s + i)
+//   iw[2^s + k]  inverse (decimation-in-time, bit-reversed input) factor for
+//                offset k at stage s: omega^-(k 2^(n-1-s)), omega = psi^2
+//   z[e]         untwist and scale: psi^-e N^-1
+// each with its Shoup companion, stored as interleaved (value, companion)
+// pairs so one 16-byte load fetches both.
 struct ModDev {
     u64 q, twoq;
+    u64 nq;            // 2^64 - q
     u64 r64, r64s;     // 2^64 mod q, Shoup companion
     u64 one_s;         // floor(2^64 / q): Shoup companion of 1
     u64 ninv, ninvs;   // N^-1 mod q
-    const u64 *fw, *fws, *iw, *iws;
+    const ulonglong2 *fw, *iw, *z;
 };
 
 // A CRT basis {m_i}: M = prod m_i, hat_i = M / m_i, inv_i = hat_i^-1 mod m_i.
@@ -40,10 +45,26 @@ struct CrtDev {
     u64 Mhalf[MAXW];          // floor(M / 2)
 };
 
+// Overflow estimate of a CRT sum: with m_i' = m_i << sh_i in [2^63, 2^64) and
+// c_i = floor(2^127 / m_i'), mulhi(y_i << sh_i, c_i) >> 5 underestimates
+// y_i / m_i * 2^58 by less than 1.07.
+struct ConvDev {
+    u64 sh[MAXP];
+    u64 c[MAXP];
+};
+
 // Everything the exact kernels need in one device block.
 struct ExactDev {
     CrtDev Q;                 // coefficient modulus basis
     CrtDev B;                 // auxiliary basis for the tensor product
+    ConvDev Qc, Bc;           // overflow estimates over Q and over B
+    // base-conversion tables with Shoup companions:
+    // QhatB[j][i] = (Q / q_i) mod b_j, BhatQ[i][j] = (B / b_j) mod q_i, Qhat_t[i] = (Q / q_i) mod t
+    u64 QhatB[MAXP][MAXP], QhatBs[MAXP][MAXP];
+    u64 BhatQ[MAXP][MAXP], BhatQs[MAXP][MAXP];
+    u64 Qhat_t[MAXP], Qhat_ts[MAXP];
+    u64 Q_bs[MAXP], B_qs[MAXP];  // Shoup companions of Q mod b_j and B mod q_i
+    u64 Q_t, Q_ts;               // Q mod t
     // per aux prime b_j: Q mod b_j, floor(Q/2) mod b_j, Q^-1 mod b_j (+Shoup), t mod b_j (+Shoup)
     u64 Q_b[MAXP], Qhalf_b[MAXP], Qinv_b[MAXP], Qinv_bs[MAXP], t_b[MAXP], t_bs[MAXP];
     // per q_i: B mod q_i, floor(Q/2) mod q_i, t mod q_i (+Shoup), Delta mod q_i (+Shoup)

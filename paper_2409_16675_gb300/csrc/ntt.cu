@@ -5,9 +5,16 @@
 // limb polynomial; each of its N/16 threads keeps 16 coefficients in
 // registers and runs up to four butterfly stages (radix 16) between exchanges
 // through padded shared memory.  The forward transform is Cooley-Tukey with
-// the psi twist merged into the twiddles (bit-reversed output), the inverse is
-// Gentleman-Sande; butterflies use Harvey's lazy reduction (values in [0,4q)
-// forward, [0,2q) inverse) with Shoup products.
+// the psi twist merged into the twiddles (natural input, bit-reversed output);
+// the inverse is a decimation-in-time Cooley-Tukey cyclic transform with
+// omega^-1 on the bit-reversed input, followed by the untwist psi^-e N^-1.
+// Both use Harvey-style lazy butterflies with the approximate-quotient Shoup
+// product built from 32-bit multiply-accumulates (twiddle product in
+// [0, 3q)); the butterfly adds 4q to the difference, so values grow by at
+// most 4q per stage: with every modulus of a launch below 2^57 they stay below 57q < 2^63
+// through 14 stages and the LAZY variants make no correction inside the
+// transform; otherwise X is brought below 4q before each butterfly and every
+// value stays below 8q < 2^64.
 //
 // NTT-domain storage order ("perm16"): memory position k*(N/16) + tau holds
 // the bit-reversed-order value of index 16*tau + k, which is exactly what the
@@ -25,6 +32,7 @@ struct Cfg {
     static constexpr int NP = (LOGN + 3) / 4;
     static constexpr int RL = LOGN - 4 * (NP - 1);
     static constexpr int SMEM = (N + N / 16) * 8;
+    static constexpr int MINB = LOGN >= 14 ? 1 : 2;  // resident CTAs per SM the register budget targets
 };
 
 __device__ __forceinline__ int padi(int j) { return j + (j >> 4); }
@@ -34,9 +42,9 @@ __device__ __forceinline__ int jidx(int tau, int k, int lo) {
     return ((tau >> lo) << (lo + 4)) | (k << lo) | (tau & ((1 << lo) - 1));
 }
 
-template <int LOGN, int R>
+template <int LOGN, int R, bool LAZY>
 __device__ __forceinline__ void fwd_pass(u64 (&v)[16], int tau, int lo, int s0, const ModDev &M) {
-    const u64 q = M.q, q2 = M.twoq;
+    const u64 q4 = 2 * M.twoq, nq = M.nq;
 #pragma unroll
     for (int st = 0; st < R; st++) {
         const int kb = R - 1 - st;
@@ -46,35 +54,38 @@ __device__ __forceinline__ void fwd_pass(u64 (&v)[16], int tau, int lo, int s0, 
         for (int k = 0; k < 16; k++) {
             if (k & (1 << kb)) continue;
             const int widx = base + (k >> (kb + 1));
-            const u64 W = __ldg(M.fw + widx), Ws = __ldg(M.fws + widx);
+            const ulonglong2 Wp = __ldg(M.fw + widx);
             u64 X = v[k];
             const u64 Y = v[k | (1 << kb)];
-            X = X >= q2 ? X - q2 : X;
-            const u64 Tt = shoup(Y, W, Ws, q);
+            if (!LAZY) X = X >= q4 ? X - q4 : X;
+            const u64 Tt = shoup3(Y, Wp.x, Wp.y, nq);
             v[k] = X + Tt;
-            v[k | (1 << kb)] = X - Tt + q2;
+            v[k | (1 << kb)] = X - Tt + q4;
         }
     }
 }
 
-template <int LOGN, int R>
-__device__ __forceinline__ void inv_pass(u64 (&v)[16], int tau, int lo, int s_top, const ModDev &M) {
-    const u64 q = M.q, q2 = M.twoq;
+// Decimation-in-time pass of the inverse: stages s0 .. s0+R-1 act on element
+// bits lo+kb0 .. lo+kb0+R-1; the factor of the pair whose lower element is e
+// is iw[2^s + (e mod 2^s)].
+template <int R, int KB0, bool LAZY>
+__device__ __forceinline__ void inv_pass(u64 (&v)[16], int tau, int lo, int s0, const ModDev &M) {
+    const u64 q4 = 2 * M.twoq, nq = M.nq;
 #pragma unroll
     for (int st = 0; st < R; st++) {
-        const int kb = st;
-        const int s = s_top - st;
-        const int base = (1 << s) + ((tau >> lo) << (3 - kb));
+        const int kb = KB0 + st;
+        const int s = s0 + st;
+        const int base = (1 << s) + (tau & ((1 << lo) - 1));
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             if (k & (1 << kb)) continue;
-            const int widx = base + (k >> (kb + 1));
-            const u64 W = __ldg(M.iw + widx), Ws = __ldg(M.iws + widx);
-            const u64 X = v[k], Y = v[k | (1 << kb)];
-            u64 S = X + Y;
-            S = S >= q2 ? S - q2 : S;
-            v[k] = S;
-            v[k | (1 << kb)] = shoup(X - Y + q2, W, Ws, q);
+            const int widx = base + ((k & ((1 << kb) - 1)) << lo);
+            const ulonglong2 Wp = __ldg(M.iw + widx);
+            u64 X = v[k];
+            if (!LAZY) X = X >= q4 ? X - q4 : X;
+            const u64 Tt = shoup3(v[k | (1 << kb)], Wp.x, Wp.y, nq);
+            v[k] = X + Tt;
+            v[k | (1 << kb)] = X - Tt + q4;
         }
     }
 }
@@ -88,8 +99,8 @@ __device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[16], int tau, int lo_
     __syncthreads();
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) k_fwd(FwdJob J, const ModDev *__restrict__ mods) {
+template <int LOGN, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J, const ModDev *__restrict__ mods) {
     extern __shared__ u64 sm[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     const int tau = threadIdx.x;
@@ -142,24 +153,22 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) k_fwd(FwdJob J, const ModDev *__
     }
     int lo = LOGN - 4;
     for (int pass = 0; pass < NP - 1; pass++) {
-        fwd_pass<LOGN, 4>(v, tau, lo, 4 * pass, M);
+        fwd_pass<LOGN, 4, LAZY>(v, tau, lo, 4 * pass, M);
         const int lo_next = pass == NP - 2 ? 0 : lo - 4;
         exchange(sm, v, tau, lo, lo_next);
         lo = lo_next;
     }
-    fwd_pass<LOGN, RL>(v, tau, 0, 4 * (NP - 1), M);
+    fwd_pass<LOGN, RL, LAZY>(v, tau, 0, 4 * (NP - 1), M);
     u64 *d = J.dst + (long long)p * J.dst_stride + (long long)limb * N;
-    const u64 q = M.q, q2 = M.twoq;
+    const u64 q = M.q;
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-        u64 x = v[k];
-        x = x >= q2 ? x - q2 : x;
-        d[k * T + tau] = red1(x, q);
+        d[k * T + tau] = reduce64(v[k], q, M.one_s);   // from [0, 57q) or [0, 8q)
     }
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T) k_mac_intt(MacJob J, const ModDev *__restrict__ mods) {
+template <int LOGN, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJob J, const ModDev *__restrict__ mods) {
     extern __shared__ u64 sm[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     const int tau = threadIdx.x;
@@ -167,39 +176,46 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) k_mac_intt(MacJob J, const ModDe
     const int o = blockIdx.x - limb * J.n_out;
     const ModDev M = mods[J.mod_base + limb];
     u64 v[16];
-    {
-        u64 lo[16], hi[16];
+    // multiply-accumulate in two halves of 8 coefficients (128-bit sums) to
+    // keep the register footprint of the accumulators small
+    const int t0 = J.ptr[o], t1 = J.ptr[o + 1];
 #pragma unroll
-        for (int k = 0; k < 16; k++) { lo[k] = 0; hi[k] = 0; }
-        const int t0 = J.ptr[o], t1 = J.ptr[o + 1];
+    for (int half = 0; half < 2; half++) {
+        u64 lo[8], hi[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; kk++) { lo[kk] = 0; hi[kk] = 0; }
         int cnt = 0;
         for (int tk = t0; tk < t1; tk++) {
-            const u64 *a = J.A + ((long long)J.ta[tk] + limb) * N;
-            const u64 *b = J.B + ((long long)J.tb[tk] + limb) * N;
+            const u64 *a = J.A + ((long long)J.ta[tk] + limb) * N + half * 8 * T + tau;
+            const u64 *b = J.B + ((long long)J.tb[tk] + limb) * N + half * 8 * T + tau;
 #pragma unroll
-            for (int k = 0; k < 16; k++) {
+            for (int kk = 0; kk < 8; kk++) {
                 u64 pl, ph;
-                mul128(a[k * T + tau], b[k * T + tau], pl, ph);
-                lo[k] += pl;
-                hi[k] += ph + (lo[k] < pl);
+                mul128(a[kk * T], b[kk * T], pl, ph);
+                lo[kk] += pl;
+                hi[kk] += ph + (lo[kk] < pl);
             }
             if (++cnt == 15) {  // products < 2^124: fold before the 128-bit sum can overflow
 #pragma unroll
-                for (int k = 0; k < 16; k++) { lo[k] = reduce128(lo[k], hi[k], M); hi[k] = 0; }
+                for (int kk = 0; kk < 8; kk++) { lo[kk] = reduce128(lo[kk], hi[kk], M); hi[kk] = 0; }
                 cnt = 0;
             }
         }
 #pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = reduce128(lo[k], hi[k], M);
+        for (int kk = 0; kk < 8; kk++) v[half * 8 + kk] = reduce128(lo[kk], hi[kk], M);
     }
-    inv_pass<LOGN, RL>(v, tau, 0, LOGN - 1, M);
+    // inverse: bits 0-3 first (the perm16 register tile), then upward; the
+    // last window is the top four bits [LOGN-4, LOGN) holding the remaining
+    // RL stages, and leaves every thread with coalesced natural-order elements
+    inv_pass<4, 0, LAZY>(v, tau, 0, 0, M);
     int lo = 0;
-    for (int pass = NP - 2; pass >= 0; pass--) {
-        const int lo_next = LOGN - 4 * (pass + 1);
-        exchange(sm, v, tau, lo, lo_next);
-        lo = lo_next;
-        inv_pass<LOGN, 4>(v, tau, lo, 4 * pass + 3, M);
+    for (int pass = 1; pass < NP - 1; pass++) {
+        exchange(sm, v, tau, lo, 4 * pass);
+        lo = 4 * pass;
+        inv_pass<4, 0, LAZY>(v, tau, lo, 4 * pass, M);
     }
+    exchange(sm, v, tau, lo, LOGN - 4);
+    inv_pass<RL, 4 - RL, LAZY>(v, tau, LOGN - 4, 4 * (NP - 1), M);
     // natural order: element j = k*T + tau
     const u64 q = M.q;
     u64 *out = J.out + (long long)o * J.out_stride + (long long)limb * N;
@@ -214,7 +230,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) k_mac_intt(MacJob J, const ModDe
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         const int x = k * T + tau;
-        u64 r = red1(shoup(v[k], M.ninv, M.ninvs, q), q);
+        const ulonglong2 zp = __ldg(M.z + x);
+        u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
         if (err) {
             const int e = err[x];
             r = e >= 0 ? addm(r, (u64)e, q) : subm(r, (u64)(-e), q);
@@ -231,21 +248,31 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T) k_mac_intt(MacJob J, const ModDe
     }
 }
 
+// true when every modulus of the launch is below 2^57 (no in-transform corrections)
+static bool lazy_ok(const he_ctx *c, int mod_base, int n_limbs) {
+    for (int i = 0; i < n_limbs; i++)
+        if (c->h_mods[mod_base + i].q >= (1ull << 57)) return false;  // 57 q < 2^63
+    return true;
+}
+
 template <int LOGN>
 static int fwd_t(he_ctx *c, const FwdJob &j, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fwd<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
+    const bool lazy = lazy_ok(c, j.mod_base, j.n_limbs);
     const long long blocks = (long long)j.n_polys * j.n_limbs;
     if (blocks == 0) return HE_OK;
     const int N = Cfg<LOGN>::N;
     const double src_bytes = j.kind == SRC_RNS ? 8.0 * j.n_limbs : (j.kind == SRC_I8 ? 1.0 : (j.kind == SRC_U32 ? 4.0 : 8.0));
     TraceScope ts(c, st, "ntt_fwd", (double)j.n_polys * N * (src_bytes + 8.0 * j.n_limbs),
                   (double)blocks * (N / 2) * LOGN);
-    k_fwd<LOGN><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    if (lazy) k_fwd<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    else k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
     return cuda_check(c, cudaGetLastError(), "k_fwd");
 }
 
@@ -254,9 +281,11 @@ static int mac_t(he_ctx *c, const MacJob &j, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_mac_intt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mac_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mac_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
+    const bool lazy = lazy_ok(c, j.mod_base, j.n_limbs);
     const long long blocks = (long long)j.n_out * j.n_limbs;
     if (blocks == 0) return HE_OK;
     const int N = Cfg<LOGN>::N;
@@ -264,7 +293,8 @@ static int mac_t(he_ctx *c, const MacJob &j, cudaStream_t st) {
     double bytes = lb * (j.n_out + j.n_dist_a + j.n_dist_b + (j.add ? j.n_out : 0));
     double mm = (double)blocks * ((N / 2) * LOGN + 3.0 * N) + (double)j.n_terms * N * j.n_limbs;
     TraceScope ts(c, st, "mac_intt", bytes, mm);
-    k_mac_intt<LOGN><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    if (lazy) k_mac_intt<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    else k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
     return cuda_check(c, cudaGetLastError(), "k_mac_intt");
 }
 

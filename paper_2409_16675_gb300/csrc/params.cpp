@@ -157,17 +157,28 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     u64 psi = root_2n(q, N);
     if (!psi) { err = "no primitive 2N-th root"; return false; }
     u64 psiinv = invmod(psi, q);
-    std::vector<u64> tab(4 * (size_t)N);
-    u64 *fw = tab.data(), *fws = fw + N, *iw = fws + N, *iws = iw + N;
-    // powers psi^e for e in [0, N)
-    std::vector<u64> pw(N), ipw(N);
+    const u64 ninv = invmod((u64)N, q);
+    // interleaved (value, Shoup companion) pairs: fw [N], iw [N], z [N]
+    std::vector<u64> tab(6 * (size_t)N, 0);
+    u64 *fw = tab.data(), *iw = fw + 2 * N, *zt = iw + 2 * N;
+    // powers psi^e and psi^-e for e in [0, 2N)
+    std::vector<u64> pw(2 * N), ipw(2 * N);
     pw[0] = ipw[0] = 1;
-    for (int e = 1; e < N; e++) { pw[e] = mulmod(pw[e - 1], psi, q); ipw[e] = mulmod(ipw[e - 1], psiinv, q); }
+    for (int e = 1; e < 2 * N; e++) { pw[e] = mulmod(pw[e - 1], psi, q); ipw[e] = mulmod(ipw[e - 1], psiinv, q); }
     for (int k = 0; k < N; k++) {
-        int e = bitrev(k, logN);
-        fw[k] = pw[e]; fws[k] = shoup_c(fw[k], q);
-        iw[k] = ipw[e]; iws[k] = shoup_c(iw[k], q);
+        fw[2 * k] = pw[bitrev(k, logN)];
+        fw[2 * k + 1] = shoup_c(fw[2 * k], q);
+        zt[2 * k] = mulmod(ipw[k], ninv, q);
+        zt[2 * k + 1] = shoup_c(zt[2 * k], q);
     }
+    // inverse stage s: omega^-(k 2^(n-1-s)) = psi^-(k 2^(n-s)) for k < 2^s
+    for (int s = 0; s < logN; s++)
+        for (int k = 0; k < (1 << s); k++) {
+            const u64 e = ((u64)k << (logN - s)) % (2 * (u64)N);
+            const size_t i = (size_t)(1 << s) + k;
+            iw[2 * i] = ipw[e];
+            iw[2 * i + 1] = shoup_c(iw[2 * i], q);
+        }
     void *d = nullptr;
     if (cudaMalloc(&d, tab.size() * 8) != cudaSuccess) { err = "cudaMalloc twiddles"; return false; }
     c->allocs.push_back(d);
@@ -179,12 +190,12 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     M.r64 = (u64)(((u128)1 << 64) % q);
     M.r64s = shoup_c(M.r64, q);
     M.one_s = (u64)(((u128)1 << 64) / q);
-    M.ninv = invmod((u64)N, q);
+    M.ninv = ninv;
     M.ninvs = shoup_c(M.ninv, q);
-    M.fw = (const u64 *)d;
-    M.fws = M.fw + N;
-    M.iw = M.fws + N;
-    M.iws = M.iw + N;
+    M.fw = (const ulonglong2 *)d;
+    M.iw = M.fw + N;
+    M.z = M.iw + N;
+    M.nq = 0 - q;
     c->h_mods.push_back(M);
     return true;
 }
@@ -295,6 +306,39 @@ int build_tables(he_ctx *c, std::string &err) {
         E.delta_q[i] = delta.mod(q);
         E.delta_qs[i] = shoup_c(E.delta_q[i], q);
     }
+    auto fill_conv = [](ConvDev &C, const std::vector<u64> &m) {
+        for (size_t i = 0; i < m.size(); i++) {
+            int sh = __builtin_clzll(m[i]);
+            u64 mp = m[i] << sh;  // in [2^63, 2^64)
+            C.sh[i] = (u64)sh;
+            C.c[i] = (u64)((((u128)1) << 127) / mp);
+        }
+    };
+    fill_conv(E.Qc, c->q);
+    fill_conv(E.Bc, c->aux);
+    for (int j = 0; j < c->K; j++) {
+        const u64 b = c->aux[j];
+        for (int i = 0; i < c->L; i++) {
+            u64 r;
+            E.QhatB[j][i] = Q.div(c->q[i], &r).mod(b);
+            E.QhatBs[j][i] = shoup_c(E.QhatB[j][i], b);
+        }
+        E.Q_bs[j] = shoup_c(E.Q_b[j], b);
+    }
+    for (int i = 0; i < c->L; i++) {
+        const u64 q = c->q[i];
+        for (int j = 0; j < c->K; j++) {
+            u64 r;
+            E.BhatQ[i][j] = Bp.div(c->aux[j], &r).mod(q);
+            E.BhatQs[i][j] = shoup_c(E.BhatQ[i][j], q);
+        }
+        E.B_qs[i] = shoup_c(E.B_q[i], q);
+        u64 r;
+        E.Qhat_t[i] = Q.div(q, &r).mod(t);
+        E.Qhat_ts[i] = shoup_c(E.Qhat_t[i], t);
+    }
+    E.Q_t = Q.mod(t);
+    E.Q_ts = shoup_c(E.Q_t, t);
     E.t = t;
     E.Qhalf_t = Qh.mod(t);
     E.Qinv_t = invmod(Q.mod(t), t);
