@@ -127,6 +127,8 @@ typedef struct he_plan_info {
     int32_t Hn, Wn, Ooff; /* conventional window and kernel offset */
     int32_t O, S;       /* correlated row stride and channel stride */
     int32_t Ho, Wo;
+    int32_t Mn, Sout;   /* output channels per kernel polynomial and their stride */
+    int32_t MG;         /* kernel polynomials per channel group: ceil(M / Mn) */
 } he_plan_info;
 
 typedef struct he_ctx he_ctx;
@@ -168,13 +170,17 @@ int he_sample_masks(he_ctx *ctx, uint64_t seed, int n, uint64_t *out, cudaStream
 int he_pt_sub(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int64_t n, uint64_t *out, cudaStream_t stream);
 
 /* he_conv_plan: window search of Section 3.3 for `encoding`; fails with
- * PLAN_DOES_NOT_FIT when no window fits the ring. */
+ * PLAN_DOES_NOT_FIT when no window fits the ring.  Besides the input window
+ * and channel packing, a plan packs Mn output channels into one kernel
+ * polynomial (as the fully connected protocol the paper builds on packs
+ * matrix rows), so a layer has MG = ceil(M / Mn) kernel polynomials per
+ * channel group; the plan minimises the products MG * G * T per image. */
 int he_conv_plan(he_ctx *ctx, const he_conv_shape *shape, int encoding, he_plan **plan);
 int he_plan_destroy(he_plan *plan);
 int he_plan_query(const he_plan *plan, he_plan_info *info);
 
 /* Encoders (Section 3.3).  role INPUT: tensor [batch][C][H][W] -> polys
- * [batch][T][G][N]; role KERNEL: tensor [M][C][h][h] -> polys [M][G][N]
+ * [batch][T][G][N]; role KERNEL: tensor [M][C][h][h] -> polys [MG][G][N]
  * (batch ignored).  Values are reduced into [0, t).  The plan's encoding
  * must match the entry point. */
 int he_encode_conventional(he_ctx *ctx, const he_plan *plan, int role, const void *tensor, int dtype, int batch,
@@ -182,14 +188,15 @@ int he_encode_conventional(he_ctx *ctx, const he_plan *plan, int role, const voi
 int he_encode_correlated(he_ctx *ctx, const he_plan *plan, int role, const void *tensor, int dtype, int batch,
                          uint64_t *polys, cudaStream_t stream);
 
-/* he_cpmul_conv: CPMul + CCAdd over a plan (Fig. 3(c); Section 3.2 online):
- *   out[b][m][t] = sum_g ct_x[b][t][g] * pt_w[m][g]
- *                + sum_g ct_w[m][g]    * pt_x[b][t][g]
- *                + ct_add[b][m][t]
+/* he_cpmul_conv: CPMul + CCAdd over a plan (Fig. 3(c); Section 3.2 online),
+ * for each kernel polynomial mg < MG:
+ *   out[b][mg][t] = sum_g ct_x[b][t][g] * pt_w[mg][g]
+ *                 + sum_g ct_w[mg][g]    * pt_x[b][t][g]
+ *                 + ct_add[b][mg][t]
  * Each family is skipped when its ciphertext pointer is NULL (at least one
  * must be given); ct_add may be NULL.  Plaintexts in [0,t) are centre-lifted.
- * Shapes: ct_x [batch][T][G][2][L][N], pt_w [M][G][N], ct_w [M][G][2][L][N],
- * pt_x [batch][T][G][N], ct_add / ct_out [batch][M][T][2][L][N].
+ * Shapes: ct_x [batch][T][G][2][L][N], pt_w [MG][G][N], ct_w [MG][G][2][L][N],
+ * pt_x [batch][T][G][N], ct_add / ct_out [batch][MG][T][2][L][N].
  * Runs as one batched forward NTT and one fused MAC -> inverse NTT -> add. */
 int he_cpmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *ct_x, const uint64_t *pt_w,
                   const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add, uint64_t *ct_out,
@@ -207,8 +214,9 @@ int he_cpmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *c
  *  - Scratch: a fixed 32 MiB static device array inside the library (held on
  *    every GPU that loads the library until the process exits).  A call whose
  *    NTT-form operands and term table need more returns
- *    HE_ERR_BUDGET_EXCEEDED and does nothing; the config-sized online layer
- *    (N = 8192, L = 4, 17 input ciphertexts, 16 outputs) needs about 13 MiB.
+ *    HE_ERR_BUDGET_EXCEEDED and does nothing; the online 3x32x32 -> 16 layer
+ *    of one image (N = 8192, L = 4, 9 input ciphertexts, 8 output
+ *    polynomials after output packing) needs about 7 MiB.
  *  - The first call on a device looks up the array's device address once
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Every call on a device shares the one array and overwrites it (each byte
@@ -230,22 +238,22 @@ int he_cpmul_conv_noalloc(he_ctx *ctx, const he_plan *plan, int batch, const uin
 int he_ccmul_precompute(he_ctx *ctx, const he_keys *keys, const uint64_t *ct_a, int n_a, const uint64_t *ct_b,
                         int n_b, const int32_t *pair_a, const int32_t *pair_b, int n_pairs, int group,
                         uint64_t *ct_out, cudaStream_t stream);
-/* The same over a plan: out[b][m][t] = sum_g [r^x][b][t][g] (x) [r^w][m][g]
+/* The same over a plan: out[b][mg][t] = sum_g [r^x][b][t][g] (x) [r^w][mg][g]
  * (the precomputed [r^x r^w] of Section 3.2).  ct_rx [batch][T][G][2][L][N],
- * ct_rw [M][G][2][L][N], out [batch][M][T][2][L][N]. */
+ * ct_rw [MG][G][2][L][N], out [batch][MG][T][2][L][N]. */
 int he_ccmul_conv_precompute(he_ctx *ctx, const he_keys *keys, const he_plan *plan, int batch,
                              const uint64_t *ct_rx, const uint64_t *ct_rw, uint64_t *ct_out, cudaStream_t stream);
 
-/* he_ppmul_conv: PPMul of Section 3.2, p[b][m][t] = sum_g pt_x[b][t][g] *
- * pt_w[m][g] in Z_t[x]/(x^N+1).  pt_x [batch][T][G][N], pt_w [M][G][N],
- * out [batch][M][T][N].  UNSUPPORTED_PARAMS if t is not an NTT prime. */
+/* he_ppmul_conv: PPMul of Section 3.2, p[b][mg][t] = sum_g pt_x[b][t][g] *
+ * pt_w[mg][g] in Z_t[x]/(x^N+1).  pt_x [batch][T][G][N], pt_w [MG][G][N],
+ * out [batch][MG][T][N].  UNSUPPORTED_PARAMS if t is not an NTT prime. */
 int he_ppmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt_x, const uint64_t *pt_w,
                   uint64_t *out, cudaStream_t stream);
 
 /* he_decode (Section 3.3, output positions of each encoding): out[b][m][a][c]
- * = centred((pt - sub)[b][m][tile(a,c)][coef(a,c)] mod t) as int64, centred
- * means v > (t-1)/2 -> v - t.  pt, sub [batch][M][T][N] (sub may be NULL);
- * out [batch][M][Ho][Wo]. */
+ * = centred((pt - sub)[b][m / Mn][tile(a,c)][coef(a,c) + (m mod Mn) Sout]
+ * mod t) as int64, centred means v > (t-1)/2 -> v - t.  pt, sub
+ * [batch][MG][T][N] (sub may be NULL); out [batch][M][Ho][Wo]. */
 int he_decode(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt, const uint64_t *sub, int64_t *out,
               cudaStream_t stream);
 

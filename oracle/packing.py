@@ -25,9 +25,16 @@ Readings where the paper is silent or garbled (each is listed in the design doc):
   R4  correlated windows are chosen over output tiles th x tw; a tile covering
       output rows [a0, a1) encodes input rows [a0-p, a1-p+h-1) clipped to the
       image; O uses the largest tile extent.
-  R5  window objective: minimise (input polynomials per image) = G T, then G,
-      then prefer larger windows; the paper's printed objective is garbled
-      (floors, and W_w + h - 1 where W_w - h + 1 is meant).
+  R5  window objective: minimise the polynomial products per image
+      ceil(M / M_n) G T, then the input polynomials G T, then G, then prefer
+      larger windows; the paper's printed objective is garbled (floors, and
+      W_w + h - 1 where W_w - h + 1 is meant).
+  R6  output packing (the FC layers follow Cheetah, which packs several
+      matrix rows per polynomial): M_n kernels share one polynomial at stride
+      S_out, kernel m at offset (m mod M_n) S_out; S_out is the smallest
+      stride that keeps the other kernels' products off each kernel's
+      requested outputs, and M_n the largest count for which every requested
+      output stays below N and no wrapped term reaches one.
 """
 from __future__ import annotations
 
@@ -60,11 +67,18 @@ class Plan:
     # correlated
     O: int = 0
     S: int = 0
+    # output packing
+    Mn: int = 1
+    Sout: int = 0
     tiles: list = field(default_factory=list)   # (a0, a1, b0, b1, r0, r1, s0, s1) per tile
 
     @property
     def T(self):
         return self.Th * self.Tw
+
+    @property
+    def MG(self):
+        return -(-self.M // self.Mn)
 
     @property
     def Ho(self):
@@ -76,7 +90,27 @@ class Plan:
 
     def key(self):
         return (self.encoding, self.N, self.C, self.H, self.W, self.M, self.h, self.pad, self.Cn, self.G,
-                self.th, self.tw, self.Th, self.Tw, self.Hn, self.Wn, self.Ooff, self.O, self.S)
+                self.th, self.tw, self.Th, self.Tw, self.Hn, self.Wn, self.Ooff, self.O, self.S, self.Mn, self.Sout)
+
+
+def _out_packing(M, N, ranges):
+    """(M_n, S_out) for product spans given as (r_lo, r_hi, D) per tile: r_lo, r_hi
+    the lowest and highest requested coefficient of one kernel's product,
+    D its highest possible degree (before any wrap)."""
+    Sout = max(max(rhi, D - rlo) for (rlo, rhi, D) in ranges) + 1
+    def fits(k):
+        for (rlo, rhi, D) in ranges:
+            if (k - 1) * Sout + rhi >= N:
+                return False
+            tot = (k - 1) * Sout + D
+            if not (tot < N or tot - N < rlo):
+                return False
+        return True
+    k = 1
+    while k < M and fits(k + 1):
+        k += 1
+    G = -(-M // k)
+    return -(-M // G), Sout
 
 
 def _check_shape(C, H, W, M, h, pad):
@@ -84,6 +118,14 @@ def _check_shape(C, H, W, M, h, pad):
         raise ValueError("bad conv shape")
     if H + 2 * pad - h + 1 < 1 or W + 2 * pad - h + 1 < 1:
         raise ValueError("empty output")
+
+
+def _conv_ranges(Cn, Hn, Wn, h, th_list):
+    """requested (r_lo, r_hi) and max degree D of a conventional window product;
+    th_list: (rows, cols) of output per tile"""
+    O = (Cn - 1) * Hn * Wn + (h - 1) * Wn + h - 1
+    D = Cn * Hn * Wn - 1 + O
+    return [(O, O + (a - 1) * Wn + (b - 1), D) for (a, b) in th_list]
 
 
 def plan_conventional(N, C, H, W, M, h, pad) -> Plan:
@@ -101,14 +143,17 @@ def plan_conventional(N, C, H, W, M, h, pad) -> Plan:
                 continue
             th, tw = Hn - h + 1, Wn - h + 1
             Th, Tw = -(-Ho // th), -(-Wo // tw)
-            key = (G * Th * Tw, G, -Hn, -Wn)
+            sizes = {(min(th, Ho - i * th), min(tw, Wo - j * tw)) for i in range(Th) for j in range(Tw)}
+            Mn, Sout = _out_packing(M, N, _conv_ranges(Cn, Hn, Wn, h, sizes))
+            MG = -(-M // Mn)
+            key = (MG * G * Th * Tw, G * Th * Tw, G, -Hn, -Wn)
             if best is None or key < best[0]:
-                best = (key, (Cn, G, Hn, Wn, th, tw, Th, Tw))
+                best = (key, (Cn, G, Hn, Wn, th, tw, Th, Tw, Mn, Sout))
     if best is None:
         raise ValueError("plan does not fit")
-    Cn, G, Hn, Wn, th, tw, Th, Tw = best[1]
+    Cn, G, Hn, Wn, th, tw, Th, Tw, Mn, Sout = best[1]
     p = Plan("conv", N, C, H, W, M, h, pad, Cn, G, th, tw, Th, Tw, Hn=Hn, Wn=Wn,
-             Ooff=(Cn - 1) * Hn * Wn + (h - 1) * Wn + h - 1)
+             Ooff=(Cn - 1) * Hn * Wn + (h - 1) * Wn + h - 1, Mn=Mn, Sout=Sout)
     for ti in range(Th):
         for tj in range(Tw):
             a0, b0 = ti * th, tj * tw
@@ -170,13 +215,17 @@ def plan_correlated(N, C, H, W, M, h, pad) -> Plan:
             G = -(-C // cmax)
             Cn = -(-C // G)
             T = len(tiles)
-            key = (G * T, G, -th, -tw)
+            ranges = [((Cn - 1) * S + rlo, (Cn - 1) * S + rhi, 2 * (Cn - 1) * S + D1) for (rlo, rhi, D1) in geo]
+            Mn, Sout = _out_packing(M, N, ranges)
+            MG = -(-M // Mn)
+            key = (MG * G * T, G * T, G, -th, -tw)
             if best is None or key < best[0]:
-                best = (key, (Cn, G, th, tw, O, S, tiles))
+                best = (key, (Cn, G, th, tw, O, S, tiles, Mn, Sout))
     if best is None:
         raise ValueError("plan does not fit")
-    Cn, G, th, tw, O, S, tiles = best[1]
-    return Plan("corr", N, C, H, W, M, h, pad, Cn, G, th, tw, -(-Ho // th), -(-Wo // tw), O=O, S=S, tiles=tiles)
+    Cn, G, th, tw, O, S, tiles, Mn, Sout = best[1]
+    return Plan("corr", N, C, H, W, M, h, pad, Cn, G, th, tw, -(-Ho // th), -(-Wo // tw), O=O, S=S, Mn=Mn,
+                Sout=Sout, tiles=tiles)
 
 
 def make_plan(encoding, N, C, H, W, M, h, pad) -> Plan:
@@ -210,7 +259,8 @@ def input_slots(p: Plan, t: int, g: int):
 
 
 def kernel_slots(p: Plan, g: int):
-    """(coefficient, channel, k, l) of every weight of kernel poly (any m, group g)."""
+    """(coefficient, channel, k, l) of every weight of the kernel of one output
+    channel in group g, before its output-packing offset (m mod M_n) S_out."""
     out = []
     for cl in range(p.Cn):
         c = g * p.Cn + cl
@@ -252,35 +302,37 @@ def encode_input(p: Plan, x, t_mod) -> np.ndarray:
 
 
 def encode_kernel(p: Plan, w, t_mod) -> np.ndarray:
-    """w: [M, C, h, h] integers -> [M][G][N] uint64 mod t."""
+    """w: [M, C, h, h] integers -> [MG][G][N] uint64 mod t; output channel m
+    sits in polynomial m // M_n at offset (m mod M_n) S_out."""
     w = np.asarray(w)
-    out = np.zeros((p.M, p.G, p.N), dtype=np.uint64)
+    out = np.zeros((p.MG, p.G, p.N), dtype=np.uint64)
     for g in range(p.G):
         slots = kernel_slots(p, g)
         for m in range(p.M):
+            off = (m % p.Mn) * p.Sout
             for (k, c, a, b) in slots:
-                out[m, g, k] = int(w[m, c, a, b]) % t_mod
+                out[m // p.Mn, g, k + off] = int(w[m, c, a, b]) % t_mod
     return out
 
 
 def decode(p: Plan, polys, t_mod) -> np.ndarray:
-    """polys: [M][T][N] mod t -> int64 [M, Ho, Wo], centred (v > t/2 -> v - t)."""
+    """polys: [MG][T][N] mod t -> int64 [M, Ho, Wo], centred (v > t/2 -> v - t)."""
     polys = np.asarray(polys)
     out = np.zeros((p.M, p.Ho, p.Wo), dtype=np.int64)
     for t in range(p.T):
         for (k, a, b) in output_slots(p, t):
             for m in range(p.M):
-                v = int(polys[m, t, k])
+                v = int(polys[m // p.Mn, t, k + (m % p.Mn) * p.Sout])
                 out[m, a, b] = v - t_mod if v > (t_mod - 1) // 2 else v
     return out
 
 
-def product_terms(p: Plan, encrypted: str = "input"):
-    """Term lists of the polynomial products: output (m, t) = sum_g in(t,g) * ker(m,g).
-    Returns, per output o = m*T + t, the list of (input poly index t*G+g,
-    kernel poly index m*G+g)."""
+def product_terms(p: Plan):
+    """Term lists of the polynomial products: output (mg, t) = sum_g in(t,g) *
+    ker(mg,g).  Returns, per output o = mg*T + t, the list of (input poly
+    index t*G+g, kernel poly index mg*G+g)."""
     terms = []
-    for m in range(p.M):
+    for mg in range(p.MG):
         for t in range(p.T):
-            terms.append([(t * p.G + g, m * p.G + g) for g in range(p.G)])
+            terms.append([(t * p.G + g, mg * p.G + g) for g in range(p.G)])
     return terms

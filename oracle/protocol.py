@@ -23,16 +23,16 @@ class LayerRun:
     plan: packing.Plan
     keys: he.Keys
     x_polys: np.ndarray      # [T*G][N]
-    w_polys: np.ndarray      # [M*G][N]
+    w_polys: np.ndarray      # [MG*G][N]
     r_x: np.ndarray
     r_w: np.ndarray
     ct_x: np.ndarray
     ct_w: np.ndarray
     ct_rx: np.ndarray
     ct_rw: np.ndarray
-    rr: np.ndarray           # [M*T][2][L][N] precomputed [r^x r^w]
-    out: np.ndarray          # [M*T][2][L][N] online result c
-    p: np.ndarray            # [M*T][N] PPMul result
+    rr: np.ndarray           # [B*MG*T][2][L][N] precomputed [r^x r^w]
+    out: np.ndarray          # [B*MG*T][2][L][N] online result c
+    p: np.ndarray            # [B*MG*T][N] PPMul result
     y: np.ndarray            # decoded [M, Ho, Wo]
 
 
@@ -41,7 +41,7 @@ def precompute_pairs(plan, batch=1):
     (b, m, t) in that order; rx index (b*T + t)*G + g, rw index m*G + g."""
     pairs = []
     for b in range(batch):
-        for m in range(plan.M):
+        for m in range(plan.MG):
             for t in range(plan.T):
                 for g in range(plan.G):
                     pairs.append(((b * plan.T + t) * plan.G + g, m * plan.G + g))
@@ -51,10 +51,10 @@ def precompute_pairs(plan, batch=1):
 def online_terms(plan, batch=1):
     """CPMul terms over ct = [ct_x ; ct_w] and pt = [(w - r^w) ; (x - r^x)],
     output order (b, m, t)."""
-    TG, MG = plan.T * plan.G, plan.M * plan.G
+    TG, MG = plan.T * plan.G, plan.MG * plan.G
     terms = []
     for b in range(batch):
-        for m in range(plan.M):
+        for m in range(plan.MG):
             for t in range(plan.T):
                 tl = []
                 for g in range(plan.G):
@@ -68,7 +68,7 @@ def online_terms(plan, batch=1):
 def ppmul_terms(plan, batch=1):
     terms = []
     for b in range(batch):
-        for m in range(plan.M):
+        for m in range(plan.MG):
             for t in range(plan.T):
                 terms.append([((b * plan.T + t) * plan.G + g, m * plan.G + g) for g in range(plan.G)])
     return terms
@@ -105,7 +105,7 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
     p = he.ppmul_terms(P, xm, wm, ppmul_terms(plan, B))
     dec = he.decrypt(P, keys, out)
     z = (dec + (tt - p)) % tt
-    zz = z.reshape(B, plan.M, plan.T, P.N)
+    zz = z.reshape(B, plan.MG, plan.T, P.N)
     y = np.stack([packing.decode(plan, zz[b], t) for b in range(B)])
     if B == 1:
         y = y[0]

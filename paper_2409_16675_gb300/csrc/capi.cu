@@ -424,7 +424,7 @@ static int encode_common(he_ctx *c, const he_plan *p, int enc, int role, const v
         return launch_encode(c, p->in_map, TG, TG, tensor, dtype, (long long)s.C * s.H * s.W, batch, TG, polys, st);
     }
     if (role == HE_ROLE_KERNEL)
-        return launch_encode_kernel(c, p->ker_map, p->info.G, s.M, tensor, dtype, (long long)s.C * s.h * s.h, polys, st);
+        return launch_encode_kernel(c, p->ker_map, p->info.G, p->info.MG, tensor, dtype, 0, polys, st);
     return fail(c, HE_ERR_INVALID_ARG, "bad role");
 }
 
@@ -445,7 +445,7 @@ int he_cpmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x, 
     if ((ct_x && !pt_w) || (ct_w && !pt_x)) return fail(c, HE_ERR_INVALID_ARG, "missing plaintext operand");
     if (!batch) return HE_OK;
     TRY(set_device(c));
-    const int N = c->N, L = c->L, T = p->info.T, G = p->info.G, M = p->s.M;
+    const int N = c->N, L = c->L, T = p->info.T, G = p->info.G, M = p->info.MG;
     const size_t LN = (size_t)L * N;
     const long long nX = ct_x ? (long long)batch * T * G * 2 : 0;   // ct polys (components)
     const long long nW = ct_w ? (long long)M * G * 2 : 0;
@@ -569,7 +569,7 @@ int he_ccmul_conv_precompute(he_ctx *c, const he_keys *k, const he_plan *p, int 
                              const uint64_t *ct_rw, uint64_t *ct_out, cudaStream_t st) {
     if (!c || !p || batch < 0) return HE_ERR_INVALID_ARG;
     if (!batch) return HE_OK;
-    const int T = p->info.T, G = p->info.G, M = p->s.M;
+    const int T = p->info.T, G = p->info.G, M = p->info.MG;
     std::vector<int32_t> pa, pb;
     for (int b = 0; b < batch; b++)
         for (int m = 0; m < M; m++)
@@ -586,7 +586,7 @@ int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, 
     if (c->t_mod < 0) return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "t is not an NTT prime for this N");
     if (!batch) return HE_OK;
     TRY(set_device(c));
-    const int N = c->N, T = p->info.T, G = p->info.G, M = p->s.M;
+    const int N = c->N, T = p->info.T, G = p->info.G, M = p->info.MG;
     const long long nX = (long long)batch * T * G, nW = (long long)M * G;
     TRY(ws_reserve(c, Carver::round((nX + nW) * N * 8) + 4096));
     Carver cv(c->ws);
@@ -615,7 +615,8 @@ int he_decode(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt, const 
               cudaStream_t st) {
     if (!c || !p || batch < 0 || (batch && (!pt || !out))) return HE_ERR_INVALID_ARG;
     TRY(set_device(c));
-    return launch_decode(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.T, batch, pt, sub, out, st);
+    return launch_decode(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.MG * p->info.T, batch, pt, sub, out,
+                         st);
 }
 
 int he_trace_enable(he_ctx *c, int on) {

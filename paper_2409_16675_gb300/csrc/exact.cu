@@ -316,26 +316,25 @@ __global__ void k_encode_input(const int32_t *__restrict__ map, int n_polys, int
     out[b * out_batch_polys * N + r] = idx >= 0 ? to_t(tensor, dtype, b * tensor_stride + idx, t) : 0;
 }
 
-// kernel role: out[(m*G + g)*N + x] = w[m*per_m + map[g*N + x]] mod t
+// kernel role: out[(mg*G + g)*N + x] = w[map[(mg*G + g)*N + x]] mod t (absolute index into w)
 __global__ void k_encode_kernel(const int32_t *__restrict__ map, int G, int M, int N, const void *tensor, int dtype,
                                 long long per_m, u64 *__restrict__ out, u64 t) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long per = (long long)G * N;
-    if (gid >= per * M) return;
-    const long long m = gid / per;
-    const long long r = gid - m * per;
-    const int idx = map[r];
-    out[gid] = idx >= 0 ? to_t(tensor, dtype, m * per_m + idx, t) : 0;
+    if (gid >= (long long)G * N * M) return;
+    (void)per_m;
+    const int idx = map[gid];
+    out[gid] = idx >= 0 ? to_t(tensor, dtype, idx, t) : 0;
 }
 
-// out[(b*M + m)*HW + i] = centred((pt - sub)[((b*M + m)*T)*N + map[i]] mod t)
-__global__ void k_decode(const int32_t *__restrict__ map, int HW, int M, int T, int N, int batch,
+// out[(b*M + m)*HW + i] = centred((pt - sub)[b*polys*N + map[m*HW + i]] mod t),
+// polys = MG*T product polynomials per image
+__global__ void k_decode(const int32_t *__restrict__ map, int HW, int M, int polys, int N, int batch,
                          const u64 *__restrict__ pt, const u64 *__restrict__ sub, long long *__restrict__ out, u64 t) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)batch * M * HW) return;
-    const int i = (int)(gid % HW);
-    const long long bm = gid / HW;
-    const long long src = bm * T * N + map[i];
+    const long long mi = gid % ((long long)M * HW);
+    const long long b = gid / ((long long)M * HW);
+    const long long src = b * polys * N + map[mi];
     u64 v = pt[src];
     v = v >= t ? v % t : v;
     if (sub) {
@@ -380,11 +379,11 @@ int launch_encode_kernel(he_ctx *c, const int32_t *map, int G, int M, const void
     return cuda_check(c, cudaGetLastError(), "k_encode_kernel");
 }
 
-int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int T, int batch, const u64 *pt, const u64 *sub,
+int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int polys, int batch, const u64 *pt, const u64 *sub,
                   int64_t *out, cudaStream_t st) {
     const long long total = (long long)batch * M * HW;
     if (!total) return HE_OK;
-    k_decode<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, HW, M, T, c->N, batch, pt, sub,
+    k_decode<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, HW, M, polys, c->N, batch, pt, sub,
                                                                (long long *)out, c->P.t);
     return cuda_check(c, cudaGetLastError(), "k_decode");
 }

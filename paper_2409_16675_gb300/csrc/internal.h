@@ -119,8 +119,8 @@ struct he_plan {
     std::vector<int> tiles;
     // device index maps
     int32_t *in_map = nullptr;   // [T*G][N] -> index into one image [C][H][W], -1 = zero
-    int32_t *ker_map = nullptr;  // [G][N]   -> index into w[m] ([C][h][h]), -1 = zero
-    int32_t *out_map = nullptr;  // [Ho*Wo]  -> t*N + coefficient
+    int32_t *ker_map = nullptr;  // [MG][G][N] -> index into w [M][C][h][h], -1 = zero
+    int32_t *out_map = nullptr;  // [M][Ho*Wo] -> (mg*T + t)*N + coefficient
     // host copies for tests of the plan
     std::vector<int32_t> h_in_map, h_ker_map, h_out_map;
 };
@@ -210,7 +210,7 @@ int launch_encode(he_ctx *c, const int32_t *map, int n_polys, int map_polys, con
                   long long tensor_stride, int batch, long long out_batch_polys, u64 *out, cudaStream_t st);
 int launch_encode_kernel(he_ctx *c, const int32_t *map, int G, int M, const void *tensor, int dtype,
                          long long per_m, u64 *out, cudaStream_t st);
-int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int T, int batch, const u64 *pt, const u64 *sub,
+int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int polys, int batch, const u64 *pt, const u64 *sub,
                   int64_t *out, cudaStream_t st);
 int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, cudaStream_t st);
 int launch_copy_sk(he_ctx *c, const int8_t *s8, u64 *sk, cudaStream_t st);

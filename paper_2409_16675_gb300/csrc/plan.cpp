@@ -14,10 +14,16 @@
 // off the requested outputs; C_n is the largest count for which the requested
 // outputs stay below N and no wrapped (x^N = -1) term lands on them.
 //
-// Window choice: minimise the number of input polynomials per image G*T
-// (= polynomial products per output channel), then G, then prefer the larger
-// window.  The paper's objective is printed with floors and W_w + h - 1 in a
-// denominator; this is the reading used everywhere in the library.
+// Output packing: Mn kernels share one polynomial at stride Sout (kernel m at
+// offset (m mod Mn) Sout), Sout being the smallest stride that keeps the
+// other kernels' products off a kernel's requested outputs and Mn the largest
+// count for which every requested output stays below N and no wrapped term
+// lands on one.
+//
+// Window choice: minimise the polynomial products per image MG*G*T, then the
+// input polynomials G*T, then G, then prefer the larger window.  The paper's
+// objective is printed with floors and W_w + h - 1 in a denominator; this is
+// the reading used everywhere in the library.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -27,11 +33,31 @@
 namespace he {
 
 struct Tile { int a0, a1, b0, b1, r0, r1, s0, s1; };
+struct Span { long long rlo, rhi, D; };  // requested range and highest degree of one product
+
+// (Mn, Sout) for the given product spans
+static void out_packing(int M, long long N, const std::vector<Span> &sp, int &Mn, long long &Sout) {
+    Sout = 0;
+    for (const Span &e : sp) Sout = std::max(Sout, std::max(e.rhi, e.D - e.rlo));
+    Sout += 1;
+    auto fits = [&](long long k) {
+        for (const Span &e : sp) {
+            if ((k - 1) * Sout + e.rhi >= N) return false;
+            const long long tot = (k - 1) * Sout + e.D;
+            if (!(tot < N || tot - N < e.rlo)) return false;
+        }
+        return true;
+    };
+    int k = 1;
+    while (k < M && fits(k + 1)) k++;
+    const int G = (M + k - 1) / k;
+    Mn = (M + G - 1) / G;
+}
 
 static bool conv_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
     const int Hp = s.H + 2 * s.pad, Wp = s.W + 2 * s.pad;
     const int Ho = Hp - s.h + 1, Wo = Wp - s.h + 1;
-    long long best[4] = {LLONG_MAX, 0, 0, 0};
+    long long best[5] = {LLONG_MAX, 0, 0, 0, 0};
     bool found = false;
     for (int G = 1; G <= s.C; G++) {
         const int Cn = (s.C + G - 1) / G;
@@ -41,11 +67,24 @@ static bool conv_search(int N, const he_conv_shape &s, he_plan_info &I, std::vec
             if ((long long)Cn * Hn * Wn > N) continue;
             const int th = Hn - s.h + 1, tw = Wn - s.h + 1;
             const int Th = (Ho + th - 1) / th, Tw = (Wo + tw - 1) / tw;
-            long long key[4] = {(long long)G * Th * Tw, G, -Hn, -Wn};
-            if (!found || std::lexicographical_compare(key, key + 4, best, best + 4)) {
-                std::copy(key, key + 4, best);
+            const long long O = (long long)(Cn - 1) * Hn * Wn + (long long)(s.h - 1) * Wn + s.h - 1;
+            const long long D = (long long)Cn * Hn * Wn - 1 + O;
+            std::vector<Span> sp;
+            for (int i = 0; i < Th; i++)
+                for (int j = 0; j < Tw; j++) {
+                    const int a = std::min(th, Ho - i * th), b = std::min(tw, Wo - j * tw);
+                    sp.push_back({O, O + (long long)(a - 1) * Wn + (b - 1), D});
+                }
+            int Mn;
+            long long Sout;
+            out_packing(s.M, N, sp, Mn, Sout);
+            const long long MG = (s.M + Mn - 1) / Mn;
+            long long key[5] = {MG * G * Th * Tw, (long long)G * Th * Tw, G, -Hn, -Wn};
+            if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
+                std::copy(key, key + 5, best);
                 found = true;
                 I.Cn = Cn; I.G = G; I.Hn = Hn; I.Wn = Wn; I.th = th; I.tw = tw; I.Th = Th; I.Tw = Tw;
+                I.Mn = Mn; I.Sout = (int)Sout;
             }
         }
     }
@@ -102,7 +141,7 @@ static bool corr_fits(long long c, long long S, const std::vector<Geo> &g, long 
 
 static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
     const int Ho = s.H + 2 * s.pad - s.h + 1, Wo = s.W + 2 * s.pad - s.h + 1;
-    long long best[4] = {LLONG_MAX, 0, 0, 0};
+    long long best[5] = {LLONG_MAX, 0, 0, 0, 0};
     bool found = false;
     std::vector<Tile> tl;
     std::vector<Geo> g;
@@ -116,12 +155,20 @@ static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vec
             while (cmax < s.C && corr_fits(cmax + 1, S, g, N)) cmax++;
             const int G = (s.C + cmax - 1) / cmax;
             const int Cn = (s.C + G - 1) / G;
-            long long key[4] = {(long long)G * (long long)tl.size(), G, -th, -tw};
-            if (!found || std::lexicographical_compare(key, key + 4, best, best + 4)) {
-                std::copy(key, key + 4, best);
+            std::vector<Span> sp;
+            for (const Geo &e : g)
+                sp.push_back({(Cn - 1) * S + e.rlo, (Cn - 1) * S + e.rhi, 2 * (long long)(Cn - 1) * S + e.D1});
+            int Mn;
+            long long Sout;
+            out_packing(s.M, N, sp, Mn, Sout);
+            const long long MG = (s.M + Mn - 1) / Mn;
+            long long key[5] = {MG * G * (long long)tl.size(), (long long)G * (long long)tl.size(), G, -th, -tw};
+            if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
+                std::copy(key, key + 5, best);
                 found = true;
                 I.Cn = Cn; I.G = G; I.th = th; I.tw = tw; I.O = (int)O; I.S = (int)S;
                 I.Th = (Ho + th - 1) / th; I.Tw = (Wo + tw - 1) / tw;
+                I.Mn = Mn; I.Sout = (int)Sout;
                 tiles = tl;
             }
         }
@@ -155,10 +202,12 @@ int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std:
         p->tiles.insert(p->tiles.end(), v, v + 8);
     }
     // index maps
-    const int T = I.T, G = I.G, Cn = I.Cn;
+    I.MG = (s.M + I.Mn - 1) / I.Mn;
+    p->info = I;
+    const int T = I.T, G = I.G, Cn = I.Cn, MG = I.MG, HW = I.Ho * I.Wo;
     p->h_in_map.assign((size_t)T * G * N, -1);
-    p->h_ker_map.assign((size_t)G * N, -1);
-    p->h_out_map.assign((size_t)I.Ho * I.Wo, -1);
+    p->h_ker_map.assign((size_t)MG * G * N, -1);
+    p->h_out_map.assign((size_t)s.M * HW, -1);
     for (int ti = 0; ti < T; ti++) {
         const Tile &t = tiles[ti];
         for (int g = 0; g < G; g++) {
@@ -188,23 +237,27 @@ int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std:
                     const long long u = a - s.pad - t.r0 + s.h - 1, v = b - s.pad - t.s0 + s.h - 1;
                     coef = (long long)(Cn - 1) * I.S + u * I.O + v;
                 }
-                p->h_out_map[(size_t)a * I.Wo + b] = (int32_t)(ti * N + coef);
+                for (int mo = 0; mo < s.M; mo++)
+                    p->h_out_map[(size_t)mo * HW + (size_t)a * I.Wo + b] =
+                        (int32_t)(((long long)(mo / I.Mn) * T + ti) * N + coef + (long long)(mo % I.Mn) * I.Sout);
             }
     }
-    for (int g = 0; g < G; g++) {
-        int32_t *m = p->h_ker_map.data() + (size_t)g * N;
-        for (int cl = 0; cl < Cn; cl++) {
-            const int ch = g * Cn + cl;
-            if (ch >= s.C) break;
-            for (int k = 0; k < s.h; k++)
-                for (int l = 0; l < s.h; l++) {
-                    long long coef = encoding == HE_ENC_CONVENTIONAL
-                        ? (long long)I.Ooff - (long long)cl * I.Hn * I.Wn - (long long)k * I.Wn - l
-                        : (long long)(Cn - 1 - cl) * I.S + (long long)(s.h - 1 - k) * I.O + (s.h - 1 - l);
-                    m[coef] = (ch * s.h + k) * s.h + l;
-                }
+    for (int mo = 0; mo < s.M; mo++)
+        for (int g = 0; g < G; g++) {
+            int32_t *m = p->h_ker_map.data() + ((size_t)(mo / I.Mn) * G + g) * N;
+            const long long off = (long long)(mo % I.Mn) * I.Sout;
+            for (int cl = 0; cl < Cn; cl++) {
+                const int ch = g * Cn + cl;
+                if (ch >= s.C) break;
+                for (int k = 0; k < s.h; k++)
+                    for (int l = 0; l < s.h; l++) {
+                        long long coef = encoding == HE_ENC_CONVENTIONAL
+                            ? (long long)I.Ooff - (long long)cl * I.Hn * I.Wn - (long long)k * I.Wn - l
+                            : (long long)(Cn - 1 - cl) * I.S + (long long)(s.h - 1 - k) * I.O + (s.h - 1 - l);
+                        m[coef + off] = ((mo * s.C + ch) * s.h + k) * s.h + l;
+                    }
+            }
         }
-    }
     // upload
     auto up = [&](const std::vector<int32_t> &h, int32_t **d) -> bool {
         if (cudaMalloc((void **)d, h.size() * 4) != cudaSuccess) return false;

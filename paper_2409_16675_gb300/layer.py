@@ -72,7 +72,7 @@ class Plan:
         self.ctx, self.shape, self.encoding = ctx, shape, encoding
         self.h = nv.he_conv_plan(ctx.h, shape.C, shape.H, shape.W, shape.M, shape.h, shape.pad, ENC[encoding])
         self.info = nv.he_plan_query(self.h)
-        self.T, self.G = self.info.T, self.info.G
+        self.T, self.G, self.MG = self.info.T, self.info.G, self.info.MG
 
     def encode_input(self, x, batch, out):
         f = nv.he_encode_conventional if self.encoding == "conv" else nv.he_encode_correlated
@@ -113,7 +113,7 @@ class PLayer:
     def __init__(self, ctx: Context, keys: Keys, plan: Plan, batch: int):
         self.ctx, self.keys, self.plan, self.B = ctx, keys, plan, batch
         c, s = ctx, plan.shape
-        nx, nw, no = batch * plan.T * plan.G, s.M * plan.G, batch * s.M * plan.T
+        nx, nw, no = batch * plan.T * plan.G, plan.MG * plan.G, batch * plan.MG * plan.T
         self.nx, self.nw, self.no = nx, nw, no
         self.buf = LayerBuffers(
             xp=c.u64(nx, c.N), wp=c.u64(nw, c.N), r_x=c.u64(nx, c.N), r_w=c.u64(nw, c.N),

@@ -55,7 +55,7 @@ class he_trace_entry(ctypes.Structure):
 
 class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("encoding", "Cn", "G", "th", "tw", "Th", "Tw", "T", "Hn", "Wn",
-                                              "Ooff", "O", "S", "Ho", "Wo")]
+                                              "Ooff", "O", "S", "Ho", "Wo", "Mn", "Sout", "MG")]
 
 
 def _load():

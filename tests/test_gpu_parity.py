@@ -109,12 +109,15 @@ def test_masks_bits(name):
 
 
 SHAPES = [
-    # (C, H, W, M, h, pad) -- several tiles / groups at small N, ragged tails
+    # (C, H, W, M, h, pad) -- several tiles / groups at small N, ragged tails,
+    # packed output channels (small images, fully connected shapes)
     (3, 12, 11, 2, 3, 1),
     (5, 20, 17, 3, 3, 2),
     (2, 7, 9, 2, 5, 4),
     (4, 1, 1, 3, 1, 0),
     (1, 28, 28, 4, 3, 0),
+    (40, 1, 1, 37, 1, 0),
+    (3, 4, 5, 11, 3, 1),
 ]
 
 
@@ -127,6 +130,7 @@ def test_plan_and_encoding_match_oracle(enc, shape):
     op = packing.make_plan(enc, c.N, C, H, W, M, h, pad)
     i = pl.info
     assert (i.Cn, i.G, i.th, i.tw, i.Th, i.Tw, i.T) == (op.Cn, op.G, op.th, op.tw, op.Th, op.Tw, op.T)
+    assert (i.Mn, i.MG) == (op.Mn, op.MG) and (op.Mn == 1 or i.Sout == op.Sout)
     if enc == "conv":
         assert (i.Hn, i.Wn, i.Ooff) == (op.Hn, op.Wn, op.Ooff)
     else:
@@ -135,7 +139,7 @@ def test_plan_and_encoding_match_oracle(enc, shape):
     x = wl.activations(11, (B, C, H, W))
     w = wl.weights(12, (M, C, h, h))
     xp = c.u64(B * op.T * op.G, c.N)
-    wp = c.u64(M * op.G, c.N)
+    wp = c.u64(op.MG * op.G, c.N)
     pl.encode_input(cuda(x), B, xp)
     pl.encode_kernel(cuda(w), wp)
     want_x = np.concatenate([packing.encode_input(op, x[b], c.t).reshape(-1, c.N) for b in range(B)])
@@ -143,8 +147,8 @@ def test_plan_and_encoding_match_oracle(enc, shape):
     assert np.array_equal(to_np(wp), packing.encode_kernel(op, w, c.t).reshape(-1, c.N))
     # decode: random polys, with a subtracted operand
     rng = np.random.default_rng(1)
-    z = rng.integers(0, c.t, (B, M, op.T, c.N), dtype=np.uint64)
-    s = rng.integers(0, c.t, (B, M, op.T, c.N), dtype=np.uint64)
+    z = rng.integers(0, c.t, (B, op.MG, op.T, c.N), dtype=np.uint64)
+    s = rng.integers(0, c.t, (B, op.MG, op.T, c.N), dtype=np.uint64)
     y = torch.empty((B, M, op.Ho, op.Wo), dtype=torch.int64, device="cuda")
     nv.he_decode(c.h, pl.h, B, cuda(z), cuda(s), y)
     tt = np.uint64(c.t)
@@ -162,7 +166,7 @@ def test_cpmul_conv_bits(name, families):
     ok = he.keygen(P, 5, False)
     shape = wl.ConvShape(5, 20, 17, 3, 3, 2) if c.N == 1024 else wl.ConvShape(16, 32, 32, 4, 3, 1)
     pl = layer.Plan(c, shape, "corr")
-    T, G, M, B = pl.T, pl.G, shape.M, 2
+    T, G, M, B = pl.T, pl.G, pl.MG, 2
     nx, nw = B * T * G, M * G
     rng = np.random.default_rng(3)
     mx = rng.integers(0, c.t, (nx, c.N), dtype=np.uint64)
@@ -217,7 +221,7 @@ def test_ppmul_bits(name):
     c = ctx_for(name)
     P = oparams(c)
     pl = layer.Plan(c, wl.ConvShape(3, 12, 11, 2, 3, 1) if c.N < 4096 else wl.ConvShape(3, 32, 32, 3, 3, 1), "conv")
-    T, G, M, B = pl.T, pl.G, pl.shape.M, 2
+    T, G, M, B = pl.T, pl.G, pl.MG, 2
     rng = np.random.default_rng(9)
     px = rng.integers(0, c.t, (B * T * G, c.N), dtype=np.uint64)
     pw = rng.integers(0, c.t, (M * G, c.N), dtype=np.uint64)

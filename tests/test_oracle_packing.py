@@ -89,6 +89,8 @@ def shapes():
         N = int(rng.choice([64, 128, 256, 512]))
         out.append((N, C, H, W, 2, h, pad))
     out += [(64, 3, 8, 8, 2, 3, 1), (128, 1, 9, 5, 2, 5, 4), (64, 2, 4, 11, 1, 2, 0), (256, 4, 1, 1, 3, 1, 0)]
+    # output packing: fully connected shapes and small images with many output channels
+    out += [(256, 10, 1, 1, 40, 1, 0), (128, 3, 1, 1, 50, 1, 0), (512, 4, 3, 3, 9, 3, 1), (256, 2, 2, 3, 7, 2, 1)]
     return out
 
 
@@ -106,8 +108,8 @@ def test_packed_products_equal_bruteforce_conv(enc, shape):
     t = 1 << 40
     xs = packing.encode_input(p, x, t)
     ws = packing.encode_kernel(p, w, t)
-    prod = np.zeros((M, p.T, N), dtype=np.uint64)
-    for m in range(M):
+    prod = np.zeros((p.MG, p.T, N), dtype=np.uint64)
+    for m in range(p.MG):
         for tt in range(p.T):
             acc = [0] * N
             for g in range(p.G):
@@ -119,6 +121,8 @@ def test_packed_products_equal_bruteforce_conv(enc, shape):
     # every output is decoded exactly once
     seen = [(a, b) for tt in range(p.T) for (_, a, b) in packing.output_slots(p, tt)]
     assert len(seen) == len(set(seen)) == p.Ho * p.Wo
+    if shape[2] == 1 and shape[3] == 1 and M > 8:
+        assert p.Mn > 1                     # FC shapes pack several output channels
 
 
 def test_plan_search_prefers_fewest_products():

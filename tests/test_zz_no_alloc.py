@@ -22,7 +22,7 @@ def _operands(c, plan, B, seed):
     """Random ciphertexts / plaintexts of the right shapes (fresh encryptions
     are not needed to compare two implementations of the same product)."""
     rng = np.random.default_rng(seed)
-    T, G, M = plan.T, plan.G, plan.shape.M
+    T, G, M = plan.T, plan.G, plan.MG
     nx, nw, no = B * T * G, M * G, B * M * T
 
     def ct(n):
@@ -69,8 +69,8 @@ def test_noalloc_matches_allocating_entry_point(ring, shape, enc, B):
 def test_noalloc_refuses_oversize_calls():
     c = layer.Context(wl.RING_MID)
     plan = layer.Plan(c, wl.CONV_MID.shape, "corr")
-    B = 64                                       # about 270 MiB of NTT-form operands
-    T, G, M = plan.T, plan.G, plan.shape.M
+    B = 64                                       # about 34 MiB of NTT-form operands
+    T, G, M = plan.T, plan.G, plan.MG
     x = c.ct(B * T * G)
     out = c.ct(B * M * T)
     with pytest.raises(nv.HEError) as e:
