@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="layer", choices=["layer", "train"],
+                    help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
+                         "train: one CNN training step's eight linear operations, batch 64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -283,10 +286,53 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
+def run_train(args):
+    """Training steps per second: the eight homomorphic linear operations of one
+    step of the 1x28x28 CNN (conv 1->16, conv 16->32, FC 512->10; forward,
+    input and weight gradients), batch 64, N = 8192, 4 x 50-bit limbs, 40-bit t,
+    with the OT non-linear layers simulated in plaintext."""
+    import numpy as np
+    import torch
+
+    from paper_2409_16675_gb300 import layer, training, workloads as wl
+
+    B = 64
+    spec = training.CNNSpec()
+    ctx = layer.Context(wl.RING_TRAIN)
+    keys = layer.Keys(ctx, 7, True)
+    tr = training.HETrainer(ctx, keys, B, spec)
+    rng = np.random.default_rng(wl.MASTER_SEED + 3)
+    x0 = torch.from_numpy(rng.integers(0, 256, (B, 1, 28, 28), dtype=np.uint8)).cuda()
+    w1 = torch.from_numpy(rng.integers(-8, 8, (spec.c1, 1, 3, 3), dtype=np.int8)).cuda()
+    w2 = torch.from_numpy(rng.integers(-8, 8, (spec.c2, spec.c1, 3, 3), dtype=np.int8)).cuda()
+    w3 = torch.from_numpy(rng.integers(-8, 8, (spec.n_out, spec.fc_in), dtype=np.int8)).cuda()
+    lab = torch.from_numpy(rng.integers(0, 10, (B,), dtype=np.int64)).cuda()
+    for i in range(args.warmup):
+        tr.step(x0, w1, w2, w3, lab, seed=100 * i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record()
+        for i in range(args.steps):
+            tr.step(x0, w1, w2, w3, lab, seed=100 * (args.warmup + i))
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "encrypted CNN training steps/s (linear layers, batch 64)", "value": 1000.0 / ms,
+                      "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+                      "config": {"workload": "cnn_train_step_b64_N8192", "batch": B,
+                                 "products_per_step": tr.products()},
+                      "clocks": clk.summary()}), flush=True)
+    tr.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "train":
+        run_train(args)
     else:
         run_gpu(args)
 
