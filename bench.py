@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="layer", choices=["layer", "train"],
+    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched"],
                     help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
-                         "train: one CNN training step's eight linear operations, batch 64")
+                         "train: one CNN training step's eight linear operations, batch 64; "
+                         "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -327,8 +328,69 @@ def run_train(args):
     tr.close()
 
 
+def run_batched(args):
+    """256 ct x pt convolution jobs of uneven shapes (channels {3,16,32,64,128},
+    spatial {8,16,32}, kernel {1,3,5}), N in {4096, 8192}, 2-5 limbs of 36-60
+    bits, both encodings: jobs per second as one call per job (plain), as
+    persistent queue kernels, and replayed from a CUDA graph, after the
+    autotuner has picked the launch configuration."""
+    import torch
+
+    from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
+
+    jobs = wl.batched_jobs()
+    ctxs, items = {}, []
+    for j in jobs:
+        key = (j.ring.N, j.ring.prime_bits)
+        if key not in ctxs:
+            ctxs[key] = layer.Context(j.ring)
+        c = ctxs[key]
+        p = layer.Plan(c, j.shape, j.encoding)
+        g = torch.Generator(device="cuda").manual_seed(j.seed)
+        nx, nw = p.T * p.G, p.MG * p.G
+        ct = torch.empty((nx, 2, c.L, c.N), dtype=torch.int64, device="cuda")
+        for i, q in enumerate(c.q):
+            ct[:, :, i, :] = torch.randint(0, q, (nx, 2, c.N), generator=g, device="cuda", dtype=torch.int64)
+        pt = torch.randint(0, c.t, (nw, c.N), generator=g, device="cuda", dtype=torch.int64)
+        items.append((c, p, ct.view(torch.uint64), pt.view(torch.uint64), c.ct(p.MG * p.T)))
+    b = nv.he_batch_create(0)
+    for (c, p, ct, pt, out) in items:
+        nv.he_batch_add_cpmul(b, c.h, p.h, 1, ct, pt, None, out)
+    nv.he_batch_prepare(b)
+    s = torch.cuda.Stream()
+    res, outs = {}, {}
+    with torch.cuda.stream(s):
+        tuning = nv.he_batch_autotune(b)
+        for name, mode in (("plain", nv.HE_BATCH_PLAIN), ("persistent", nv.HE_BATCH_PERSISTENT),
+                           ("graph", nv.HE_BATCH_GRAPH)):
+            for _ in range(max(1, args.warmup)):
+                nv.he_batch_run(b, mode)
+            s.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(args.steps):
+                nv.he_batch_run(b, mode)
+            e1.record(s)
+            s.synchronize()
+            res[name] = e0.elapsed_time(e1) / args.steps
+            outs[name] = [it[4][:1].clone() for it in items[::16]]
+    same = all(torch.equal(a, r) for m in outs for a, r in zip(outs[m], outs["plain"]))
+    print(json.dumps({"metric": "batched ct x pt conv jobs/s (256 uneven jobs)", "unit": "jobs/s",
+                      "value": len(jobs) / (res["graph"] / 1000.0), "higher_is_better": True,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "u64", "data": "synthetic",
+                      "ms_per_batch": res, "jobs_per_s": {k: len(jobs) / (v / 1000.0) for k, v in res.items()},
+                      "speedup_vs_plain": {k: res["plain"] / v for k, v in res.items()},
+                      "identical_results": bool(same), "autotune": tuning, "contexts": len(ctxs),
+                      "config": {"workload": "256 uneven conv jobs, N 4096/8192, 2-5 limbs of 36-60 bits"}}),
+          flush=True)
+    nv.he_batch_destroy(b)
+
+
 def main():
     args = parse()
+    if args.workload == "batched":
+        run_batched(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "train":

@@ -257,6 +257,56 @@ int he_ppmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *p
 int he_decode(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt, const uint64_t *sub, int64_t *out,
               cudaStream_t stream);
 
+/* ------------------------------------------------------------------
+ * Batched execution of many heterogeneous CPMul convolutions (an execution
+ * form of he_cpmul_conv; the paper has no counterpart).  Jobs may use
+ * different contexts (ring degree, limbs, primes) and plans on one device.
+ *   plain       one he_cpmul_conv call per job (three launches per job);
+ *   persistent  per ring degree present, one persistent forward-NTT kernel
+ *               and one persistent multiply-accumulate/inverse-NTT kernel
+ *               whose CTAs pull work items (one limb polynomial each, the
+ *               heaviest first) from a device counter;
+ *   graph       the persistent launch sequence captured once in a CUDA graph
+ *               and replayed (needs a non-default stream).
+ * Results are bit-identical in every form and to a job run alone.  The batch
+ * owns one device allocation (made by he_batch_prepare) holding every job's
+ * NTT-form operands, term tables and work lists; input and output pointers
+ * stay caller-owned and must stay valid while the batch is used.
+ * ------------------------------------------------------------------ */
+#define HE_BATCH_PLAIN 0
+#define HE_BATCH_PERSISTENT 1
+#define HE_BATCH_GRAPH 2
+
+typedef struct he_batch he_batch;
+/* launch configuration chosen by he_batch_autotune for one ring degree */
+typedef struct he_batch_tuning {
+    int32_t logN;
+    int32_t regs_ctas_per_sm;  /* register budget: resident CTAs per SM the kernels are compiled for */
+    int32_t grid_ctas_per_sm;  /* persistent CTAs launched per SM */
+    float ms;                  /* best time of the ring degree's two launches */
+    int32_t fwd_items, mac_items;
+} he_batch_tuning;
+
+int he_batch_create(int device, he_batch **batch);
+int he_batch_destroy(he_batch *batch);
+int he_batch_last_error(const he_batch *batch, char *buf, int len);
+/* Register one job with the arguments of he_cpmul_conv (the ciphertext-input
+ * family: ct_x [batch][T][G][2][L][N], pt_w [MG][G][N], ct_add nullable,
+ * ct_out [batch][MG][T][2][L][N]).  Returns the job index (>= 0). */
+int he_batch_add_cpmul(he_batch *batch, he_ctx *ctx, const he_plan *plan, int n_images, const uint64_t *ct_x,
+                       const uint64_t *pt_w, const uint64_t *ct_add, uint64_t *ct_out);
+/* Freeze the job list: one device allocation for the batch, work lists built
+ * and uploaded (synchronous). */
+int he_batch_prepare(he_batch *batch);
+/* Run the batch in `mode` on `stream` (asynchronous). */
+int he_batch_run(he_batch *batch, int mode, cudaStream_t stream);
+/* Time every candidate launch configuration of each ring degree on the
+ * prepared batch (register budget 1 or 2 CTAs per SM, 1..4 persistent CTAs
+ * per SM; three runs each, best kept), keep the fastest, and report it in
+ * out[0 .. min(max_out, n)) with n = number of ring degrees.  Overwrites the
+ * jobs' outputs; synchronises; invalidates a captured graph. */
+int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out, int max_out, int *n);
+
 /* Launch tracing (profiling aid, not part of the paper's method).  While
  * enabled, every kernel launch of the context is bracketed by two CUDA events
  * on its stream and tagged with the kernel family name and its algorithmic

@@ -195,6 +195,31 @@ struct MacJob {
 };
 int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st);
 
+// Work items of the persistent queue kernels (batched execution).
+struct FwdItem {            // forward NTT of one limb polynomial
+    const void *src;        // this limb's source (kind as in FwdJob)
+    u64 *dst;               // this limb's NTT-form output
+    const ModDev *mod;      // its modulus (device pointer)
+    u64 t;                  // plaintext modulus for SRC_T_LIFT
+    int kind;
+    int pad_;
+};
+struct MacItem {            // multiply-accumulate + inverse NTT + add of one output limb
+    const u64 *A, *B;       // NTT-form bases (limb 0) of the operands
+    const int32_t *ta, *tb; // term tables
+    int t0, t1;             // term range
+    int limb;
+    int pad_;
+    u64 *out;               // this limb's output (coefficient form)
+    const u64 *add;         // this limb's addend or null
+    const ModDev *mod;
+};
+// Persistent kernel over items (fi != null: forward items, else MAC items)
+// of ring degree 2^logN; minb selects the register budget (resident CTAs per
+// SM the kernel is compiled for); grid CTAs; *counter must be 0.
+int launch_queue(int logN, int minb, const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid,
+                 cudaStream_t st);
+
 // sampling (ChaCha20 streams): kinds
 enum SampleKind { SAMPLE_TERNARY = 0, SAMPLE_CBD = 1, SAMPLE_UNIFORM_Q = 2, SAMPLE_UNIFORM_T = 3 };
 // n_obj objects, object k uses stream (seed, tag, idx0 + k, limb); for

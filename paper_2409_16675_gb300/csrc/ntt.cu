@@ -99,28 +99,22 @@ __device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[16], int tau, int lo_
     __syncthreads();
 }
 
-template <int LOGN, bool LAZY>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J, const ModDev *__restrict__ mods) {
-    extern __shared__ u64 sm[];
-    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
-    const int tau = threadIdx.x;
-    const int limb = blockIdx.x / J.n_polys;
-    const int p = blockIdx.x - limb * J.n_polys;
-    const ModDev M = mods[J.mod_base + limb];
-    u64 v[16];
-    // first window: bits [LOGN-4, LOGN): element j = k*T + tau (coalesced)
-    switch (J.kind) {
+// ---------------------------------------------------------------- per-polynomial building blocks
+// Load one limb polynomial into the first register window (bits [LOGN-4,
+// LOGN): element k*T + tau, coalesced), reducing / lifting it into [0, q).
+template <int LOGN>
+__device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const ModDev &M, int tau, u64 (&v)[16]) {
+    constexpr int T = Cfg<LOGN>::T;
+    switch (kind) {
     case SRC_RNS: {
-        const u64 *s = limb < J.split
-            ? (const u64 *)J.src + (long long)p * J.src_stride + (long long)limb * N
-            : (const u64 *)J.src2 + (long long)p * J.src2_stride + (long long)(limb - J.split) * N;
+        const u64 *s = (const u64 *)src;
 #pragma unroll
         for (int k = 0; k < 16; k++) v[k] = s[k * T + tau];
         break;
     }
     case SRC_T_LIFT: {
-        const u64 *s = (const u64 *)J.src + (long long)p * J.src_stride;
-        const u64 t = J.t, half = (J.t - 1) / 2;
+        const u64 *s = (const u64 *)src;
+        const u64 half = (t - 1) / 2;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             u64 x = s[k * T + tau];
@@ -130,7 +124,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J,
         break;
     }
     case SRC_I8: {
-        const int8_t *s = (const int8_t *)J.src + (long long)p * J.src_stride;
+        const int8_t *s = (const int8_t *)src;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
             const int x = s[k * T + tau];
@@ -139,18 +133,25 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J,
         break;
     }
     case SRC_U32: {
-        const uint32_t *s = (const uint32_t *)J.src + (long long)p * J.src_stride;
+        const uint32_t *s = (const uint32_t *)src;
 #pragma unroll
         for (int k = 0; k < 16; k++) v[k] = s[k * T + tau];
         break;
     }
     default: {  // SRC_T_RAW
-        const u64 *s = (const u64 *)J.src + (long long)p * J.src_stride;
+        const u64 *s = (const u64 *)src;
 #pragma unroll
         for (int k = 0; k < 16; k++) v[k] = reduce64(s[k * T + tau], M.q, M.one_s);
         break;
     }
     }
+}
+
+// Forward transform of a loaded polynomial and its store in perm16 order
+// (position k*T + tau), fully reduced.
+template <int LOGN, bool LAZY>
+__device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int tau, const ModDev &M, u64 *d) {
+    constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     int lo = LOGN - 4;
     for (int pass = 0; pass < NP - 1; pass++) {
         fwd_pass<LOGN, 4, LAZY>(v, tau, lo, 4 * pass, M);
@@ -159,26 +160,17 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J,
         lo = lo_next;
     }
     fwd_pass<LOGN, RL, LAZY>(v, tau, 0, 4 * (NP - 1), M);
-    u64 *d = J.dst + (long long)p * J.dst_stride + (long long)limb * N;
-    const u64 q = M.q;
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-        d[k * T + tau] = reduce64(v[k], q, M.one_s);   // from [0, 57q) or [0, 8q)
-    }
+    for (int k = 0; k < 16; k++) d[k * T + tau] = reduce64(v[k], M.q, M.one_s);  // from [0, 57q) or [0, 8q)
 }
 
-template <int LOGN, bool LAZY>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJob J, const ModDev *__restrict__ mods) {
-    extern __shared__ u64 sm[];
-    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
-    const int tau = threadIdx.x;
-    const int limb = blockIdx.x / J.n_out;
-    const int o = blockIdx.x - limb * J.n_out;
-    const ModDev M = mods[J.mod_base + limb];
-    u64 v[16];
-    // multiply-accumulate in two halves of 8 coefficients (128-bit sums) to
-    // keep the register footprint of the accumulators small
-    const int t0 = J.ptr[o], t1 = J.ptr[o + 1];
+// sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
+// in two halves of 8 coefficients (128-bit sums), result fully reduced
+template <int LOGN>
+__device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const u64 *__restrict__ B,
+                                               const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int t0,
+                                               int t1, int limb, const ModDev &M, int tau, u64 (&v)[16]) {
+    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T;
 #pragma unroll
     for (int half = 0; half < 2; half++) {
         u64 lo[8], hi[8];
@@ -186,8 +178,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
         for (int kk = 0; kk < 8; kk++) { lo[kk] = 0; hi[kk] = 0; }
         int cnt = 0;
         for (int tk = t0; tk < t1; tk++) {
-            const u64 *a = J.A + ((long long)J.ta[tk] + limb) * N + half * 8 * T + tau;
-            const u64 *b = J.B + ((long long)J.tb[tk] + limb) * N + half * 8 * T + tau;
+            const u64 *a = A + ((long long)ta[tk] + limb) * N + half * 8 * T + tau;
+            const u64 *b = B + ((long long)tb[tk] + limb) * N + half * 8 * T + tau;
 #pragma unroll
             for (int kk = 0; kk < 8; kk++) {
                 u64 pl, ph;
@@ -204,9 +196,15 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
 #pragma unroll
         for (int kk = 0; kk < 8; kk++) v[half * 8 + kk] = reduce128(lo[kk], hi[kk], M);
     }
-    // inverse: bits 0-3 first (the perm16 register tile), then upward; the
-    // last window is the top four bits [LOGN-4, LOGN) holding the remaining
-    // RL stages, and leaves every thread with coalesced natural-order elements
+}
+
+// Inverse transform: bits 0-3 first (the perm16 register tile), then upward;
+// the last window is the top four bits [LOGN-4, LOGN) holding the remaining
+// RL stages, and leaves every thread with the natural-order elements k*T + tau
+// (before the untwist / N^-1 scaling).
+template <int LOGN, bool LAZY>
+__device__ __forceinline__ void inv_transform(u64 (&v)[16], u64 *sm, int tau, const ModDev &M) {
+    constexpr int NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     inv_pass<4, 0, LAZY>(v, tau, 0, 0, M);
     int lo = 0;
     for (int pass = 1; pass < NP - 1; pass++) {
@@ -216,6 +214,44 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
     }
     exchange(sm, v, tau, lo, LOGN - 4);
     inv_pass<RL, 4 - RL, LAZY>(v, tau, LOGN - 4, 4 * (NP - 1), M);
+}
+
+// ---------------------------------------------------------------- grid kernels (one CTA per limb polynomial)
+template <int LOGN, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J, const ModDev *__restrict__ mods) {
+    extern __shared__ u64 sm[];
+    constexpr int N = Cfg<LOGN>::N;
+    const int tau = threadIdx.x;
+    const int limb = blockIdx.x / J.n_polys;
+    const int p = blockIdx.x - limb * J.n_polys;
+    const ModDev M = mods[J.mod_base + limb];
+    const void *src;
+    if (J.kind == SRC_RNS)
+        src = limb < J.split ? (const void *)((const u64 *)J.src + (long long)p * J.src_stride + (long long)limb * N)
+                             : (const void *)((const u64 *)J.src2 + (long long)p * J.src2_stride +
+                                              (long long)(limb - J.split) * N);
+    else if (J.kind == SRC_I8)
+        src = (const int8_t *)J.src + (long long)p * J.src_stride;
+    else if (J.kind == SRC_U32)
+        src = (const uint32_t *)J.src + (long long)p * J.src_stride;
+    else
+        src = (const u64 *)J.src + (long long)p * J.src_stride;
+    u64 v[16];
+    fwd_load<LOGN>(J.kind, src, J.t, M, tau, v);
+    fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, J.dst + (long long)p * J.dst_stride + (long long)limb * N);
+}
+
+template <int LOGN, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJob J, const ModDev *__restrict__ mods) {
+    extern __shared__ u64 sm[];
+    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T;
+    const int tau = threadIdx.x;
+    const int limb = blockIdx.x / J.n_out;
+    const int o = blockIdx.x - limb * J.n_out;
+    const ModDev M = mods[J.mod_base + limb];
+    u64 v[16];
+    mac_accumulate<LOGN>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
+    inv_transform<LOGN, LAZY>(v, sm, tau, M);
     // natural order: element j = k*T + tau
     const u64 q = M.q;
     u64 *out = J.out + (long long)o * J.out_stride + (long long)limb * N;
@@ -245,6 +281,63 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
         }
         if (add) r = addm(r, add[x], q);
         out[x] = r;
+    }
+}
+
+// ---------------------------------------------------------------- persistent queue kernels
+// Each CTA repeatedly takes the next item of a device work list (one atomic
+// per item) until the list is exhausted; items of one launch share the ring
+// degree but may use any modulus of any context.  The counter must be zero
+// at launch.
+template <int LOGN, int MINB>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const FwdItem *__restrict__ items, int n,
+                                                                  int *counter) {
+    extern __shared__ u64 sm[];
+    __shared__ int s_item;
+    const int tau = threadIdx.x;
+    for (;;) {
+        if (tau == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n) break;
+        const FwdItem I = items[it];
+        const ModDev M = *I.mod;
+        u64 v[16];
+        fwd_load<LOGN>(I.kind, I.src, I.t, M, tau, v);
+        if (M.q < (1ull << 57)) fwd_transform_store<LOGN, true>(v, sm, tau, M, I.dst);
+        else fwd_transform_store<LOGN, false>(v, sm, tau, M, I.dst);
+    }
+}
+
+template <int LOGN, int MINB>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const MacItem *__restrict__ items, int n,
+                                                                  int *counter) {
+    extern __shared__ u64 sm[];
+    __shared__ int s_item;
+    constexpr int T = Cfg<LOGN>::T;
+    const int tau = threadIdx.x;
+    for (;;) {
+        if (tau == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n) break;
+        const MacItem I = items[it];
+        const ModDev M = *I.mod;
+        u64 v[16];
+        mac_accumulate<LOGN>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
+        if (M.q < (1ull << 57)) inv_transform<LOGN, true>(v, sm, tau, M);
+        else inv_transform<LOGN, false>(v, sm, tau, M);
+        const u64 q = M.q;
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int x = k * T + tau;
+            const ulonglong2 zp = __ldg(M.z + x);
+            u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
+            if (I.add) r = addm(r, I.add[x], q);
+            I.out[x] = r;
+        }
     }
 }
 
@@ -307,6 +400,38 @@ int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) {
     case 14: return fwd_t<14>(c, j, st);
     }
     return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
+}
+
+template <int LOGN, int MINB>
+static int queue_t(const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid, cudaStream_t st) {
+    const int smem = Cfg<LOGN>::SMEM;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_fwd_queue<LOGN, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mac_queue<LOGN, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    if (fi) k_fwd_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(fi, nf, counter);
+    else k_mac_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(mi, nm, counter);
+    return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ERR_CUDA;
+}
+
+int launch_queue(int logN, int minb, const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid,
+                 cudaStream_t st) {
+    if ((fi ? nf : nm) <= 0) return HE_OK;
+    switch (logN * 2 + (minb >= 2 ? 1 : 0)) {
+    case 20: return queue_t<10, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 21: return queue_t<10, 2>(fi, nf, mi, nm, counter, grid, st);
+    case 22: return queue_t<11, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 23: return queue_t<11, 2>(fi, nf, mi, nm, counter, grid, st);
+    case 24: return queue_t<12, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 25: return queue_t<12, 2>(fi, nf, mi, nm, counter, grid, st);
+    case 26: return queue_t<13, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 27: return queue_t<13, 2>(fi, nf, mi, nm, counter, grid, st);
+    case 28: return queue_t<14, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 29: return queue_t<14, 1>(fi, nf, mi, nm, counter, grid, st);
+    }
+    return HE_ERR_UNSUPPORTED_PARAMS;
 }
 
 int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st) {

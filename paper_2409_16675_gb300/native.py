@@ -24,6 +24,7 @@ HE_ENC_CONVENTIONAL, HE_ENC_CORRELATED = 0, 1
 HE_ROLE_INPUT, HE_ROLE_KERNEL = 0, 1
 HE_DTYPE_U8, HE_DTYPE_I8, HE_DTYPE_I64 = 0, 1, 2
 HE_KEY_SK, HE_KEY_PK, HE_KEY_RLK = 0, 1, 2
+HE_BATCH_PLAIN, HE_BATCH_PERSISTENT, HE_BATCH_GRAPH = 0, 1, 2
 
 
 class HEError(RuntimeError):
@@ -51,6 +52,11 @@ class he_conv_shape(ctypes.Structure):
 class he_trace_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("modmuls", ctypes.c_double)]
+
+
+class he_batch_tuning(ctypes.Structure):
+    _fields_ = [("logN", ctypes.c_int32), ("regs_ctas_per_sm", ctypes.c_int32), ("grid_ctas_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("fwd_items", ctypes.c_int32), ("mac_items", ctypes.c_int32)]
 
 
 class he_plan_info(ctypes.Structure):
@@ -88,6 +94,13 @@ def _load():
         "he_ccmul_conv_precompute": [vp, vp, vp, i32, vp, vp, vp, vp],
         "he_ppmul_conv": [vp, vp, i32, vp, vp, vp, vp],
         "he_decode": [vp, vp, i32, vp, vp, vp, vp],
+        "he_batch_create": [i32, pp],
+        "he_batch_destroy": [vp],
+        "he_batch_last_error": [vp, ctypes.c_char_p, i32],
+        "he_batch_add_cpmul": [vp, vp, vp, i32, vp, vp, vp, vp],
+        "he_batch_prepare": [vp],
+        "he_batch_run": [vp, i32, vp],
+        "he_batch_autotune": [vp, vp, ctypes.POINTER(he_batch_tuning), i32, ctypes.POINTER(i32)],
         "he_trace_enable": [vp, i32],
         "he_trace_read": [vp, ctypes.POINTER(he_trace_entry), i32, ctypes.POINTER(i32)],
     }
@@ -264,3 +277,52 @@ def he_trace_read(ctx) -> dict:
     _check(lib.he_trace_read(ctx, arr, 64, ctypes.byref(n)), ctx)
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes, arr[i].modmuls)
             for i in range(min(n.value, 64))}
+
+
+def _bcheck(rc, b):
+    if rc < 0:
+        buf = ctypes.create_string_buffer(512)
+        lib.he_batch_last_error(b, buf, 512)
+        raise HEError(rc, buf.value.decode())
+    return rc
+
+
+def he_batch_create(device=0):
+    h = ctypes.c_void_p()
+    _check(lib.he_batch_create(device, ctypes.byref(h)))
+    return h
+
+
+def he_batch_destroy(b):
+    _check(lib.he_batch_destroy(b))
+
+
+def he_batch_add_cpmul(b, ctx, plan, n_images, ct_x, pt_w, ct_add, ct_out) -> int:
+    return _bcheck(lib.he_batch_add_cpmul(b, ctx, plan, n_images, _ptr(ct_x), _ptr(pt_w), _ptr(ct_add),
+                                          _ptr(ct_out)), b)
+
+
+def he_batch_prepare(b):
+    _bcheck(lib.he_batch_prepare(b), b)
+
+
+def he_batch_run(b, mode):
+    _bcheck(lib.he_batch_run(b, mode, _stream()), b)
+
+
+def he_batch_autotune(b):
+    arr = (he_batch_tuning * 8)()
+    n = ctypes.c_int32()
+    _bcheck(lib.he_batch_autotune(b, _stream(), arr, 8, ctypes.byref(n)), b)
+    return [dict(logN=arr[i].logN, regs_ctas_per_sm=arr[i].regs_ctas_per_sm, grid_ctas_per_sm=arr[i].grid_ctas_per_sm,
+                 ms=arr[i].ms, fwd_items=arr[i].fwd_items, mac_items=arr[i].mac_items) for i in range(min(n.value, 8))]
+
+
+def he_batch_last_error(b) -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.he_batch_last_error(b, buf, 512)
+    return buf.value.decode()
+
+
+def he_last_error(ctx=None) -> str:
+    return last_error(ctx)

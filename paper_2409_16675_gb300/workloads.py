@@ -129,3 +129,35 @@ class ProtocolSeeds:
 def protocol_seeds(seed: int) -> ProtocolSeeds:
     return ProtocolSeeds(seed * 7 + 1, seed * 7 + 2, seed * 7 + 3, seed * 7 + 4, seed * 7 + 5,
                          seed * 7 + 6, seed * 7 + 7)
+
+
+@dataclass(frozen=True)
+class BatchJob:
+    """One ct x pt convolution job of the batched form."""
+
+    ring: RingSpec
+    shape: ConvShape
+    encoding: str
+    seed: int
+
+
+def batched_jobs(seed: int = MASTER_SEED + 4, n_jobs: int = 256, channels=(3, 16, 32, 64, 128),
+                 sizes=(8, 16, 32), kernels=(1, 3, 5), degrees=(4096, 8192), limbs=(2, 5), bits=(36, 60)):
+    """Uneven CNN-layer jobs: C and M uniform over `channels`, H = W uniform over
+    `sizes`, kernel uniform over `kernels` with same padding (h-1)/2, N uniform
+    over `degrees`, L uniform in `limbs`, each limb's prime size uniform in
+    `bits`, encoding conventional or correlated with equal probability,
+    t = 65537."""
+    r = rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        C = int(r.choice(channels))
+        M = int(r.choice(channels))
+        H = int(r.choice(sizes))
+        h = int(r.choice(kernels))
+        N = int(r.choice(degrees))
+        L = int(r.integers(limbs[0], limbs[1] + 1))
+        pb = tuple(int(b) for b in r.integers(bits[0], bits[1] + 1, size=L))
+        enc = "corr" if r.integers(0, 2) else "conv"
+        jobs.append(BatchJob(RingSpec(N, pb, 65537), ConvShape(C, H, H, M, h, (h - 1) // 2), enc, seed * 1000 + j))
+    return jobs

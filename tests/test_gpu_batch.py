@@ -1,0 +1,87 @@
+"""Batched form: many ct x pt convolution jobs of uneven shapes, ring degrees,
+limb counts and primes.  The plain, persistent and graph forms give identical
+bits, a job's result is the same alone and in the mix, and the results equal
+the oracle's."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import he, packing  # noqa: E402
+from paper_2409_16675_gb300 import layer, native as nv, workloads as wl  # noqa: E402
+
+
+def make_inputs(ctx, plan, B, seed):
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    T, G, MG = plan.T, plan.G, plan.MG
+    ct = torch.empty((B * T * G, 2, ctx.L, ctx.N), dtype=torch.int64, device="cuda")
+    for i, q in enumerate(ctx.q):
+        ct[:, :, i, :] = torch.randint(0, q, (B * T * G, 2, ctx.N), generator=g, device="cuda", dtype=torch.int64)
+    pt = torch.randint(0, ctx.t, (MG * G, ctx.N), generator=g, device="cuda", dtype=torch.int64)
+    return ct.view(torch.uint64), pt.view(torch.uint64)
+
+
+def build(jobs, B=1):
+    ctxs, items = {}, []
+    for j in jobs:
+        key = (j.ring.N, j.ring.prime_bits)
+        if key not in ctxs:
+            ctxs[key] = layer.Context(j.ring)
+        c = ctxs[key]
+        p = layer.Plan(c, j.shape, j.encoding)
+        ct, pt = make_inputs(c, p, B, j.seed)
+        out = c.ct(B * p.MG * p.T)
+        items.append((c, p, ct, pt, out))
+    return ctxs, items
+
+
+def test_batch_forms_identical_and_equal_alone():
+    jobs = wl.batched_jobs(seed=123, n_jobs=14, channels=(3, 5, 16), sizes=(6, 8, 12), kernels=(1, 3, 5))
+    ctxs, items = build(jobs, B=2)
+    b = nv.he_batch_create(0)
+    for (c, p, ct, pt, out) in items:
+        nv.he_batch_add_cpmul(b, c.h, p.h, 2, ct, pt, None, out)
+    nv.he_batch_prepare(b)
+    s = torch.cuda.Stream()
+    results = {}
+    with torch.cuda.stream(s):
+        for mode in (nv.HE_BATCH_PLAIN, nv.HE_BATCH_PERSISTENT, nv.HE_BATCH_GRAPH, nv.HE_BATCH_GRAPH):
+            for it in items:
+                it[4].zero_()
+            nv.he_batch_run(b, mode)
+            s.synchronize()
+            results.setdefault(mode, []).append([it[4].clone() for it in items])
+        tuning = nv.he_batch_autotune(b)
+        nv.he_batch_run(b, nv.HE_BATCH_PERSISTENT)
+        s.synchronize()
+        tuned = [it[4].clone() for it in items]
+    assert tuning and all(t["ms"] > 0 for t in tuning)
+    ref = results[nv.HE_BATCH_PLAIN][0]
+    for mode, runs in results.items():
+        for run in runs:
+            for a, r in zip(run, ref):
+                assert torch.equal(a, r), mode
+    for a, r in zip(tuned, ref):
+        assert torch.equal(a, r)
+    # a job alone equals the same job inside the batch
+    for (c, p, ct, pt, out), r in zip(items, ref):
+        alone = c.ct(out.shape[0])
+        nv.he_cpmul_conv(c.h, p.h, 2, ct, pt, None, None, None, alone)
+        torch.cuda.synchronize()
+        assert torch.equal(alone, r)
+    nv.he_batch_destroy(b)
+    # two jobs against the oracle
+    for (c, p, ct, pt, out), r in list(zip(items, ref))[:2]:
+        P = he.Params(c.N, c.q, c.t)
+        op = packing.make_plan(p.encoding, c.N, *[getattr(p.shape, k) for k in ("C", "H", "W", "M", "h", "pad")])
+        T, G, MG = op.T, op.G, op.MG
+        terms = [[((bb * T + t) * G + g, m * G + g) for g in range(G)]
+                 for bb in range(2) for m in range(MG) for t in range(T)]
+        want = he.cpmul_terms(P, ct.cpu().numpy(), pt.cpu().numpy(), terms)
+        assert np.array_equal(r.cpu().numpy(), want)
+    for c in ctxs.values():
+        c.close()
