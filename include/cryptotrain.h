@@ -295,6 +295,12 @@ int he_batch_last_error(const he_batch *batch, char *buf, int len);
  * ct_out [batch][MG][T][2][L][N]).  Returns the job index (>= 0). */
 int he_batch_add_cpmul(he_batch *batch, he_ctx *ctx, const he_plan *plan, int n_images, const uint64_t *ct_x,
                        const uint64_t *pt_w, const uint64_t *ct_add, uint64_t *ct_out);
+/* The same with both operand families of he_cpmul_conv (the CryptoTrain-P
+ * online layer: ct_x * pt_w + ct_w * pt_x + ct_add); either family may be
+ * NULL but not both. */
+int he_batch_add_cpmul2(he_batch *batch, he_ctx *ctx, const he_plan *plan, int n_images, const uint64_t *ct_x,
+                        const uint64_t *pt_w, const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add,
+                        uint64_t *ct_out);
 /* Freeze the job list: one device allocation for the batch, work lists built
  * and uploaded (synchronous). */
 int he_batch_prepare(he_batch *batch);
@@ -306,6 +312,55 @@ int he_batch_run(he_batch *batch, int mode, cudaStream_t stream);
  * out[0 .. min(max_out, n)) with n = number of ring degrees.  Overwrites the
  * jobs' outputs; synchronises; invalidates a captured graph. */
 int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out, int max_out, int *n);
+
+/* ------------------------------------------------------------------
+ * Continuous-batching request server for CPMul convolution layers (the
+ * online phase of the CryptoTrain-P linear layer; a serving form, the paper
+ * has no counterpart).  At creation the server reserves hbm_budget_bytes of
+ * device memory as its arena and starts a worker thread.  A submitted
+ * request (the arguments of he_cpmul_conv, whose keys, precomputed products
+ * and operands stay resident in caller memory) waits until its scratch fits
+ * in the arena and fewer than max_inflight launch groups are running; the
+ * worker then launches up to max_group admitted requests together as
+ * persistent queue kernels on the next of n_streams streams, so requests
+ * arriving while others run join the next group and groups overlap on the
+ * device.  Each result is bit-identical to he_cpmul_conv on the same
+ * arguments.  Latency is measured from submission to the worker observing
+ * completion (polling every poll_us).
+ * ------------------------------------------------------------------ */
+typedef struct he_server he_server;
+typedef struct he_server_config {
+    int32_t device;
+    double hbm_budget_bytes;  /* arena size (admission cap) */
+    int32_t max_group;        /* requests per launch group */
+    int32_t max_inflight;     /* launch groups on the device at once */
+    int32_t n_streams;
+    int32_t poll_us;          /* completion polling interval (0 -> 20) */
+} he_server_config;
+typedef struct he_server_report {
+    int64_t submitted, completed, images, groups;
+    double p50_us, p99_us, mean_us, max_us;
+    double span_s;            /* first submission to last completion */
+    double arena_peak_bytes, arena_bytes;
+} he_server_report;
+int he_server_create(const he_server_config *cfg, he_server **server);
+/* Queue one request; returns at once.  BUDGET_EXCEEDED if it could never fit
+ * the arena.  Buffers must stay valid until the request is done. */
+int he_server_submit(he_server *server, he_ctx *ctx, const he_plan *plan, int n_images, const uint64_t *ct_x,
+                     const uint64_t *pt_w, const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add,
+                     uint64_t *ct_out, int64_t *request_id);
+int he_server_poll(he_server *server, int64_t request_id, int *done, double *latency_us);
+/* Arena bytes one request would reserve (its scratch plus its share of the
+ * work lists), for admission planning; has_x / has_w select the families. */
+int he_server_request_bytes(const he_ctx *ctx, const he_plan *plan, int n_images, int has_x, int has_w,
+                            double *bytes);
+/* Block until every submitted request is done (TIMEOUT after timeout_s). */
+int he_server_wait_all(he_server *server, double timeout_s);
+/* Statistics over the requests submitted since the last reset. */
+int he_server_stats(he_server *server, he_server_report *stats);
+int he_server_reset_stats(he_server *server);
+/* Drain the queue, stop the worker, release the arena. */
+int he_server_destroy(he_server *server);
 
 /* Launch tracing (profiling aid, not part of the paper's method).  While
  * enabled, every kernel launch of the context is bracketed by two CUDA events

@@ -16,17 +16,79 @@
 
 #include "internal.h"
 
+namespace he {
+
+JobLayout job_layout(const JobDesc &J) {
+    const int L = J.c->L, N = J.c->N, T = J.p->info.T, G = J.p->info.G, MG = J.p->info.MG;
+    const size_t LN = (size_t)L * N;
+    const long long nX = J.ct_x ? (long long)J.batch * T * G * 2 : 0, nW = J.ct_w ? (long long)MG * G * 2 : 0;
+    const long long nWp = J.ct_x ? (long long)MG * G : 0, nXp = J.ct_w ? (long long)J.batch * T * G : 0;
+    const long long n_out = (long long)J.batch * MG * T * 2;
+    const long long n_terms = n_out * G * ((J.ct_x ? 1 : 0) + (J.ct_w ? 1 : 0));
+    auto al = [](size_t n) { return (n + 255) & ~size_t(255); };
+    JobLayout l;
+    l.a_bytes = al((size_t)(nX + nW) * LN * 8);
+    l.b_bytes = al((size_t)(nWp + nXp) * LN * 8);
+    l.t_bytes = al((size_t)(n_out + 1 + 2 * n_terms) * 4);
+    l.n_fwd = (size_t)(nX + nW + nWp + nXp) * L;
+    l.n_mac = (size_t)n_out * L;
+    return l;
+}
+
+void job_items(const JobDesc &J, char *dev, std::vector<int32_t> &terms, std::vector<FwdItem> &F,
+               std::vector<MacItem> &Mi) {
+    const int L = J.c->L, N = J.c->N, T = J.p->info.T, G = J.p->info.G, MG = J.p->info.MG;
+    const size_t LN = (size_t)L * N;
+    const JobLayout l = job_layout(J);
+    const long long nX = J.ct_x ? (long long)J.batch * T * G * 2 : 0, nW = J.ct_w ? (long long)MG * G * 2 : 0;
+    const long long nWp = J.ct_x ? (long long)MG * G : 0, nXp = J.ct_w ? (long long)J.batch * T * G : 0;
+    u64 *A = (u64 *)dev, *B = (u64 *)(dev + l.a_bytes);
+    // term table: ta then tb
+    std::vector<int32_t> ta, tb;
+    std::vector<int> t0;
+    for (int bb = 0; bb < J.batch; bb++)
+        for (int m = 0; m < MG; m++)
+            for (int t = 0; t < T; t++)
+                for (int comp = 0; comp < 2; comp++) {
+                    t0.push_back((int)ta.size());
+                    for (int g = 0; g < G; g++) {
+                        const long long xi = (long long)(bb * T + t) * G + g;
+                        if (J.ct_x) {
+                            ta.push_back((int32_t)((xi * 2 + comp) * L));
+                            tb.push_back((int32_t)((long long)(m * G + g) * L));
+                        }
+                        if (J.ct_w) {
+                            ta.push_back((int32_t)((nX + (long long)(m * G + g) * 2 + comp) * L));
+                            tb.push_back((int32_t)((nWp + xi) * L));
+                        }
+                    }
+                }
+    t0.push_back((int)ta.size());
+    terms.assign(l.t_bytes / 4, 0);
+    std::copy(ta.begin(), ta.end(), terms.begin());
+    std::copy(tb.begin(), tb.end(), terms.begin() + ta.size());
+    const int32_t *dta = (const int32_t *)(dev + l.a_bytes + l.b_bytes), *dtb = dta + ta.size();
+    auto fwd = [&](const u64 *src, int kind, u64 *dst, long long n, long long stride) {
+        for (long long p = 0; p < n; p++)
+            for (int li = 0; li < L; li++)
+                F.push_back({kind == SRC_RNS ? (const void *)(src + p * LN + (size_t)li * N) : (const void *)(src + p * stride),
+                             dst + p * LN + (size_t)li * N, J.c->d_mods + li, J.c->P.t, kind, 0});
+    };
+    if (J.ct_x) { fwd(J.ct_x, SRC_RNS, A, nX, 0); fwd(J.pt_w, SRC_T_LIFT, B, nWp, N); }
+    if (J.ct_w) { fwd(J.ct_w, SRC_RNS, A + nX * LN, nW, 0); fwd(J.pt_x, SRC_T_LIFT, B + nWp * LN, nXp, N); }
+    const long long n_out = (long long)J.batch * MG * T * 2;
+    for (long long o = 0; o < n_out; o++)
+        for (int li = 0; li < L; li++)
+            Mi.push_back({A, B, dta, dtb, t0[o], t0[o + 1], li, 0, J.out + o * LN + (size_t)li * N,
+                          J.ct_add ? J.ct_add + o * LN + (size_t)li * N : nullptr, J.c->d_mods + li});
+}
+
+}  // namespace he
+
 struct he_batch {
     int device = 0;
     int n_sms = 0;
-    struct Job {
-        he_ctx *c;
-        const he_plan *p;
-        int batch;
-        const u64 *ct_x, *pt_w, *ct_add;
-        u64 *out;
-    };
-    std::vector<Job> jobs;
+    std::vector<he::JobDesc> jobs;
     bool prepared = false;
     void *mem = nullptr;
     struct Class {
@@ -35,6 +97,7 @@ struct he_batch {
         int nf;
         const he::MacItem *mi;
         int nm;
+        const he::ItemSeg *fseg, *mseg;  // one-segment tables (device)
         int minb = 2;
         int grid_mult = 2;
         float best_ms = 0;
@@ -61,12 +124,12 @@ int run_persistent(he_batch *b, cudaStream_t st) {
         return bfail(b, HE_ERR_CUDA, "counter reset");
     for (size_t i = 0; i < b->classes.size(); i++) {
         const auto &k = b->classes[i];
-        int rc = he::launch_queue(k.logN, k.minb, k.fi, k.nf, nullptr, 0, b->counters + 2 * i, b->n_sms * k.grid_mult, st);
+        int rc = he::launch_queue(k.logN, k.minb, true, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * k.grid_mult, st);
         if (rc) return bfail(b, rc, "forward queue launch");
     }
     for (size_t i = 0; i < b->classes.size(); i++) {
         const auto &k = b->classes[i];
-        int rc = he::launch_queue(k.logN, k.minb, nullptr, 0, k.mi, k.nm, b->counters + 2 * i + 1,
+        int rc = he::launch_queue(k.logN, k.minb, false, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
                                   b->n_sms * k.grid_mult, st);
         if (rc) return bfail(b, rc, "multiply-accumulate queue launch");
     }
@@ -114,132 +177,96 @@ int he_batch_last_error(const he_batch *b, char *buf, int len) {
     return HE_OK;
 }
 
-int he_batch_add_cpmul(he_batch *b, he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x,
-                       const uint64_t *pt_w, const uint64_t *ct_add, uint64_t *ct_out) {
-    if (!b || !c || !p || batch < 1 || !ct_x || !pt_w || !ct_out) return HE_ERR_INVALID_ARG;
+int he_batch_add_cpmul2(he_batch *b, he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x,
+                        const uint64_t *pt_w, const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add,
+                        uint64_t *ct_out) {
+    if (!b || !c || !p || batch < 1 || !ct_out || (!ct_x && !ct_w) || (ct_x && !pt_w) || (ct_w && !pt_x))
+        return HE_ERR_INVALID_ARG;
     if (b->prepared) return bfail(b, HE_ERR_INVALID_ARG, "batch already prepared");
     if (c->P.device != b->device) return bfail(b, HE_ERR_INVALID_ARG, "context on another device");
     if (p->N != c->N) return bfail(b, HE_ERR_INVALID_ARG, "plan of another ring");
-    b->jobs.push_back({c, p, batch, ct_x, pt_w, ct_add, ct_out});
+    b->jobs.push_back({c, p, batch, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out});
     return (int)b->jobs.size() - 1;
+}
+
+int he_batch_add_cpmul(he_batch *b, he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x,
+                       const uint64_t *pt_w, const uint64_t *ct_add, uint64_t *ct_out) {
+    if (!ct_x || !pt_w) return HE_ERR_INVALID_ARG;
+    return he_batch_add_cpmul2(b, c, p, batch, ct_x, pt_w, nullptr, nullptr, ct_add, ct_out);
 }
 
 int he_batch_prepare(he_batch *b) {
     if (!b) return HE_ERR_INVALID_ARG;
     if (b->prepared) return HE_OK;
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HE_ERR_CUDA, "cudaSetDevice");
-    // scratch layout and term tables
-    struct JL { size_t a_off, b_off, t_off; std::vector<int32_t> ta, tb; int G; };
-    std::vector<JL> lay(b->jobs.size());
-    size_t off = 0;
-    for (size_t j = 0; j < b->jobs.size(); j++) {
-        const auto &J = b->jobs[j];
-        const int L = J.c->L, N = J.c->N, T = J.p->info.T, G = J.p->info.G, MG = J.p->info.MG;
-        const size_t LN = (size_t)L * N;
-        const long long nX = (long long)J.batch * T * G * 2, nW = (long long)MG * G;
-        JL &l = lay[j];
-        l.G = G;
-        for (int bb = 0; bb < J.batch; bb++)
-            for (int m = 0; m < MG; m++)
-                for (int t = 0; t < T; t++)
-                    for (int comp = 0; comp < 2; comp++)
-                        for (int g = 0; g < G; g++) {
-                            l.ta.push_back((int32_t)((((long long)(bb * T + t) * G + g) * 2 + comp) * L));
-                            l.tb.push_back((m * G + g) * L);
-                        }
-        l.a_off = off;
-        off += al((size_t)nX * LN * 8);
-        l.b_off = off;
-        off += al((size_t)nW * LN * 8);
-        l.t_off = off;
-        off += al(l.ta.size() * 8);
-    }
-    // items, grouped by ring degree
     std::vector<int> degrees;
     for (const auto &J : b->jobs)
         if (std::find(degrees.begin(), degrees.end(), J.c->logN) == degrees.end()) degrees.push_back(J.c->logN);
     std::sort(degrees.begin(), degrees.end());
-    std::vector<std::vector<he::FwdItem>> F(degrees.size());
-    std::vector<std::vector<he::MacItem>> Mi(degrees.size());
-    char *base = nullptr;  // device base, known after allocation: build items with offsets first
-    // first pass: compute total sizes of the item arrays
-    size_t items_off = off;
-    size_t nf_total = 0, nm_total = 0;
-    for (const auto &J : b->jobs) {
-        const long long L = J.c->L, T = J.p->info.T, G = J.p->info.G, MG = J.p->info.MG;
-        nf_total += (size_t)(J.batch * T * G * 2 + MG * G) * L;
-        nm_total += (size_t)(J.batch * MG * T * 2) * L;
+    // layout: per job [A][B][terms], then all forward items, all MAC items, counters
+    std::vector<size_t> job_off(b->jobs.size());
+    size_t off = 0, nf_total = 0, nm_total = 0;
+    for (size_t j = 0; j < b->jobs.size(); j++) {
+        const he::JobLayout l = he::job_layout(b->jobs[j]);
+        job_off[j] = off;
+        off += l.a_bytes + l.b_bytes + l.t_bytes;
+        nf_total += l.n_fwd;
+        nm_total += l.n_mac;
     }
+    const size_t items_off = off;
     off += al(nf_total * sizeof(he::FwdItem));
-    size_t mitems_off = off;
+    const size_t mitems_off = off;
     off += al(nm_total * sizeof(he::MacItem));
-    size_t cnt_off = off;
+    const size_t seg_off = off;
+    off += al(2 * degrees.size() * sizeof(he::ItemSeg));
+    const size_t cnt_off = off;
     off += al(2 * degrees.size() * sizeof(int));
     if (cudaMalloc(&b->mem, off) != cudaSuccess) return bfail(b, HE_ERR_OOM, "batch scratch allocation");
-    base = (char *)b->mem;
+    char *base = (char *)b->mem;
+    std::vector<std::vector<he::FwdItem>> F(degrees.size());
+    std::vector<std::vector<he::MacItem>> Mi(degrees.size());
+    std::vector<int32_t> terms;
     for (size_t j = 0; j < b->jobs.size(); j++) {
         const auto &J = b->jobs[j];
-        const JL &l = lay[j];
         const int ci = (int)(std::find(degrees.begin(), degrees.end(), J.c->logN) - degrees.begin());
-        const int L = J.c->L, N = J.c->N, T = J.p->info.T, G = J.p->info.G, MG = J.p->info.MG;
-        const size_t LN = (size_t)L * N;
-        u64 *A = (u64 *)(base + l.a_off), *B = (u64 *)(base + l.b_off);
-        const int32_t *ta = (const int32_t *)(base + l.t_off), *tb = ta + l.ta.size();
-        const long long nX = (long long)J.batch * T * G * 2, nW = (long long)MG * G;
-        for (long long p = 0; p < nX; p++)
-            for (int li = 0; li < L; li++)
-                F[ci].push_back({J.ct_x + p * LN + (size_t)li * N, A + p * LN + (size_t)li * N, J.c->d_mods + li, 0,
-                                 he::SRC_RNS, 0});
-        for (long long p = 0; p < nW; p++)
-            for (int li = 0; li < L; li++)
-                F[ci].push_back({J.pt_w + p * N, B + p * LN + (size_t)li * N, J.c->d_mods + li, J.c->P.t,
-                                 he::SRC_T_LIFT, 0});
-        const long long n_out = (long long)J.batch * MG * T * 2;
-        for (long long o = 0; o < n_out; o++)
-            for (int li = 0; li < L; li++)
-                Mi[ci].push_back({A, B, ta, tb, (int)(o * G), (int)((o + 1) * G), li, 0,
-                                  J.out + o * LN + (size_t)li * N,
-                                  J.ct_add ? J.ct_add + o * LN + (size_t)li * N : nullptr, J.c->d_mods + li});
+        const he::JobLayout l = he::job_layout(J);
+        he::job_items(J, base + job_off[j], terms, F[ci], Mi[ci]);
+        if (cudaMemcpy(base + job_off[j] + l.a_bytes + l.b_bytes, terms.data(), terms.size() * 4,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, HE_ERR_CUDA, "term upload");
     }
     // heaviest multiply-accumulate items first
     for (auto &v : Mi)
         std::stable_sort(v.begin(), v.end(), [](const he::MacItem &x, const he::MacItem &y) {
             return (x.t1 - x.t0) > (y.t1 - y.t0);
         });
-    // stage everything on the host and upload once
-    std::vector<char> host(off, 0);
-    for (size_t j = 0; j < b->jobs.size(); j++) {
-        const JL &l = lay[j];
-        memcpy(host.data() + l.t_off, l.ta.data(), l.ta.size() * 4);
-        memcpy(host.data() + l.t_off + l.ta.size() * 4, l.tb.data(), l.tb.size() * 4);
-    }
     size_t fo = items_off, mo = mitems_off;
+    std::vector<he::ItemSeg> segs;
     b->classes.clear();
     for (size_t ci = 0; ci < degrees.size(); ci++) {
         he_batch::Class k;
         k.logN = degrees[ci];
-        memcpy(host.data() + fo, F[ci].data(), F[ci].size() * sizeof(he::FwdItem));
-        memcpy(host.data() + mo, Mi[ci].data(), Mi[ci].size() * sizeof(he::MacItem));
+        if (cudaMemcpy(base + fo, F[ci].data(), F[ci].size() * sizeof(he::FwdItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(base + mo, Mi[ci].data(), Mi[ci].size() * sizeof(he::MacItem), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, HE_ERR_CUDA, "item upload");
         k.fi = (const he::FwdItem *)(base + fo);
         k.nf = (int)F[ci].size();
         k.mi = (const he::MacItem *)(base + mo);
         k.nm = (int)Mi[ci].size();
+        k.fseg = (const he::ItemSeg *)(base + seg_off) + 2 * ci;
+        k.mseg = k.fseg + 1;
+        segs.push_back({k.fi, 0, 0});
+        segs.push_back({k.mi, 0, 0});
         k.minb = k.logN >= 14 ? 1 : 2;
         k.grid_mult = k.minb;
         fo += F[ci].size() * sizeof(he::FwdItem);
         mo += Mi[ci].size() * sizeof(he::MacItem);
         b->classes.push_back(k);
     }
+    if (cudaMemcpy(base + seg_off, segs.data(), segs.size() * sizeof(he::ItemSeg), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return bfail(b, HE_ERR_CUDA, "segment upload");
     b->counters = (int *)(base + cnt_off);
-    // only the term tables and the items need initial contents (counters are
-    // reset before every run)
-    for (size_t j = 0; j < b->jobs.size(); j++) {
-        const JL &l = lay[j];
-        if (cudaMemcpy(base + l.t_off, host.data() + l.t_off, l.ta.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess)
-            return bfail(b, HE_ERR_CUDA, "term upload");
-    }
-    if (cudaMemcpy(base + items_off, host.data() + items_off, off - items_off, cudaMemcpyHostToDevice) != cudaSuccess)
-        return bfail(b, HE_ERR_CUDA, "item upload");
     b->prepared = true;
     return HE_OK;
 }
@@ -249,7 +276,7 @@ int he_batch_run(he_batch *b, int mode, cudaStream_t st) {
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HE_ERR_CUDA, "cudaSetDevice");
     if (mode == HE_BATCH_PLAIN) {
         for (const auto &J : b->jobs) {
-            int rc = he_cpmul_conv(J.c, J.p, J.batch, J.ct_x, J.pt_w, nullptr, nullptr, J.ct_add, J.out, st);
+            int rc = he_cpmul_conv(J.c, J.p, J.batch, J.ct_x, J.pt_w, J.ct_w, J.pt_x, J.ct_add, J.out, st);
             if (rc) return bfail(b, rc, "plain job: " + J.c->err);
         }
         return HE_OK;
@@ -299,8 +326,8 @@ int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int ma
                 for (int rep = 0; rep < 3; rep++) {
                     cudaMemsetAsync(b->counters + 2 * i, 0, 2 * sizeof(int), st);
                     cudaEventRecord(e0, st);
-                    int rc = he::launch_queue(k.logN, mb, k.fi, k.nf, nullptr, 0, b->counters + 2 * i, b->n_sms * gm, st);
-                    if (!rc) rc = he::launch_queue(k.logN, mb, nullptr, 0, k.mi, k.nm, b->counters + 2 * i + 1,
+                    int rc = he::launch_queue(k.logN, mb, true, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * gm, st);
+                    if (!rc) rc = he::launch_queue(k.logN, mb, false, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
                                                    b->n_sms * gm, st);
                     cudaEventRecord(e1, st);
                     if (rc || cudaEventSynchronize(e1) != cudaSuccess) {

@@ -214,10 +214,35 @@ struct MacItem {            // multiply-accumulate + inverse NTT + add of one ou
     const u64 *add;         // this limb's addend or null
     const ModDev *mod;
 };
-// Persistent kernel over items (fi != null: forward items, else MAC items)
-// of ring degree 2^logN; minb selects the register budget (resident CTAs per
-// SM the kernel is compiled for); grid CTAs; *counter must be 0.
-int launch_queue(int logN, int minb, const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid,
+// One CPMul convolution job (he_cpmul_conv arguments) for the work-list forms.
+struct JobDesc {
+    he_ctx *c;
+    const he_plan *p;
+    int batch;
+    const u64 *ct_x, *pt_w, *ct_w, *pt_x, *ct_add;
+    u64 *out;
+};
+struct JobLayout {
+    size_t a_bytes, b_bytes, t_bytes;  // device scratch: ct NTT forms, pt NTT forms, term table (256-aligned)
+    size_t n_fwd, n_mac;               // work items the job adds
+};
+JobLayout job_layout(const JobDesc &J);
+// Work items of a job whose scratch starts at device address dev; terms gets
+// the host image of its term table (to be copied to dev + a_bytes + b_bytes).
+void job_items(const JobDesc &J, char *dev, std::vector<int32_t> &terms, std::vector<FwdItem> &F,
+               std::vector<MacItem> &M);
+
+// A contiguous array of work items and the launch-wide index of its first item.
+struct ItemSeg {
+    const void *items;
+    int begin;
+    int pad_;
+};
+// Persistent kernel over `total` items (fwd: FwdItem, else MacItem) held in
+// nseg segments sorted by begin (device table), ring degree 2^logN; minb
+// selects the register budget (resident CTAs per SM the kernel is compiled
+// for); grid CTAs; *counter must be 0.
+int launch_queue(int logN, int minb, bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
                  cudaStream_t st);
 
 // sampling (ChaCha20 streams): kinds

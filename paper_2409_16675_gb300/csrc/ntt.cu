@@ -285,23 +285,46 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
 }
 
 // ---------------------------------------------------------------- persistent queue kernels
-// Each CTA repeatedly takes the next item of a device work list (one atomic
-// per item) until the list is exhausted; items of one launch share the ring
+// Each CTA repeatedly takes the next item index of a launch (one atomic per
+// item) until all `total` items are done; items live in `nseg` segments (an
+// item array each, with the index of its first item) so a launch can cover
+// several independently built work lists.  Items of one launch share the ring
 // degree but may use any modulus of any context.  The counter must be zero
 // at launch.
+template <typename ITEM>
+__device__ __forceinline__ bool next_item(const ItemSeg *segs, int nseg, int total, int *counter, int *s_meta,
+                                          ITEM &out) {
+    if (threadIdx.x == 0) {
+        const int it = atomicAdd(counter, 1);
+        int sidx = 0;
+        if (it < total) {
+            int lo = 0, hi = nseg - 1;  // last segment whose begin <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (segs[mid].begin <= it) lo = mid;
+                else hi = mid - 1;
+            }
+            sidx = lo;
+        }
+        s_meta[0] = it;
+        s_meta[1] = sidx;
+    }
+    __syncthreads();
+    const int it = s_meta[0], sidx = s_meta[1];
+    __syncthreads();
+    if (it >= total) return false;
+    out = ((const ITEM *)segs[sidx].items)[it - segs[sidx].begin];
+    return true;
+}
+
 template <int LOGN, int MINB>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const FwdItem *__restrict__ items, int n,
-                                                                  int *counter) {
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const ItemSeg *__restrict__ segs, int nseg,
+                                                                  int total, int *counter) {
     extern __shared__ u64 sm[];
-    __shared__ int s_item;
+    __shared__ int s_meta[2];
     const int tau = threadIdx.x;
-    for (;;) {
-        if (tau == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= n) break;
-        const FwdItem I = items[it];
+    FwdItem I;
+    while (next_item<FwdItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
         u64 v[16];
         fwd_load<LOGN>(I.kind, I.src, I.t, M, tau, v);
@@ -311,19 +334,14 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const FwdItem 
 }
 
 template <int LOGN, int MINB>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const MacItem *__restrict__ items, int n,
-                                                                  int *counter) {
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg *__restrict__ segs, int nseg,
+                                                                  int total, int *counter) {
     extern __shared__ u64 sm[];
-    __shared__ int s_item;
+    __shared__ int s_meta[2];
     constexpr int T = Cfg<LOGN>::T;
     const int tau = threadIdx.x;
-    for (;;) {
-        if (tau == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
-        if (it >= n) break;
-        const MacItem I = items[it];
+    MacItem I;
+    while (next_item<MacItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
         u64 v[16];
         mac_accumulate<LOGN>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
@@ -403,7 +421,7 @@ int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) {
 }
 
 template <int LOGN, int MINB>
-static int queue_t(const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid, cudaStream_t st) {
+static int queue_t(bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
@@ -411,25 +429,25 @@ static int queue_t(const FwdItem *fi, int nf, const MacItem *mi, int nm, int *co
         cudaFuncSetAttribute(k_mac_queue<LOGN, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    if (fi) k_fwd_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(fi, nf, counter);
-    else k_mac_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(mi, nm, counter);
+    if (fwd) k_fwd_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+    else k_mac_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ERR_CUDA;
 }
 
-int launch_queue(int logN, int minb, const FwdItem *fi, int nf, const MacItem *mi, int nm, int *counter, int grid,
+int launch_queue(int logN, int minb, bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
                  cudaStream_t st) {
-    if ((fi ? nf : nm) <= 0) return HE_OK;
+    if (total <= 0 || nseg <= 0) return HE_OK;
     switch (logN * 2 + (minb >= 2 ? 1 : 0)) {
-    case 20: return queue_t<10, 1>(fi, nf, mi, nm, counter, grid, st);
-    case 21: return queue_t<10, 2>(fi, nf, mi, nm, counter, grid, st);
-    case 22: return queue_t<11, 1>(fi, nf, mi, nm, counter, grid, st);
-    case 23: return queue_t<11, 2>(fi, nf, mi, nm, counter, grid, st);
-    case 24: return queue_t<12, 1>(fi, nf, mi, nm, counter, grid, st);
-    case 25: return queue_t<12, 2>(fi, nf, mi, nm, counter, grid, st);
-    case 26: return queue_t<13, 1>(fi, nf, mi, nm, counter, grid, st);
-    case 27: return queue_t<13, 2>(fi, nf, mi, nm, counter, grid, st);
-    case 28: return queue_t<14, 1>(fi, nf, mi, nm, counter, grid, st);
-    case 29: return queue_t<14, 1>(fi, nf, mi, nm, counter, grid, st);
+    case 20: return queue_t<10, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 21: return queue_t<10, 2>(fwd, segs, nseg, total, counter, grid, st);
+    case 22: return queue_t<11, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 23: return queue_t<11, 2>(fwd, segs, nseg, total, counter, grid, st);
+    case 24: return queue_t<12, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 25: return queue_t<12, 2>(fwd, segs, nseg, total, counter, grid, st);
+    case 26: return queue_t<13, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 27: return queue_t<13, 2>(fwd, segs, nseg, total, counter, grid, st);
+    case 28: return queue_t<14, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 29: return queue_t<14, 1>(fwd, segs, nseg, total, counter, grid, st);
     }
     return HE_ERR_UNSUPPORTED_PARAMS;
 }

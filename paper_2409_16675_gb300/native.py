@@ -59,6 +59,18 @@ class he_batch_tuning(ctypes.Structure):
                 ("ms", ctypes.c_float), ("fwd_items", ctypes.c_int32), ("mac_items", ctypes.c_int32)]
 
 
+class he_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_double), ("max_group", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("poll_us", ctypes.c_int32)]
+
+
+class he_server_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("images", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("arena_peak_bytes", ctypes.c_double), ("arena_bytes", ctypes.c_double)]
+
+
 class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("encoding", "Cn", "G", "th", "tw", "Th", "Tw", "T", "Hn", "Wn",
                                               "Ooff", "O", "S", "Ho", "Wo", "Mn", "Sout", "MG")]
@@ -101,6 +113,15 @@ def _load():
         "he_batch_prepare": [vp],
         "he_batch_run": [vp, i32, vp],
         "he_batch_autotune": [vp, vp, ctypes.POINTER(he_batch_tuning), i32, ctypes.POINTER(i32)],
+        "he_batch_add_cpmul2": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp],
+        "he_server_create": [ctypes.POINTER(he_server_config), pp],
+        "he_server_submit": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)],
+        "he_server_poll": [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
+        "he_server_wait_all": [vp, ctypes.c_double],
+        "he_server_request_bytes": [vp, vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)],
+        "he_server_stats": [vp, ctypes.POINTER(he_server_report)],
+        "he_server_reset_stats": [vp],
+        "he_server_destroy": [vp],
         "he_trace_enable": [vp, i32],
         "he_trace_read": [vp, ctypes.POINTER(he_trace_entry), i32, ctypes.POINTER(i32)],
     }
@@ -326,3 +347,53 @@ def he_batch_last_error(b) -> str:
 
 def he_last_error(ctx=None) -> str:
     return last_error(ctx)
+
+
+def he_batch_add_cpmul2(b, ctx, plan, n_images, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out) -> int:
+    return _bcheck(lib.he_batch_add_cpmul2(b, ctx, plan, n_images, _ptr(ct_x), _ptr(pt_w), _ptr(ct_w), _ptr(pt_x),
+                                           _ptr(ct_add), _ptr(ct_out)), b)
+
+
+def he_server_create(device=0, hbm_budget_bytes=150e9, max_group=64, max_inflight=4, n_streams=4, poll_us=20):
+    cfg = he_server_config(device, float(hbm_budget_bytes), max_group, max_inflight, n_streams, poll_us)
+    h = ctypes.c_void_p()
+    _check(lib.he_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def he_server_submit(s, ctx, plan, n_images, ct_x, pt_w, ct_w, pt_x, ct_add, ct_out) -> int:
+    rid = ctypes.c_int64()
+    _check(lib.he_server_submit(s, ctx, plan, n_images, _ptr(ct_x), _ptr(pt_w), _ptr(ct_w), _ptr(pt_x), _ptr(ct_add),
+                                _ptr(ct_out), ctypes.byref(rid)))
+    return rid.value
+
+
+def he_server_poll(s, rid):
+    done = ctypes.c_int32()
+    lat = ctypes.c_double()
+    _check(lib.he_server_poll(s, rid, ctypes.byref(done), ctypes.byref(lat)))
+    return bool(done.value), lat.value
+
+
+def he_server_wait_all(s, timeout_s=600.0):
+    _check(lib.he_server_wait_all(s, timeout_s))
+
+
+def he_server_stats(s) -> dict:
+    st = he_server_report()
+    _check(lib.he_server_stats(s, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in he_server_report._fields_}
+
+
+def he_server_reset_stats(s):
+    _check(lib.he_server_reset_stats(s))
+
+
+def he_server_destroy(s):
+    _check(lib.he_server_destroy(s))
+
+
+def he_server_request_bytes(ctx, plan, n_images, has_x=True, has_w=True) -> float:
+    b = ctypes.c_double()
+    _check(lib.he_server_request_bytes(ctx, plan, n_images, int(has_x), int(has_w), ctypes.byref(b)), ctx)
+    return b.value

@@ -1,0 +1,94 @@
+"""Served form: continuous batching of CryptoTrain-P online layers from several
+clients (each with its own ring, keys and resident precomputed products).
+Every result is bit-identical to the same request run alone, decodes to the
+exact convolution, and admission respects the HBM budget."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import protocol  # noqa: E402
+from paper_2409_16675_gb300 import layer, native as nv, workloads as wl  # noqa: E402
+
+CLIENTS = [
+    (wl.RingSpec(4096, (40, 45, 50), 65537), wl.ConvShape(3, 12, 12, 5, 3, 1), "corr"),
+    (wl.RingSpec(8192, (50, 50, 50, 50), 1032193), wl.ConvShape(16, 8, 8, 16, 3, 1), "conv"),
+    (wl.RingSpec(16384, (60, 55), 65537), wl.ConvShape(5, 16, 16, 7, 5, 2), "corr"),
+]
+
+
+def setup_clients(B=2):
+    out = []
+    for i, (ring, shape, enc) in enumerate(CLIENTS):
+        ctx = layer.Context(ring)
+        keys = layer.Keys(ctx, 100 + i, True)
+        plan = layer.Plan(ctx, shape, enc)
+        pl = layer.PLayer(ctx, keys, plan, B)
+        x = torch.from_numpy(wl.activations(10 + i, (B, shape.C, shape.H, shape.W))).cuda()
+        w = torch.from_numpy(wl.weights(20 + i, (shape.M, shape.C, shape.h, shape.h))).cuda()
+        seeds = wl.protocol_seeds(30 + i)
+        pl.client_prepare(x, w, seeds)
+        pl.offline()                      # [r^x r^w] resident on the device
+        pl.online()                       # reference: the request run alone
+        torch.cuda.synchronize()
+        out.append((ctx, keys, plan, pl, x, w))
+    return out
+
+
+def test_server_results_equal_alone_and_decode():
+    clients = setup_clients()
+    srv = nv.he_server_create(0, hbm_budget_bytes=4e9, max_group=8, max_inflight=3, n_streams=3)
+    outs, ids = [], []
+    for rep in range(3):                 # several requests per client, interleaved
+        for (ctx, keys, plan, pl, x, w) in clients:
+            b = pl.buf
+            o = torch.zeros_like(b.out)
+            ids.append(nv.he_server_submit(srv, ctx.h, plan.h, pl.B, b.ct_x, b.wm, b.ct_w, b.xm, b.rr, o))
+            outs.append((pl, o))
+    nv.he_server_wait_all(srv, 120.0)
+    st = nv.he_server_stats(srv)
+    assert st["completed"] == len(ids) and st["p50_us"] > 0 and st["p99_us"] >= st["p50_us"]
+    for rid in ids:
+        done, lat = nv.he_server_poll(srv, rid)
+        assert done and lat > 0
+    for pl, o in outs:
+        assert torch.equal(o, pl.buf.out)           # same bits as the request alone
+    # decode one result per client: the exact convolution
+    for (ctx, keys, plan, pl, x, w), (pl2, o) in zip(clients, outs[:len(clients)]):
+        pl.buf.out.copy_(o)
+        y = pl.client_finish().cpu().numpy()
+        xs, ws = x.cpu().numpy(), w.cpu().numpy()
+        for bb in range(pl.B):
+            assert np.array_equal(y[bb], protocol.conv_reference(xs[bb], ws, plan.shape.pad))
+    nv.he_server_destroy(srv)
+
+
+def test_server_admission_under_a_small_budget():
+    clients = setup_clients()
+    need = [nv.he_server_request_bytes(c.h, p.h, l.B) for (c, k, p, l, _, _) in clients]
+    # a budget that holds only about one request at a time (plus item lists)
+    budget = 1.3 * max(need) + (1 << 20)
+    srv = nv.he_server_create(0, hbm_budget_bytes=budget, max_group=4, max_inflight=2, n_streams=2)
+    outs = []
+    for rep in range(3):
+        for (c, k, p, l, _, _) in clients:
+            o = torch.zeros_like(l.buf.out)
+            nv.he_server_submit(srv, c.h, p.h, l.B, l.buf.ct_x, l.buf.wm, l.buf.ct_w, l.buf.xm, l.buf.rr, o)
+            outs.append((l, o))
+    # a request that could never fit is refused at submission (sizes are
+    # checked before any buffer is touched)
+    ctx, keys, plan, pl, x, w = clients[2]
+    with pytest.raises(nv.HEError) as e:
+        nv.he_server_submit(srv, ctx.h, plan.h, 4096, pl.buf.ct_x, pl.buf.wm, pl.buf.ct_w, pl.buf.xm, pl.buf.rr,
+                            torch.zeros_like(pl.buf.out))
+    assert e.value.code == -5
+    nv.he_server_wait_all(srv, 120.0)
+    st = nv.he_server_stats(srv)
+    assert st["completed"] == len(outs) and st["arena_peak_bytes"] <= st["arena_bytes"]
+    for l, o in outs:
+        assert torch.equal(o, l.buf.out)
+    nv.he_server_destroy(srv)
