@@ -40,10 +40,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched"],
+    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve"],
                     help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
                          "train: one CNN training step's eight linear operations, batch 64; "
-                         "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph")
+                         "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph; "
+                         "serve: 64 clients, Poisson arrivals swept over --rates, p50/p99 latency")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000,6000", help="serve: arrival rates (req/s)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: measured seconds per rate")
+    ap.add_argument("--serve-warmup", type=float, default=1.0, help="serve: warm-up seconds per rate")
+    ap.add_argument("--hbm-budget-gb", type=float, default=150.0, help="serve: admission budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -386,10 +391,145 @@ def run_batched(args):
     nv.he_batch_destroy(b)
 
 
+def run_serve(args):
+    """Served form: 64 clients, each with its own ring (N in {4096, 8192,
+    16384}, 2-8 limbs of 36-60 bits), keys, plan and layer (shapes as in the
+    batched form), whose encrypted inputs, masked plaintexts and precomputed
+    [r^x r^w] stay resident on the device.  One request is the online phase
+    of one CryptoTrain-P layer (two CPMuls and the precomputed add, one
+    image).  Requests arrive open-loop as a Poisson process at each rate; a
+    client holds at most DEPTH requests in flight (one output buffer each) and
+    an arrival that finds all of them busy is shed.  Reported per rate: layers
+    per second (completions over the span from first submission to last
+    completion), p50/p99 latency (submission to completion), shed arrivals;
+    plus the saturated throughput of the server against one he_cpmul_conv
+    call per request on one stream (the plain launch), and whether every
+    sampled result equals the request run alone."""
+    import numpy as np
+    import torch
+
+    from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
+
+    DEPTH = 4
+    t0 = time.perf_counter()
+    clients = []
+    for j in wl.served_clients():
+        s = j.shape
+        ctx = layer.Context(j.ring)
+        keys = layer.Keys(ctx, j.seed, True)
+        plan = layer.Plan(ctx, s, j.encoding)
+        pl = layer.PLayer(ctx, keys, plan, 1)
+        x = torch.from_numpy(wl.activations(j.seed + 1, (1, s.C, s.H, s.W))).cuda()
+        w = torch.from_numpy(wl.weights(j.seed + 2, (s.M, s.C, s.h, s.h))).cuda()
+        pl.client_prepare(x, w, wl.protocol_seeds(j.seed))
+        pl.offline()                          # [r^x r^w], resident
+        pl.online()                           # the request alone: pl.buf.out
+        clients.append((ctx, keys, plan, pl, [torch.empty_like(pl.buf.out) for _ in range(DEPTH)]))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    resident = torch.cuda.memory_allocated()
+
+    def submit(srv, ci, slot):
+        ctx, keys, plan, pl, outs = clients[ci]
+        b = pl.buf
+        return nv.he_server_submit(srv, ctx.h, plan.h, 1, b.ct_x, b.wm, b.ct_w, b.xm, b.rr, outs[slot])
+
+    # plain launch: one he_cpmul_conv per request, one stream
+    reps = 3
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for _ in range(2):
+            for (ctx, keys, plan, pl, outs) in clients:
+                b = pl.buf
+                nv.he_cpmul_conv(ctx.h, plan.h, 1, b.ct_x, b.wm, b.ct_w, b.xm, b.rr, outs[0])
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            for (ctx, keys, plan, pl, outs) in clients:
+                b = pl.buf
+                nv.he_cpmul_conv(ctx.h, plan.h, 1, b.ct_x, b.wm, b.ct_w, b.xm, b.rr, outs[0])
+        e1.record(st)
+        st.synchronize()
+    plain_lps = reps * len(clients) / (e0.elapsed_time(e1) / 1000.0)
+
+    srv = nv.he_server_create(0, hbm_budget_bytes=args.hbm_budget_gb * 1e9, max_group=64, max_inflight=4,
+                              n_streams=4, poll_us=20)
+    # saturation: every client submits DEPTH requests at once
+    for rep in range(2):
+        nv.he_server_reset_stats(srv)
+        for slot in range(DEPTH):
+            for ci in range(len(clients)):
+                submit(srv, ci, slot)
+        nv.he_server_wait_all(srv, 600.0)
+        sat = nv.he_server_stats(srv)
+    sat_lps = sat["completed"] / sat["span_s"]
+    same = all(torch.equal(outs[k], pl.buf.out) for (_, _, _, pl, outs) in clients for k in range(DEPTH))
+
+    sweep = []
+    gpu = int(os.environ.get("LOCAL_RANK", "0"))
+    with ClockSampler(gpu) as clk:
+        for ri, rate in enumerate(float(r) for r in args.rates.split(",")):
+            times, who = wl.poisson_arrivals(wl.MASTER_SEED + 50 + ri, rate,
+                                             args.serve_warmup + args.serve_seconds, len(clients))
+            inflight = [[] for _ in clients]          # (request id, slot)
+            shed, lag, measured = 0, [], False
+            start = time.perf_counter()
+            for tt, ci in zip(times, who):
+                if not measured and tt >= args.serve_warmup:
+                    nv.he_server_reset_stats(srv)
+                    measured = True
+                while True:
+                    dt = start + tt - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    if dt > 2e-4:
+                        time.sleep(dt - 1e-4)
+                inflight[ci] = [(r, k) for (r, k) in inflight[ci] if not nv.he_server_poll(srv, r)[0]]
+                if len(inflight[ci]) >= DEPTH:
+                    if measured:
+                        shed += 1
+                    continue
+                busy = {k for _, k in inflight[ci]}
+                slot = next(k for k in range(DEPTH) if k not in busy)
+                inflight[ci].append((submit(srv, ci, int(slot)), slot))
+                if measured:
+                    lag.append(time.perf_counter() - (start + tt))
+            nv.he_server_wait_all(srv, 600.0)
+            r = nv.he_server_stats(srv)
+            same = same and all(torch.equal(outs[k], pl.buf.out)
+                                for (_, _, _, pl, outs) in clients[:: 7] for k in range(DEPTH))
+            sweep.append({"rate": rate, "completed": r["completed"], "shed": shed,
+                          "layers_per_s": r["completed"] / r["span_s"] if r["span_s"] > 0 else 0.0,
+                          "p50_ms": r["p50_us"] / 1e3, "p99_ms": r["p99_us"] / 1e3, "max_ms": r["max_us"] / 1e3,
+                          "groups": r["groups"], "arena_peak_gb": r["arena_peak_bytes"] / 1e9,
+                          "submit_lag_p99_ms": float(np.percentile(lag, 99)) * 1e3 if lag else None})
+    nv.he_server_destroy(srv)
+    print(json.dumps({
+        "metric": "served CryptoTrain-P layers/s with p50/p99 latency (64 clients, Poisson arrivals)",
+        "unit": "layers/s", "value": sat_lps, "higher_is_better": True, "n_gpus": 1, "dtype": "u64",
+        "data": "synthetic", "plain_launch_layers_per_s": plain_lps, "speedup_vs_plain": sat_lps / plain_lps,
+        "saturation": {"requests": sat["completed"], "p50_ms": sat["p50_us"] / 1e3, "p99_ms": sat["p99_us"] / 1e3,
+                       "groups": sat["groups"]},
+        "sweep": sweep, "identical_results": bool(same), "clocks": clk.summary(),
+        "setup_s": setup_s, "resident_gb": resident / 1e9,
+        "config": {"workload": "64 clients, N 4096/8192/16384, 2-8 limbs of 36-60 bits, batched-form shapes, "
+                               "one image per request",
+                   "hbm_budget_gb": args.hbm_budget_gb, "seconds_per_rate": args.serve_seconds,
+                   "warmup_s_per_rate": args.serve_warmup, "max_requests_per_client": DEPTH}}), flush=True)
+    for (ctx, keys, plan, pl, outs) in clients:
+        keys.close()
+        plan.close()
+        ctx.close()
+
+
 def main():
     args = parse()
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -161,3 +161,22 @@ def batched_jobs(seed: int = MASTER_SEED + 4, n_jobs: int = 256, channels=(3, 16
         enc = "corr" if r.integers(0, 2) else "conv"
         jobs.append(BatchJob(RingSpec(N, pb, 65537), ConvShape(C, H, H, M, h, (h - 1) // 2), enc, seed * 1000 + j))
     return jobs
+
+
+def served_clients(seed: int = MASTER_SEED + 5, n_clients: int = 64):
+    """Clients of the served form: each owns one layer drawn as in the batched
+    form (channels {3,16,32,64,128}, spatial {8,16,32}, kernel {1,3,5}, both
+    encodings) on its own ring: N uniform over {4096, 8192, 16384}, 2-8 limbs
+    whose prime sizes are uniform in [36, 60] bits, t = 65537."""
+    return batched_jobs(seed=seed, n_jobs=n_clients, degrees=(4096, 8192, 16384), limbs=(2, 8), bits=(36, 60))
+
+
+def poisson_arrivals(seed: int, rate: float, seconds: float, n_clients: int):
+    """Open-loop arrivals: exponential inter-arrival times of mean 1/rate over
+    `seconds`, each arrival from a client drawn uniformly; returns (times,
+    clients) as numpy arrays."""
+    r = rng(seed)
+    n = int(rate * seconds * 1.5) + 16
+    t = np.cumsum(r.exponential(1.0 / rate, size=n))
+    t = t[t < seconds]
+    return t, r.integers(0, n_clients, size=len(t))
