@@ -98,6 +98,7 @@ struct he_batch {
         const he::MacItem *mi;
         int nm;
         const he::ItemSeg *fseg, *mseg;  // one-segment tables (device)
+        bool lazy = true;                // every job's moduli below 2^57
         int minb = 2;
         int grid_mult = 2;
         float best_ms = 0;
@@ -124,12 +125,12 @@ int run_persistent(he_batch *b, cudaStream_t st) {
         return bfail(b, HE_ERR_CUDA, "counter reset");
     for (size_t i = 0; i < b->classes.size(); i++) {
         const auto &k = b->classes[i];
-        int rc = he::launch_queue(k.logN, k.minb, true, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * k.grid_mult, st);
+        int rc = he::launch_queue(k.logN, k.minb, true, k.lazy, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * k.grid_mult, st);
         if (rc) return bfail(b, rc, "forward queue launch");
     }
     for (size_t i = 0; i < b->classes.size(); i++) {
         const auto &k = b->classes[i];
-        int rc = he::launch_queue(k.logN, k.minb, false, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
+        int rc = he::launch_queue(k.logN, k.minb, false, k.lazy, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
                                   b->n_sms * k.grid_mult, st);
         if (rc) return bfail(b, rc, "multiply-accumulate queue launch");
     }
@@ -257,6 +258,8 @@ int he_batch_prepare(he_batch *b) {
         k.mseg = k.fseg + 1;
         segs.push_back({k.fi, 0, 0});
         segs.push_back({k.mi, 0, 0});
+        for (const auto &J : b->jobs)
+            if (J.c->logN == k.logN && !he::ctx_lazy(J.c)) k.lazy = false;
         k.minb = k.logN >= 14 ? 1 : 2;
         k.grid_mult = k.minb;
         fo += F[ci].size() * sizeof(he::FwdItem);
@@ -326,8 +329,8 @@ int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int ma
                 for (int rep = 0; rep < 3; rep++) {
                     cudaMemsetAsync(b->counters + 2 * i, 0, 2 * sizeof(int), st);
                     cudaEventRecord(e0, st);
-                    int rc = he::launch_queue(k.logN, mb, true, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * gm, st);
-                    if (!rc) rc = he::launch_queue(k.logN, mb, false, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
+                    int rc = he::launch_queue(k.logN, mb, true, k.lazy, k.fseg, 1, k.nf, b->counters + 2 * i, b->n_sms * gm, st);
+                    if (!rc) rc = he::launch_queue(k.logN, mb, false, k.lazy, k.mseg, 1, k.nm, b->counters + 2 * i + 1,
                                                    b->n_sms * gm, st);
                     cudaEventRecord(e1, st);
                     if (rc || cudaEventSynchronize(e1) != cudaSuccess) {

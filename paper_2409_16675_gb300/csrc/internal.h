@@ -241,9 +241,12 @@ struct ItemSeg {
 // Persistent kernel over `total` items (fwd: FwdItem, else MacItem) held in
 // nseg segments sorted by begin (device table), ring degree 2^logN; minb
 // selects the register budget (resident CTAs per SM the kernel is compiled
-// for); grid CTAs; *counter must be 0.
-int launch_queue(int logN, int minb, bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
-                 cudaStream_t st);
+// for); lazy only when every item's modulus is below 2^57; grid CTAs;
+// *counter must be 0.
+int launch_queue(int logN, int minb, bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter,
+                 int grid, cudaStream_t st);
+// true when every limb modulus of the context is below 2^57
+bool ctx_lazy(const he_ctx *c);
 
 // sampling (ChaCha20 streams): kinds
 enum SampleKind { SAMPLE_TERNARY = 0, SAMPLE_CBD = 1, SAMPLE_UNIFORM_Q = 2, SAMPLE_UNIFORM_T = 3 };

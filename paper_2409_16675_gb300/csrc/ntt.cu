@@ -25,6 +25,11 @@
 
 namespace he {
 
+// Coefficients per 128-bit accumulator group of the multiply-accumulate: 4
+// when the register budget is 64 per thread (resident threads per SM =
+// 1024), else 8.
+__host__ __device__ constexpr int mac_group(int threads, int minb) { return threads * minb >= 1024 ? 4 : 8; }
+
 template <int LOGN>
 struct Cfg {
     static constexpr int N = 1 << LOGN;
@@ -153,6 +158,7 @@ template <int LOGN, bool LAZY>
 __device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int tau, const ModDev &M, u64 *d) {
     constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     int lo = LOGN - 4;
+#pragma unroll
     for (int pass = 0; pass < NP - 1; pass++) {
         fwd_pass<LOGN, 4, LAZY>(v, tau, lo, 4 * pass, M);
         const int lo_next = pass == NP - 2 ? 0 : lo - 4;
@@ -165,23 +171,23 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int t
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
-// in two halves of 8 coefficients (128-bit sums), result fully reduced
-template <int LOGN>
+// in groups of CH coefficients (128-bit sums), result fully reduced
+template <int LOGN, int CH>
 __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const u64 *__restrict__ B,
                                                const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int t0,
                                                int t1, int limb, const ModDev &M, int tau, u64 (&v)[16]) {
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T;
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
-        u64 lo[8], hi[8];
+    for (int part = 0; part < 16 / CH; part++) {
+        u64 lo[CH], hi[CH];
 #pragma unroll
-        for (int kk = 0; kk < 8; kk++) { lo[kk] = 0; hi[kk] = 0; }
+        for (int kk = 0; kk < CH; kk++) { lo[kk] = 0; hi[kk] = 0; }
         int cnt = 0;
         for (int tk = t0; tk < t1; tk++) {
-            const u64 *a = A + ((long long)ta[tk] + limb) * N + half * 8 * T + tau;
-            const u64 *b = B + ((long long)tb[tk] + limb) * N + half * 8 * T + tau;
+            const u64 *a = A + ((long long)ta[tk] + limb) * N + part * CH * T + tau;
+            const u64 *b = B + ((long long)tb[tk] + limb) * N + part * CH * T + tau;
 #pragma unroll
-            for (int kk = 0; kk < 8; kk++) {
+            for (int kk = 0; kk < CH; kk++) {
                 u64 pl, ph;
                 mul128(a[kk * T], b[kk * T], pl, ph);
                 lo[kk] += pl;
@@ -189,12 +195,12 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
             }
             if (++cnt == 15) {  // products < 2^124: fold before the 128-bit sum can overflow
 #pragma unroll
-                for (int kk = 0; kk < 8; kk++) { lo[kk] = reduce128(lo[kk], hi[kk], M); hi[kk] = 0; }
+                for (int kk = 0; kk < CH; kk++) { lo[kk] = reduce128(lo[kk], hi[kk], M); hi[kk] = 0; }
                 cnt = 0;
             }
         }
 #pragma unroll
-        for (int kk = 0; kk < 8; kk++) v[half * 8 + kk] = reduce128(lo[kk], hi[kk], M);
+        for (int kk = 0; kk < CH; kk++) v[part * CH + kk] = reduce128(lo[kk], hi[kk], M);
     }
 }
 
@@ -207,6 +213,7 @@ __device__ __forceinline__ void inv_transform(u64 (&v)[16], u64 *sm, int tau, co
     constexpr int NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
     inv_pass<4, 0, LAZY>(v, tau, 0, 0, M);
     int lo = 0;
+#pragma unroll
     for (int pass = 1; pass < NP - 1; pass++) {
         exchange(sm, v, tau, lo, 4 * pass);
         lo = 4 * pass;
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJ
     const int o = blockIdx.x - limb * J.n_out;
     const ModDev M = mods[J.mod_base + limb];
     u64 v[16];
-    mac_accumulate<LOGN>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
+    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
     inv_transform<LOGN, LAZY>(v, sm, tau, M);
     // natural order: element j = k*T + tau
     const u64 q = M.q;
@@ -317,7 +324,8 @@ __device__ __forceinline__ bool next_item(const ItemSeg *segs, int nseg, int tot
     return true;
 }
 
-template <int LOGN, int MINB>
+// LAZY: every item's modulus is below 2^57 (checked by the host per launch)
+template <int LOGN, int MINB, bool LAZY>
 __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const ItemSeg *__restrict__ segs, int nseg,
                                                                   int total, int *counter) {
     extern __shared__ u64 sm[];
@@ -328,12 +336,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const ItemSeg 
         const ModDev M = *I.mod;
         u64 v[16];
         fwd_load<LOGN>(I.kind, I.src, I.t, M, tau, v);
-        if (M.q < (1ull << 57)) fwd_transform_store<LOGN, true>(v, sm, tau, M, I.dst);
-        else fwd_transform_store<LOGN, false>(v, sm, tau, M, I.dst);
+        fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, I.dst);
     }
 }
 
-template <int LOGN, int MINB>
+template <int LOGN, int MINB, bool LAZY>
 __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg *__restrict__ segs, int nseg,
                                                                   int total, int *counter) {
     extern __shared__ u64 sm[];
@@ -344,9 +351,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg 
     while (next_item<MacItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
         u64 v[16];
-        mac_accumulate<LOGN>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
-        if (M.q < (1ull << 57)) inv_transform<LOGN, true>(v, sm, tau, M);
-        else inv_transform<LOGN, false>(v, sm, tau, M);
+        mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
+        inv_transform<LOGN, LAZY>(v, sm, tau, M);
         const u64 q = M.q;
 #pragma unroll
         for (int k = 0; k < 16; k++) {
@@ -365,6 +371,8 @@ static bool lazy_ok(const he_ctx *c, int mod_base, int n_limbs) {
         if (c->h_mods[mod_base + i].q >= (1ull << 57)) return false;  // 57 q < 2^63
     return true;
 }
+
+bool ctx_lazy(const he_ctx *c) { return lazy_ok(c, 0, c->L); }
 
 template <int LOGN>
 static int fwd_t(he_ctx *c, const FwdJob &j, cudaStream_t st) {
@@ -420,34 +428,41 @@ int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) {
     return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
 }
 
-template <int LOGN, int MINB>
-static int queue_t(bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid, cudaStream_t st) {
+template <int LOGN, int MINB, bool LAZY>
+static int queue_l(bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_fwd_queue<LOGN, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_mac_queue<LOGN, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_fwd_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mac_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    if (fwd) k_fwd_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
-    else k_mac_queue<LOGN, MINB><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+    if (fwd) k_fwd_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+    else k_mac_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ERR_CUDA;
 }
 
-int launch_queue(int logN, int minb, bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
-                 cudaStream_t st) {
+template <int LOGN, int MINB>
+static int queue_t(bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
+                   cudaStream_t st) {
+    return lazy ? queue_l<LOGN, MINB, true>(fwd, segs, nseg, total, counter, grid, st)
+                : queue_l<LOGN, MINB, false>(fwd, segs, nseg, total, counter, grid, st);
+}
+
+int launch_queue(int logN, int minb, bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter,
+                 int grid, cudaStream_t st) {
     if (total <= 0 || nseg <= 0) return HE_OK;
     switch (logN * 2 + (minb >= 2 ? 1 : 0)) {
-    case 20: return queue_t<10, 1>(fwd, segs, nseg, total, counter, grid, st);
-    case 21: return queue_t<10, 2>(fwd, segs, nseg, total, counter, grid, st);
-    case 22: return queue_t<11, 1>(fwd, segs, nseg, total, counter, grid, st);
-    case 23: return queue_t<11, 2>(fwd, segs, nseg, total, counter, grid, st);
-    case 24: return queue_t<12, 1>(fwd, segs, nseg, total, counter, grid, st);
-    case 25: return queue_t<12, 2>(fwd, segs, nseg, total, counter, grid, st);
-    case 26: return queue_t<13, 1>(fwd, segs, nseg, total, counter, grid, st);
-    case 27: return queue_t<13, 2>(fwd, segs, nseg, total, counter, grid, st);
-    case 28: return queue_t<14, 1>(fwd, segs, nseg, total, counter, grid, st);
-    case 29: return queue_t<14, 1>(fwd, segs, nseg, total, counter, grid, st);
+    case 20: return queue_t<10, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 21: return queue_t<10, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 22: return queue_t<11, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 23: return queue_t<11, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 24: return queue_t<12, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 25: return queue_t<12, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 26: return queue_t<13, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 27: return queue_t<13, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 28: return queue_t<14, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 29: return queue_t<14, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
     }
     return HE_ERR_UNSUPPORTED_PARAMS;
 }

@@ -207,12 +207,17 @@ int launch_group(he_server *s, std::vector<int64_t> &ids, he_server::Flight &f) 
     char *ctl = s->arena_base + s->slots_off + (size_t)f.slot * s->slot_bytes;
     if (cudaMemcpyAsync(ctl, h, s->slot_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return HE_ERR_CUDA;
     int *counters = (int *)ctl;
+    std::vector<char> lazy(degrees.size(), 1);
+    for (int64_t id : ids) {
+        const he_ctx *c = s->reqs[id].J.c;
+        if (!he::ctx_lazy(c)) lazy[std::find(degrees.begin(), degrees.end(), c->logN) - degrees.begin()] = 0;
+    }
     for (int pass = 0; pass < 2; pass++)
         for (size_t i = 0; i < degrees.size(); i++) {
             const int k = 2 * (int)i + pass;
             const int mb = degrees[i] >= 14 ? 1 : 2;
             const he::ItemSeg *segs = (const he::ItemSeg *)(ctl + seg_base + k * per_table);
-            int rc = he::launch_queue(degrees[i], mb, pass == 0, segs, nseg[k], total[k], counters + k,
+            int rc = he::launch_queue(degrees[i], mb, pass == 0, lazy[i] != 0, segs, nseg[k], total[k], counters + k,
                                       s->n_sms * 2, st);
             if (rc) return rc;
         }
