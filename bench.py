@@ -36,7 +36,7 @@ UNIT = "layers/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
@@ -53,13 +53,6 @@ def parse():
     return ap.parse_args()
 
 
-def dist_info():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -70,7 +63,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    """nvidia-smi clock / throttle samples every 50 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,7 +77,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -150,7 +143,8 @@ def cpu_oracle_layers(seconds_budget: float, steps: int = 1):
 
 
 def run_reference(args):
-    ws, rank, _ = dist_info()
+    from paper_2409_16675_gb300 import dist as hd
+    ws, rank, _ = hd.world()
     if rank != 0:
         return
     from paper_2409_16675_gb300 import workloads as wl
@@ -171,7 +165,8 @@ def run_reference(args):
 def run_gpu(args):
     import torch
 
-    ws, rank, local = dist_info()
+    from paper_2409_16675_gb300 import dist as hd
+    ws, rank, local = hd.world()
     torch.cuda.set_device(local)
     pg = None
     if ws > 1:
@@ -184,7 +179,7 @@ def run_gpu(args):
     s = w.shape
     B = args.batch
     ctx = layer.Context(w.ring, device=local)
-    keys = layer.Keys(ctx, w.seed * 7 + 1 + 1000 * rank, True)
+    keys = layer.Keys(ctx, hd.rank_seed(w.seed * 7 + 1, rank), True)
     plan = layer.Plan(ctx, s, w.encoding)
     pl = layer.PLayer(ctx, keys, plan, B)
     x_h, k_h = wl.layer_inputs(w, B)
@@ -195,15 +190,14 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def step(i):
-        return pl.step(x, k, wl.protocol_seeds(w.seed + 17 * i + 100003 * rank))
+        return pl.step(x, k, wl.protocol_seeds(hd.rank_seed(w.seed + 17 * i, rank)))
 
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
 
     def barrier():
-        if pg:
-            pg.barrier()
+        hd.barrier()
         torch.cuda.synchronize()
 
     # ---- device-resident timed region
@@ -219,13 +213,9 @@ def run_gpu(args):
     barrier()
     nv.he_trace_enable(ctx.h, False)
     trace = nv.he_trace_read(ctx.h)
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = hd.reduce_max(ev0.elapsed_time(ev1), device="cuda")
     ms_step = ms / args.steps
-    value = ws * B * args.steps / (ms / 1000.0)
+    value = hd.whole_job_rate(B * args.steps, ws, ms / 1000.0)
 
     # ---- end to end through the API with host buffers
     xp = torch.from_numpy(x_h).pin_memory()
@@ -236,7 +226,7 @@ def run_gpu(args):
     def e2e_step(i):
         xd.copy_(xp, non_blocking=True)
         kd.copy_(kp, non_blocking=True)
-        y = pl.step(xd, kd, wl.protocol_seeds(w.seed + 31 * i + 100003 * rank))
+        y = pl.step(xd, kd, wl.protocol_seeds(hd.rank_seed(w.seed + 31 * i, rank)))
         yp.copy_(y, non_blocking=True)
 
     for i in range(max(1, args.warmup)):
@@ -249,12 +239,8 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ems = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ems], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ems = float(t.item())
-    e2e_value = ws * B * args.steps / (ems / 1000.0)
+    ems = hd.reduce_max(e0.elapsed_time(e1), device="cuda")
+    e2e_value = hd.whole_job_rate(B * args.steps, ws, ems / 1000.0)
 
     if rank != 0:
         if pg:
@@ -262,13 +248,26 @@ def run_gpu(args):
         return
     # ---- roofline of the dominant kernel family
     peak, peak_kind = peaks()
+    clocks = clk.summary()
     dom = max(trace.items(), key=lambda kv: kv[1][1])
     name, (launches, tot_ms, byt, mm) = dom
-    achieved = byt / (tot_ms / 1000.0) / 1e9
-    roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-            "avg_launch_us": 1000.0 * tot_ms / launches,
-            "modmul_rate_T_per_s": mm / (tot_ms / 1000.0) / 1e12}
+    gbs = byt / (tot_ms / 1000.0) / 1e9
+    # The NTT / multiply-accumulate kernels are bound by the integer multiply
+    # pipe, not by HBM: peak = SMs x 64 IMAD lanes per cycle x SM clock / 10
+    # (the 32-bit multiplies of one 64-bit Shoup modular product); achieved =
+    # algorithmic modular products (butterflies, untwist/scaling products, MAC
+    # terms) per second over the kernel's event-timed launches.
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 64 * mhz * 1e6 / 10 / 1e12
+    alu = mm / (tot_ms / 1000.0) / 1e12
+    roof = {"kernel": name, "bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tmodmul/s",
+            "frac": alu / alu_peak,
+            "peak_source": "derived: %d SMs x 64 IMAD lanes/cycle x %.0f MHz / 10 IMAD per 64-bit modular product"
+                           % (sms, mhz),
+            "traffic": None, "launches": launches, "avg_launch_us": 1000.0 * tot_ms / launches,
+            "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind}}
     kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(u[1] for u in trace.values()),
                    "GB/s": v[2] / (v[1] / 1000.0) / 1e9 if v[1] else None} for k, v in trace.items()}
     launches_total = sum(v[0] for v in trace.values())
@@ -278,7 +277,7 @@ def run_gpu(args):
             "config": {"workload": w.name, "batch": B, "N": w.ring.N, "L": w.ring.L, "t": w.ring.t,
                        "encoding": w.encoding, "parallelism": "independent batches per GPU" if ws > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (working set of one step > 129 MB)"},
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_h.nbytes + k_h.nbytes),
                     "d2h_bytes_per_step": int(yp.numel() * 8)},
             "gpu_launches": int(launches_total),
