@@ -29,6 +29,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per launch of the k_mac_intt family in this
+# workload, averaged over its launches in one ncu capture of this command
+# (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
+MAC_INTT_TRAFFIC = 324.47e6
+
 METRIC = "Encrypted conv layers/s & NTT HBM GB/s (% of peak) vs plain launch; p50/p99 latency"
 UNIT = "layers/s"
 
@@ -265,7 +270,8 @@ def run_gpu(args):
             "frac": alu / alu_peak,
             "peak_source": "derived: %d SMs x 64 IMAD lanes/cycle x %.0f MHz / 10 IMAD per 64-bit modular product"
                            % (sms, mhz),
-            "traffic": None, "launches": launches, "avg_launch_us": 1000.0 * tot_ms / launches,
+            "traffic": MAC_INTT_TRAFFIC if name == "mac_intt" else None,
+            "launches": launches, "avg_launch_us": 1000.0 * tot_ms / launches,
             "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                     "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind}}
     kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(u[1] for u in trace.values()),

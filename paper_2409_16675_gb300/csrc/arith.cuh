@@ -69,6 +69,17 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const ModDev &M) {
     r = r >= M.twoq ? r - M.twoq : r;
     return red1(r, M.q);
 }
+// x mod q for x < 64 q, fully reduced, from a single-precision quotient
+// estimate: every rounding is toward zero and qf <= 2^qsh / q, so the
+// estimate never exceeds floor(x / q); its relative error (< 2^-21) and the
+// dropped low bits (< 2^qsh, at most 2^-25 q) keep it at least floor(x/q) - 1
+// below 64, so one conditional subtraction finishes.  The conversions run on
+// the conversion unit, leaving the integer multiply pipe two multiplies.
+__device__ __forceinline__ u64 reduce_small(u64 x, const ModDev &M) {
+    const uint32_t xh = (uint32_t)(x >> M.qsh);
+    const uint32_t k = __float2uint_rz(__fmul_rz(__uint2float_rz(xh), M.qf));
+    return red1(x - (u64)k * M.q, M.q);
+}
 // a (< 2^64) mod q given r64-style constants, fully reduced
 __device__ __forceinline__ u64 reduce64(u64 a, u64 q, u64 one_s) { return red1(shoup(a, 1, one_s, q), q); }
 

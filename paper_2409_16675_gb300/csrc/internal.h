@@ -33,6 +33,8 @@ struct ModDev {
     u64 one_s;         // floor(2^64 / q): Shoup companion of 1
     u64 ninv, ninvs;   // N^-1 mod q
     const ulonglong2 *fw, *iw, *z;
+    float qf;          // 2^qsh / q in single precision, rounded down
+    int qsh;           // max(0, bitlen(q) + 6 - 32): x >> qsh fits 32 bits for x < 64 q
 };
 
 // A CRT basis {m_i}: M = prod m_i, hat_i = M / m_i, inv_i = hat_i^-1 mod m_i.

@@ -167,7 +167,7 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int t
     }
     fwd_pass<LOGN, RL, LAZY>(v, tau, 0, 4 * (NP - 1), M);
 #pragma unroll
-    for (int k = 0; k < 16; k++) d[k * T + tau] = reduce64(v[k], M.q, M.one_s);  // from [0, 57q) or [0, 8q)
+    for (int k = 0; k < 16; k++) d[k * T + tau] = reduce_small(v[k], M);  // from [0, 57q) or [0, 8q)
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,

@@ -4,6 +4,7 @@
 // he_setup; everything it computes is uploaded to the device.
 #include <cstring>
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
@@ -196,6 +197,15 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     M.iw = M.fw + N;
     M.z = M.iw + N;
     M.nq = 0 - q;
+    {
+        int bq = 0;
+        while (bq < 64 && (q >> bq)) bq++;
+        M.qsh = bq + 6 > 32 ? bq + 6 - 32 : 0;
+        const double d = std::ldexp(1.0, M.qsh) / (double)q;
+        float f = (float)d;
+        while ((double)f > d * (1.0 - 1e-12)) f = std::nextafter(f, 0.0f);  // round down, with margin
+        M.qf = f;
+    }
     c->h_mods.push_back(M);
     return true;
 }
