@@ -160,6 +160,15 @@ int he_keys_export(he_ctx *ctx, const he_keys *keys, int which, void *dst, cudaS
  * reduced mod t. */
 int he_encrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *pt, int n, uint64_t seed, uint64_t *ct,
                cudaStream_t stream);
+/* he_encrypt_many: he_encrypt of n_groups (1 to 4) independent groups in
+ * one call, group g encrypting pts[g] [counts[g]][N] with seed seeds[g] into
+ * cts[g] [counts[g]][2][L][N] -- bit-identical to n_groups he_encrypt calls,
+ * with all groups' transforms sharing the same kernel launches (the client
+ * side of a CryptoTrain-P layer encrypts x, w, r^x and r^w, Section 3.2).
+ * No paper counterpart beyond eps(p, pk).  INVALID_ARG for n_groups outside
+ * [1, 4], a negative count or a missing pointer of a non-empty group. */
+int he_encrypt_many(he_ctx *ctx, const he_keys *keys, int n_groups, const uint64_t *const *pts, const int *counts,
+                    const uint64_t *seeds, uint64_t *const *cts, cudaStream_t stream);
 /* he_decrypt, sigma(c, sk) of Section 2: m = floor((t [c0 + c1 s]_q +
  * floor(q/2)) / q) mod t, exactly.  ct [n][2][L][N] -> pt [n][N]. */
 int he_decrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t stream);

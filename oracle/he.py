@@ -131,11 +131,11 @@ def sample_uniform(seed, tag, idx, limb, q, N):
     return out
 
 
-def sample_masks(P: Params, seed: int, n: int) -> np.ndarray:
-    """n uniform polynomials mod t; polynomial k uses stream (seed, MASK, k)."""
+def sample_masks(P: Params, seed: int, n: int, first: int = 0) -> np.ndarray:
+    """n uniform polynomials mod t; row k uses stream (seed, MASK, first + k)."""
     out = np.zeros((n, P.N), dtype=np.uint64)
     for k in range(n):
-        _clib.lib().orc_sample_uniform_t(seed, TAG_MASK, k, P.t, P.N, _u64(out[k]))
+        _clib.lib().orc_sample_uniform_t(seed, TAG_MASK, first + k, P.t, P.N, _u64(out[k]))
     return out
 
 
@@ -167,13 +167,14 @@ def keygen(P: Params, seed: int, with_relin: bool = True) -> Keys:
     return Keys(sk, pk, rlk)
 
 
-def encrypt(P: Params, keys: Keys, m, seed: int) -> np.ndarray:
-    """m: [n][N] in [0, t) -> [n][2][L][N]; ciphertext k uses object index k."""
+def encrypt(P: Params, keys: Keys, m, seed: int, first: int = 0) -> np.ndarray:
+    """m: [n][N] in [0, t) -> [n][2][L][N]; row k is encrypted with object
+    index first + k (its position in a larger flattened batch)."""
     m = np.ascontiguousarray(np.atleast_2d(m), dtype=np.uint64)
     ct = np.zeros((m.shape[0], 2, P.L, P.N), dtype=np.uint64)
     pc = P.c()
     for k in range(m.shape[0]):
-        _clib.lib().orc_encrypt(ctypes.byref(pc), _u64(keys.pk), _u64(m[k]), seed, k, _u64(ct[k]))
+        _clib.lib().orc_encrypt(ctypes.byref(pc), _u64(keys.pk), _u64(m[k]), seed, first + k, _u64(ct[k]))
     return ct
 
 

@@ -74,10 +74,13 @@ def ppmul_terms(plan, batch=1):
     return terms
 
 
-def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
+def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0) -> LayerRun:
     """x: [C,H,W] or [B,C,H,W] ints, w: [M,C,h,h] ints; seeds:
     workloads.ProtocolSeeds.  Every random object of the batch is drawn from
-    one stream per kind, object index = position in the flattened batch."""
+    one stream per kind, object index = position in the flattened batch.
+    first_image: the batch position of x's first image, so that images of a
+    large batch can be recomputed one at a time (the weight-side objects do
+    not depend on it)."""
     t = P.t
     x = np.asarray(x)
     if x.ndim == 3:
@@ -87,11 +90,12 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRun:
         keys = he.keygen(P, seeds.keys, True)
     xp = np.concatenate([packing.encode_input(plan, x[b], t).reshape(-1, P.N) for b in range(B)])
     wp = packing.encode_kernel(plan, w, t).reshape(-1, P.N)
-    r_x = he.sample_masks(P, seeds.mask_x, xp.shape[0])
+    first = first_image * plan.T * plan.G
+    r_x = he.sample_masks(P, seeds.mask_x, xp.shape[0], first)
     r_w = he.sample_masks(P, seeds.mask_w, wp.shape[0])
-    ct_x = he.encrypt(P, keys, xp, seeds.enc_x)
+    ct_x = he.encrypt(P, keys, xp, seeds.enc_x, first)
     ct_w = he.encrypt(P, keys, wp, seeds.enc_w)
-    ct_rx = he.encrypt(P, keys, r_x, seeds.enc_rx)
+    ct_rx = he.encrypt(P, keys, r_x, seeds.enc_rx, first)
     ct_rw = he.encrypt(P, keys, r_w, seeds.enc_rw)
     # offline: [r^x r^w] summed over channel groups
     rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan, B), plan.G)

@@ -314,9 +314,17 @@ int he_keys_export(he_ctx *c, const he_keys *k, int which, void *dst, cudaStream
 }
 
 // ------------------------------------------------------------------ encrypt / decrypt
-int he_encrypt(he_ctx *c, const he_keys *k, const uint64_t *pt, int n, uint64_t seed, uint64_t *ct,
-               cudaStream_t st) {
-    if (!c || !k || n < 0 || (n && (!pt || !ct))) return HE_ERR_INVALID_ARG;
+// Encryption of n_groups groups (each its own plaintexts, count and seed) in
+// one forward launch (the u of every ciphertext) and one multiply-accumulate
+// launch (both components of every ciphertext: u pk_comp + e (+ Delta m)).
+static int encrypt_groups(he_ctx *c, const he_keys *k, int n_groups, const uint64_t *const *pts, const int *counts,
+                          const uint64_t *seeds, uint64_t *const *cts, cudaStream_t st) {
+    if (!c || !k || n_groups < 1 || n_groups > 4 || !pts || !counts || !seeds || !cts) return HE_ERR_INVALID_ARG;
+    int n = 0;
+    for (int g = 0; g < n_groups; g++) {
+        if (counts[g] < 0 || (counts[g] && (!pts[g] || !cts[g]))) return HE_ERR_INVALID_ARG;
+        n += counts[g];
+    }
     if (!n) return HE_OK;
     TRY(set_device(c));
     const int N = c->N, L = c->L;
@@ -325,28 +333,51 @@ int he_encrypt(he_ctx *c, const he_keys *k, const uint64_t *pt, int n, uint64_t 
                           Carver::round((size_t)n * LN * 8) + 4096));
     Carver cv(c->ws);
     int8_t *u8 = cv.take<int8_t>((size_t)n * N);
-    int8_t *e8 = cv.take<int8_t>((size_t)n * 2 * N);
+    int8_t *e8 = cv.take<int8_t>((size_t)n * 2 * N);  // per group: e1 of its ciphertexts, then e2
     u64 *un = cv.take<u64>((size_t)n * LN);
-    TRY(launch_sample(c, SAMPLE_TERNARY, seed, 4, 0, n, 1, u8, st));
-    // e1 for every ciphertext in the first half of e8, e2 in the second half
-    TRY(launch_sample(c, SAMPLE_CBD, seed, 5, 0, n, 1, e8, st));
-    TRY(launch_sample(c, SAMPLE_CBD, seed, 6, 0, n, 1, e8 + (size_t)n * N, st));
-    FwdJob f = fwd_job();
-    f.src = u8; f.kind = SRC_I8; f.src_stride = N; f.dst = un; f.dst_stride = LN; f.n_polys = n; f.n_limbs = L;
-    TRY(launch_fwd(c, f, st));
-    // outputs in component-major order: o = comp * n + k  -> ct + (2k + comp) LN
-    for (int comp = 0; comp < 2; comp++) {
-        Terms T;
-        for (int i = 0; i < n; i++) { T.add(i * L, comp * L); T.close(); }
-        MacJob m = mac_job();
-        TRY(upload_terms(c, T, m));
-        m.A = un; m.B = k->pk_ntt; m.out = ct + comp * LN; m.out_stride = 2 * LN;
-        m.err = e8 + (size_t)comp * n * N; m.err_stride = N;
-        if (comp == 0) { m.msg = pt; m.msg_stride = N; m.msg_div = 1; m.E = c->d_exact; }
-        m.n_out = n; m.n_limbs = L;
-        TRY(launch_mac_intt(c, m, st));
+    FwdJob fj[4];
+    MacJob mj[8];
+    int nf = 0, nm = 0;
+    size_t off = 0;
+    for (int g = 0; g < n_groups; g++) {
+        const int m = counts[g];
+        if (!m) continue;
+        int8_t *ug = u8 + off * N, *eg = e8 + off * 2 * N;
+        u64 *ung = un + off * LN;
+        TRY(launch_sample(c, SAMPLE_TERNARY, seeds[g], 4, 0, m, 1, ug, st));
+        TRY(launch_sample(c, SAMPLE_CBD, seeds[g], 5, 0, m, 1, eg, st));
+        TRY(launch_sample(c, SAMPLE_CBD, seeds[g], 6, 0, m, 1, eg + (size_t)m * N, st));
+        FwdJob f = fwd_job();
+        f.src = ug; f.kind = SRC_I8; f.src_stride = N; f.dst = ung; f.dst_stride = LN; f.n_polys = m; f.n_limbs = L;
+        fj[nf++] = f;
+        // component comp of ciphertext i: u_i pk_comp + e_comp,i (+ Delta m_i for comp 0)
+        for (int comp = 0; comp < 2; comp++) {
+            Terms T;
+            for (int i = 0; i < m; i++) { T.add((int)((off + i) * L), comp * L); T.close(); }
+            MacJob mk = mac_job();
+            TRY(upload_terms(c, T, mk));
+            mk.A = un; mk.B = k->pk_ntt; mk.out = cts[g] + comp * LN; mk.out_stride = 2 * LN;
+            mk.err = eg + (size_t)comp * m * N; mk.err_stride = N;
+            if (comp == 0) { mk.msg = pts[g]; mk.msg_stride = N; mk.msg_div = 1; mk.E = c->d_exact; }
+            mk.n_out = m; mk.n_limbs = L;
+            mj[nm++] = mk;
+        }
+        off += m;
     }
-    return HE_OK;
+    TRY(launch_fwd_multi(c, fj, nf, st));
+    return launch_mac_multi(c, mj, nm, st);
+}
+
+int he_encrypt(he_ctx *c, const he_keys *k, const uint64_t *pt, int n, uint64_t seed, uint64_t *ct,
+               cudaStream_t st) {
+    if (!c || !k || n < 0 || (n && (!pt || !ct))) return HE_ERR_INVALID_ARG;
+    if (!n) return HE_OK;
+    return encrypt_groups(c, k, 1, &pt, &n, &seed, &ct, st);
+}
+
+int he_encrypt_many(he_ctx *c, const he_keys *k, int n_groups, const uint64_t *const *pts, const int *counts,
+                    const uint64_t *seeds, uint64_t *const *cts, cudaStream_t st) {
+    return encrypt_groups(c, k, n_groups, pts, counts, seeds, cts, st);
 }
 
 int he_decrypt(he_ctx *c, const he_keys *k, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t st) {
@@ -455,20 +486,24 @@ int he_cpmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x, 
     Carver cv(c->ws);
     u64 *An = cv.take<u64>((nX + nW) * LN);
     u64 *Bn = cv.take<u64>((nWp + nXp) * LN);
-    FwdJob f = fwd_job();
-    f.n_limbs = L;
+    // every operand to the NTT domain in one launch
+    FwdJob fj[4];
+    int nf = 0;
+    auto add_fwd = [&](const void *src, int kind, long long src_stride, u64 *dst, long long n_polys) {
+        FwdJob f = fwd_job();
+        f.n_limbs = L; f.src = src; f.kind = kind; f.t = c->P.t; f.src_stride = src_stride;
+        f.dst = dst; f.dst_stride = LN; f.n_polys = (int)n_polys;
+        fj[nf++] = f;
+    };
     if (ct_x) {
-        f.src = ct_x; f.kind = SRC_RNS; f.src_stride = LN; f.dst = An; f.dst_stride = LN; f.n_polys = (int)nX;
-        TRY(launch_fwd(c, f, st));
-        f.src = pt_w; f.kind = SRC_T_LIFT; f.t = c->P.t; f.src_stride = N; f.dst = Bn; f.n_polys = (int)nWp;
-        TRY(launch_fwd(c, f, st));
+        add_fwd(ct_x, SRC_RNS, LN, An, nX);
+        add_fwd(pt_w, SRC_T_LIFT, N, Bn, nWp);
     }
     if (ct_w) {
-        f.src = ct_w; f.kind = SRC_RNS; f.src_stride = LN; f.dst = An + nX * LN; f.dst_stride = LN; f.n_polys = (int)nW;
-        TRY(launch_fwd(c, f, st));
-        f.src = pt_x; f.kind = SRC_T_LIFT; f.t = c->P.t; f.src_stride = N; f.dst = Bn + nWp * LN; f.n_polys = (int)nXp;
-        TRY(launch_fwd(c, f, st));
+        add_fwd(ct_w, SRC_RNS, LN, An + nX * LN, nW);
+        add_fwd(pt_x, SRC_T_LIFT, N, Bn + nWp * LN, nXp);
     }
+    TRY(launch_fwd_multi(c, fj, nf, st));
     Terms Tm;
     for (int b = 0; b < batch; b++)
         for (int m = 0; m < M; m++)
@@ -523,12 +558,14 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     TRY(launch_base_extend(c, ct_a, (long long)n_a * 2, aux_a, st));
     TRY(launch_base_extend(c, ct_b, (long long)n_b * 2, aux_b, st));
     // 2. forward NTT over Q u B
+    FwdJob fab[2];
     FwdJob f = fwd_job();
     f.kind = SRC_RNS; f.split = L; f.n_limbs = LK; f.dst_stride = LKN;
     f.src = ct_a; f.src_stride = LN; f.src2 = aux_a; f.src2_stride = KN; f.dst = An; f.n_polys = n_a * 2;
-    TRY(launch_fwd(c, f, st));
+    fab[0] = f;
     f.src = ct_b; f.src2 = aux_b; f.dst = Bn; f.n_polys = n_b * 2;
-    TRY(launch_fwd(c, f, st));
+    fab[1] = f;
+    TRY(launch_fwd_multi(c, fab, 2, st));
     // 3. tensor product (summed over the group) + inverse NTT, output o*3 + j
     Terms Tt;
     for (int o = 0; o < n_out; o++)
@@ -592,12 +629,14 @@ int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, 
     Carver cv(c->ws);
     u64 *Xn = cv.take<u64>(nX * N);
     u64 *Wn = cv.take<u64>(nW * N);
+    FwdJob fxw[2];
     FwdJob f = fwd_job();
     f.kind = SRC_T_RAW; f.n_limbs = 1; f.mod_base = c->t_mod; f.dst_stride = N; f.src_stride = N;
     f.src = pt_x; f.dst = Xn; f.n_polys = (int)nX;
-    TRY(launch_fwd(c, f, st));
+    fxw[0] = f;
     f.src = pt_w; f.dst = Wn; f.n_polys = (int)nW;
-    TRY(launch_fwd(c, f, st));
+    fxw[1] = f;
+    TRY(launch_fwd_multi(c, fxw, 2, st));
     Terms Tm;
     for (int b = 0; b < batch; b++)
         for (int m = 0; m < M; m++)

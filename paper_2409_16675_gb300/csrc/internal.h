@@ -167,6 +167,15 @@ struct FwdJob {
     int n_polys, n_limbs, mod_base;
 };
 int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st);
+// Several forward jobs over the same moduli (n_limbs, mod_base) in one grid,
+// so that small transforms of one call fill the GPU together.
+constexpr int kMaxFwdJobs = 4;
+struct FwdJobs {
+    FwdJob j[kMaxFwdJobs];
+    int start[kMaxFwdJobs];
+    int n;
+};
+int launch_fwd_multi(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st);
 
 // Fused multiply-accumulate in the NTT domain followed by the inverse NTT and
 // an epilogue.  Output o, limb l:
@@ -196,6 +205,14 @@ struct MacJob {
     int n_dist_a, n_dist_b, n_terms;
 };
 int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st);
+// Several multiply-accumulate jobs over the same moduli in one grid.
+constexpr int kMaxMacJobs = 8;
+struct MacJobs {
+    MacJob j[kMaxMacJobs];
+    int start[kMaxMacJobs];
+    int n;
+};
+int launch_mac_multi(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st);
 
 // Work items of the persistent queue kernels (batched execution).
 struct FwdItem {            // forward NTT of one limb polynomial

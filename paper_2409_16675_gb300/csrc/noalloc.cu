@@ -94,22 +94,25 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
     rc = cuda_check(c, cudaMemcpyAsync(dterms, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice, st),
                     "term table copy");
     if (rc) return rc;
-    FwdJob f;
-    memset(&f, 0, sizeof f);
-    f.split = 1 << 30;
-    f.n_limbs = L;
+    FwdJob fj[4];
+    int nf = 0;
+    auto add_fwd = [&](const void *src, int kind, long long src_stride, u64 *dst, long long n_polys) {
+        FwdJob f;
+        memset(&f, 0, sizeof f);
+        f.split = 1 << 30;
+        f.n_limbs = L; f.src = src; f.kind = kind; f.t = c->P.t; f.src_stride = src_stride;
+        f.dst = dst; f.dst_stride = LN; f.n_polys = (int)n_polys;
+        fj[nf++] = f;
+    };
     if (ct_x) {
-        f.src = ct_x; f.kind = SRC_RNS; f.src_stride = LN; f.dst = An; f.dst_stride = LN; f.n_polys = (int)nX;
-        if ((rc = launch_fwd(c, f, st))) return rc;
-        f.src = pt_w; f.kind = SRC_T_LIFT; f.t = c->P.t; f.src_stride = N; f.dst = Bn; f.n_polys = (int)nWp;
-        if ((rc = launch_fwd(c, f, st))) return rc;
+        add_fwd(ct_x, SRC_RNS, LN, An, nX);
+        add_fwd(pt_w, SRC_T_LIFT, N, Bn, nWp);
     }
     if (ct_w) {
-        f.src = ct_w; f.kind = SRC_RNS; f.src_stride = LN; f.dst = An + nX * LN; f.dst_stride = LN; f.n_polys = (int)nW;
-        if ((rc = launch_fwd(c, f, st))) return rc;
-        f.src = pt_x; f.kind = SRC_T_LIFT; f.t = c->P.t; f.src_stride = N; f.dst = Bn + nWp * LN; f.n_polys = (int)nXp;
-        if ((rc = launch_fwd(c, f, st))) return rc;
+        add_fwd(ct_w, SRC_RNS, LN, An + nX * LN, nW);
+        add_fwd(pt_x, SRC_T_LIFT, N, Bn + nWp * LN, nXp);
     }
+    if ((rc = launch_fwd_multi(c, fj, nf, st))) return rc;
     MacJob mj;
     memset(&mj, 0, sizeof mj);
     mj.msg_div = 1;

@@ -21,6 +21,8 @@
 // last forward pass and the first inverse pass hold in registers, so both the
 // forward store and the multiply-accumulate loads are coalesced.  This order
 // never leaves the library.
+#include <cstring>
+
 #include "arith.cuh"
 
 namespace he {
@@ -224,13 +226,22 @@ __device__ __forceinline__ void inv_transform(u64 (&v)[16], u64 *sm, int tau, co
 }
 
 // ---------------------------------------------------------------- grid kernels (one CTA per limb polynomial)
+// Up to kMaxFwdJobs forward jobs over the same moduli in one grid: blocks
+// [start[i], start[i+1]) belong to job i.  The job is selected with constant
+// indices only, so the parameter block is never copied to local memory.
 template <int LOGN, bool LAZY>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J, const ModDev *__restrict__ mods) {
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJobs JS, const ModDev *__restrict__ mods) {
     extern __shared__ u64 sm[];
     constexpr int N = Cfg<LOGN>::N;
     const int tau = threadIdx.x;
-    const int limb = blockIdx.x / J.n_polys;
-    const int p = blockIdx.x - limb * J.n_polys;
+    FwdJob J = JS.j[0];
+    int base = 0;
+#pragma unroll
+    for (int i = 1; i < kMaxFwdJobs; i++)
+        if (i < JS.n && (int)blockIdx.x >= JS.start[i]) { J = JS.j[i]; base = JS.start[i]; }
+    const int local = (int)blockIdx.x - base;
+    const int limb = local / J.n_polys;
+    const int p = local - limb * J.n_polys;
     const ModDev M = mods[J.mod_base + limb];
     const void *src;
     if (J.kind == SRC_RNS)
@@ -248,13 +259,24 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJob J,
     fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, J.dst + (long long)p * J.dst_stride + (long long)limb * N);
 }
 
+// Up to kMaxMacJobs multiply-accumulate jobs over the same moduli in one
+// grid (blocks [start[i], start[i+1]) belong to job i).  The job block stays
+// in the constant bank (__grid_constant__): fields are read through a
+// block-uniform index, never copied to registers or local memory.
 template <int LOGN, bool LAZY>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_mac_intt(MacJob J, const ModDev *__restrict__ mods) {
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
+    k_mac_intt(const __grid_constant__ MacJobs JS, const ModDev *__restrict__ mods) {
     extern __shared__ u64 sm[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T;
     const int tau = threadIdx.x;
-    const int limb = blockIdx.x / J.n_out;
-    const int o = blockIdx.x - limb * J.n_out;
+    int jj = 0;
+#pragma unroll
+    for (int i = 1; i < kMaxMacJobs; i++)
+        if (i < JS.n && (int)blockIdx.x >= JS.start[i]) jj = i;
+    const MacJob &J = JS.j[jj];
+    const int local = (int)blockIdx.x - JS.start[jj];
+    const int limb = local / J.n_out;
+    const int o = local - limb * J.n_out;
     const ModDev M = mods[J.mod_base + limb];
     u64 v[16];
     mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
@@ -375,7 +397,7 @@ static bool lazy_ok(const he_ctx *c, int mod_base, int n_limbs) {
 bool ctx_lazy(const he_ctx *c) { return lazy_ok(c, 0, c->L); }
 
 template <int LOGN>
-static int fwd_t(he_ctx *c, const FwdJob &j, cudaStream_t st) {
+static int fwd_t(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
@@ -383,20 +405,34 @@ static int fwd_t(he_ctx *c, const FwdJob &j, cudaStream_t st) {
         cudaFuncSetAttribute(k_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    const bool lazy = lazy_ok(c, j.mod_base, j.n_limbs);
-    const long long blocks = (long long)j.n_polys * j.n_limbs;
-    if (blocks == 0) return HE_OK;
+    FwdJobs JS;
+    memset(&JS, 0, sizeof JS);
+    long long blocks = 0;
+    double bytes = 0;
     const int N = Cfg<LOGN>::N;
-    const double src_bytes = j.kind == SRC_RNS ? 8.0 * j.n_limbs : (j.kind == SRC_I8 ? 1.0 : (j.kind == SRC_U32 ? 4.0 : 8.0));
-    TraceScope ts(c, st, "ntt_fwd", (double)j.n_polys * N * (src_bytes + 8.0 * j.n_limbs),
-                  (double)blocks * (N / 2) * LOGN);
-    if (lazy) k_fwd<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
-    else k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    for (int i = 0; i < n; i++) {
+        const FwdJob &j = jobs[i];
+        if (j.n_limbs != jobs[0].n_limbs || j.mod_base != jobs[0].mod_base)
+            return fail(c, HE_ERR_INVALID_ARG, "merged forward jobs must share their moduli");
+        if (j.n_polys <= 0) continue;
+        JS.start[JS.n] = (int)blocks;
+        JS.j[JS.n++] = j;
+        blocks += (long long)j.n_polys * j.n_limbs;
+        const double src_bytes =
+            j.kind == SRC_RNS ? 8.0 * j.n_limbs : (j.kind == SRC_I8 ? 1.0 : (j.kind == SRC_U32 ? 4.0 : 8.0));
+        bytes += (double)j.n_polys * N * (src_bytes + 8.0 * j.n_limbs);
+    }
+    if (blocks == 0) return HE_OK;
+    if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "forward launch too large");
+    const bool lazy = lazy_ok(c, jobs[0].mod_base, jobs[0].n_limbs);
+    TraceScope ts(c, st, "ntt_fwd", bytes, (double)blocks * (N / 2) * LOGN);
+    if (lazy) k_fwd<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    else k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
     return cuda_check(c, cudaGetLastError(), "k_fwd");
 }
 
 template <int LOGN>
-static int mac_t(he_ctx *c, const MacJob &j, cudaStream_t st) {
+static int mac_t(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
@@ -404,29 +440,46 @@ static int mac_t(he_ctx *c, const MacJob &j, cudaStream_t st) {
         cudaFuncSetAttribute(k_mac_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    const bool lazy = lazy_ok(c, j.mod_base, j.n_limbs);
-    const long long blocks = (long long)j.n_out * j.n_limbs;
-    if (blocks == 0) return HE_OK;
+    MacJobs JS;
+    memset(&JS, 0, sizeof JS);
+    long long blocks = 0;
+    double bytes = 0, mm = 0;
     const int N = Cfg<LOGN>::N;
-    const double lb = 8.0 * N * j.n_limbs;  // one polynomial over all limbs
-    double bytes = lb * (j.n_out + j.n_dist_a + j.n_dist_b + (j.add ? j.n_out : 0));
-    double mm = (double)blocks * ((N / 2) * LOGN + 3.0 * N) + (double)j.n_terms * N * j.n_limbs;
+    for (int i = 0; i < n; i++) {
+        const MacJob &j = jobs[i];
+        if (j.n_limbs != jobs[0].n_limbs || j.mod_base != jobs[0].mod_base)
+            return fail(c, HE_ERR_INVALID_ARG, "merged multiply-accumulate jobs must share their moduli");
+        if (j.n_out <= 0) continue;
+        JS.start[JS.n] = (int)blocks;
+        JS.j[JS.n++] = j;
+        const long long b = (long long)j.n_out * j.n_limbs;
+        blocks += b;
+        const double lb = 8.0 * N * j.n_limbs;  // one polynomial over all limbs
+        bytes += lb * (j.n_out + j.n_dist_a + j.n_dist_b + (j.add ? j.n_out : 0));
+        mm += (double)b * ((N / 2) * LOGN + 3.0 * N) + (double)j.n_terms * N * j.n_limbs;
+    }
+    if (blocks == 0) return HE_OK;
+    if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "multiply-accumulate launch too large");
+    const bool lazy = lazy_ok(c, jobs[0].mod_base, jobs[0].n_limbs);
     TraceScope ts(c, st, "mac_intt", bytes, mm);
-    if (lazy) k_mac_intt<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
-    else k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(j, c->d_mods);
+    if (lazy) k_mac_intt<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    else k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
     return cuda_check(c, cudaGetLastError(), "k_mac_intt");
 }
 
-int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) {
+int launch_fwd_multi(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
+    if (n < 1 || n > kMaxFwdJobs) return fail(c, HE_ERR_INVALID_ARG, "1 to 4 forward jobs per launch");
     switch (c->logN) {
-    case 10: return fwd_t<10>(c, j, st);
-    case 11: return fwd_t<11>(c, j, st);
-    case 12: return fwd_t<12>(c, j, st);
-    case 13: return fwd_t<13>(c, j, st);
-    case 14: return fwd_t<14>(c, j, st);
+    case 10: return fwd_t<10>(c, jobs, n, st);
+    case 11: return fwd_t<11>(c, jobs, n, st);
+    case 12: return fwd_t<12>(c, jobs, n, st);
+    case 13: return fwd_t<13>(c, jobs, n, st);
+    case 14: return fwd_t<14>(c, jobs, n, st);
     }
     return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
 }
+
+int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) { return launch_fwd_multi(c, &j, 1, st); }
 
 template <int LOGN, int MINB, bool LAZY>
 static int queue_l(bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid, cudaStream_t st) {
@@ -467,15 +520,18 @@ int launch_queue(int logN, int minb, bool fwd, bool lazy, const ItemSeg *segs, i
     return HE_ERR_UNSUPPORTED_PARAMS;
 }
 
-int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st) {
+int launch_mac_multi(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
+    if (n < 1 || n > kMaxMacJobs) return fail(c, HE_ERR_INVALID_ARG, "1 to 8 multiply-accumulate jobs per launch");
     switch (c->logN) {
-    case 10: return mac_t<10>(c, j, st);
-    case 11: return mac_t<11>(c, j, st);
-    case 12: return mac_t<12>(c, j, st);
-    case 13: return mac_t<13>(c, j, st);
-    case 14: return mac_t<14>(c, j, st);
+    case 10: return mac_t<10>(c, jobs, n, st);
+    case 11: return mac_t<11>(c, jobs, n, st);
+    case 12: return mac_t<12>(c, jobs, n, st);
+    case 13: return mac_t<13>(c, jobs, n, st);
+    case 14: return mac_t<14>(c, jobs, n, st);
     }
     return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
 }
+
+int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st) { return launch_mac_multi(c, &j, 1, st); }
 
 }  // namespace he

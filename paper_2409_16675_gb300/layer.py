@@ -128,10 +128,10 @@ class PLayer:
         self.plan.encode_kernel(w, b.wp)
         nv.he_sample_masks(c.h, seeds.mask_x, self.nx, b.r_x)
         nv.he_sample_masks(c.h, seeds.mask_w, self.nw, b.r_w)
-        nv.he_encrypt(c.h, self.keys.h, b.xp, self.nx, seeds.enc_x, b.ct_x)
-        nv.he_encrypt(c.h, self.keys.h, b.wp, self.nw, seeds.enc_w, b.ct_w)
-        nv.he_encrypt(c.h, self.keys.h, b.r_x, self.nx, seeds.enc_rx, b.ct_rx)
-        nv.he_encrypt(c.h, self.keys.h, b.r_w, self.nw, seeds.enc_rw, b.ct_rw)
+        nv.he_encrypt_many(c.h, self.keys.h, [(b.xp, self.nx, seeds.enc_x, b.ct_x),
+                                               (b.wp, self.nw, seeds.enc_w, b.ct_w),
+                                               (b.r_x, self.nx, seeds.enc_rx, b.ct_rx),
+                                               (b.r_w, self.nw, seeds.enc_rw, b.ct_rw)])
         nv.he_pt_sub(c.h, b.xp, b.r_x, self.nx * c.N, b.xm)
         nv.he_pt_sub(c.h, b.wp, b.r_w, self.nw * c.N, b.wm)
 

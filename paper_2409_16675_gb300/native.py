@@ -101,6 +101,8 @@ def _load():
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
+        "he_encrypt_many": [vp, vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64),
+                            ctypes.POINTER(vp), vp],
         "he_cpmul_conv_noalloc": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
         "he_ccmul_precompute": [vp, vp, vp, i32, vp, i32, vp, vp, i32, i32, vp, vp],
         "he_ccmul_conv_precompute": [vp, vp, vp, i32, vp, vp, vp, vp],
@@ -210,6 +212,16 @@ def he_keys_export(ctx, keys, which: int, dst: torch.Tensor):
 
 def he_encrypt(ctx, keys, pt: torch.Tensor, n: int, seed: int, ct: torch.Tensor):
     _check(lib.he_encrypt(ctx, keys, _ptr(pt), n, seed, _ptr(ct), _stream()), ctx)
+
+
+def he_encrypt_many(ctx, keys, groups):
+    """groups: up to 4 tuples (pt [n][N], n, seed, ct [n][2][L][N])."""
+    k = len(groups)
+    pts = (ctypes.c_void_p * k)(*[_ptr(g[0]) for g in groups])
+    counts = (ctypes.c_int32 * k)(*[int(g[1]) for g in groups])
+    seeds = (ctypes.c_uint64 * k)(*[int(g[2]) for g in groups])
+    cts = (ctypes.c_void_p * k)(*[_ptr(g[3]) for g in groups])
+    _check(lib.he_encrypt_many(ctx, keys, k, pts, counts, seeds, cts, _stream()), ctx)
 
 
 def he_decrypt(ctx, keys, ct: torch.Tensor, n: int, pt: torch.Tensor):

@@ -80,6 +80,27 @@ def test_encrypt_decrypt_bits(name):
     k.close()
 
 
+def test_encrypt_many_equals_separate_calls():
+    """he_encrypt_many shares the launches of several groups (own seeds and
+    counts, one of them empty) and gives the bits of separate he_encrypt calls."""
+    c = ctx_for("n4096")
+    keys = layer.Keys(c, 77, False)
+    counts, seeds = [3, 0, 2, 5], [101, 102, 103, 104]
+    pts = [cuda(wl.uniform_mod(200 + g, (max(n, 1), c.N), c.t)) for g, n in enumerate(counts)]
+    many = [c.ct(max(n, 1)).zero_() for n in counts]
+    nv.he_encrypt_many(c.h, keys.h, [(pts[g], counts[g], seeds[g], many[g]) for g in range(4)])
+    for g in range(4):
+        if counts[g] == 0:
+            assert not to_np(many[g]).any()     # an empty group writes nothing
+            continue
+        one = c.ct(counts[g])
+        nv.he_encrypt(c.h, keys.h, pts[g], counts[g], seeds[g], one)
+        assert np.array_equal(to_np(many[g]), to_np(one))
+    with pytest.raises(nv.HEError):
+        nv.he_encrypt_many(c.h, keys.h, [(pts[0], 3, 1, many[0])] * 5)   # at most 4 groups
+    keys.close()
+
+
 def test_decrypt_rounding_edges():
     # ciphertexts (x, 0) with x at the rounding boundaries of floor((t x + q/2)/q)
     c = ctx_for("n4096")
@@ -275,6 +296,38 @@ def test_layer_conv_3x32x32_n8192_end_to_end(enc):
     assert np.array_equal(ref.y, protocol.conv_reference(x[0], w, 1))
     for h in hs:
         h.close()
+
+
+def test_layer_bench_configuration_batch64_sampled():
+    """The benchmark's launch configuration: the 3x32x32 -> 16 layer at N = 8192
+    with batch 64 and the seeds of its first timed step.  Every image decodes
+    to the exact convolution; the ciphertext bits of images 0 and 63 (input
+    encryptions, precomputed [r^x r^w], online result) equal the oracle's,
+    which recomputes those images one at a time at their batch positions."""
+    w_ = wl.CONV_MID
+    s, B = w_.shape, 64
+    c = ctx_for("n8192")
+    seeds = wl.protocol_seeds(w_.seed)
+    keys = layer.Keys(c, seeds.keys, True)
+    plan = layer.Plan(c, s, w_.encoding)
+    pl = layer.PLayer(c, keys, plan, B)
+    x, k = wl.layer_inputs(w_, B)
+    y = to_np(pl.step(cuda(x), cuda(k), seeds))
+    for b in range(B):
+        assert np.array_equal(y[b], protocol.conv_reference(x[b], k, s.pad)), b
+    P = oparams(c)
+    okeys = he.keygen(P, seeds.keys, True)
+    op = packing.make_plan(w_.encoding, c.N, s.C, s.H, s.W, s.M, s.h, s.pad)
+    nx, no = plan.T * plan.G, plan.MG * plan.T
+    ct_x, rr, out = to_np(pl.buf.ct_x), to_np(pl.buf.rr), to_np(pl.buf.out)
+    for b in (0, B - 1):
+        ref = protocol.run_layer(P, op, x[b], k, seeds, keys=okeys, first_image=b)
+        assert np.array_equal(ct_x[b * nx:(b + 1) * nx], ref.ct_x)
+        assert np.array_equal(rr[b * no:(b + 1) * no], ref.rr)
+        assert np.array_equal(out[b * no:(b + 1) * no], ref.out)
+        assert np.array_equal(y[b], ref.y)
+    keys.close()
+    plan.close()
 
 
 def test_layer_batched_ragged_tiles():

@@ -178,3 +178,28 @@ def test_protocol_identity_decodes_to_conv(enc, pad):
     xw = he.ppmul_terms(P, run.x_polys, run.w_polys, packing.product_terms(plan))
     tt = np.uint64(P.t)
     assert np.array_equal((dec + tt - run.p) % tt, xw)
+
+
+def test_protocol_images_of_a_batch_one_at_a_time():
+    """Recomputing image b of a batch alone (first_image = b) reproduces that
+    image's rows of the batched run: the per-image random objects take their
+    flattened batch index, the weight-side objects do not move."""
+    spec = wl.RingSpec(256, (30, 30), 65537)
+    P = he.Params.from_spec(spec)
+    plan = packing.make_plan("corr", P.N, 2, 6, 5, 3, 3, 1)
+    x = wl.activations(5, (3, 2, 6, 5))
+    w = wl.weights(6, (3, 2, 3, 3))
+    seeds = wl.protocol_seeds(13)
+    full = protocol.run_layer(P, plan, x, w, seeds)
+    nx, no = plan.T * plan.G, plan.MG * plan.T
+    for b in (0, 2):
+        one = protocol.run_layer(P, plan, x[b], w, seeds, keys=full.keys, first_image=b)
+        assert np.array_equal(one.ct_x, full.ct_x[b * nx:(b + 1) * nx])
+        assert np.array_equal(one.ct_rx, full.ct_rx[b * nx:(b + 1) * nx])
+        assert np.array_equal(one.ct_w, full.ct_w)
+        assert np.array_equal(one.rr, full.rr[b * no:(b + 1) * no])
+        assert np.array_equal(one.out, full.out[b * no:(b + 1) * no])
+        assert np.array_equal(one.y, full.y[b])
+    # a wrong offset gives other ciphertexts (the index really enters the streams)
+    other = protocol.run_layer(P, plan, x[2], w, seeds, keys=full.keys, first_image=1)
+    assert not np.array_equal(other.ct_x, full.ct_x[2 * nx:3 * nx])
