@@ -2,25 +2,26 @@
 //
 // The product in A_{N,q} = Z_q[x]/(x^N+1) (Section 2, Notations) is computed
 // as NTT -> pointwise multiply-accumulate -> inverse NTT.  One CTA owns one
-// limb polynomial; each of its N/16 threads keeps 16 coefficients in
-// registers and runs up to four butterfly stages (radix 16) between exchanges
-// through padded shared memory.  The forward transform is Cooley-Tukey with
-// the psi twist merged into the twiddles (natural input, bit-reversed output);
-// the inverse is a decimation-in-time Cooley-Tukey cyclic transform with
-// omega^-1 on the bit-reversed input, followed by the untwist psi^-e N^-1.
-// Both use Harvey-style lazy butterflies with the approximate-quotient Shoup
-// product built from 32-bit multiply-accumulates (twiddle product in
-// [0, 3q)); the butterfly adds 4q to the difference, so values grow by at
-// most 4q per stage: with every modulus of a launch below 2^57 they stay below 57q < 2^63
-// through 14 stages and the LAZY variants make no correction inside the
-// transform; otherwise X is brought below 4q before each butterfly and every
-// value stays below 8q < 2^64.
+// limb polynomial; each of its N/R threads keeps R = 2^RB = 16 coefficients
+// in registers and runs up to RB butterfly stages between exchanges through
+// padded shared memory.  The forward
+// transform is Cooley-Tukey with the psi twist merged into the twiddles
+// (natural input, bit-reversed output); the inverse is a decimation-in-time
+// Cooley-Tukey cyclic transform with omega^-1 on the bit-reversed input,
+// followed by the untwist psi^-e N^-1.  Both use Harvey-style lazy
+// butterflies with the approximate-quotient Shoup product built from 32-bit
+// multiply-accumulates (twiddle product in [0, 3q)); the butterfly adds 4q to
+// the difference, so values grow by at most 4q per stage: with every modulus
+// of a launch below 2^57 they stay below 57q < 2^63 through 14 stages and the
+// LAZY variants make no correction inside the transform; otherwise X is
+// brought below 4q before each butterfly and every value stays below
+// 8q < 2^64.
 //
-// NTT-domain storage order ("perm16"): memory position k*(N/16) + tau holds
-// the bit-reversed-order value of index 16*tau + k, which is exactly what the
-// last forward pass and the first inverse pass hold in registers, so both the
-// forward store and the multiply-accumulate loads are coalesced.  This order
-// never leaves the library.
+// NTT-domain storage order (register-tile order): memory position
+// k*(N/R) + tau holds the bit-reversed-order value of index R*tau + k, which
+// is exactly what the last forward pass and the first inverse pass hold in
+// registers, so both the forward store and the multiply-accumulate loads are
+// coalesced.  This order never leaves the library.
 #include <cstring>
 
 #include "arith.cuh"
@@ -32,33 +33,50 @@ namespace he {
 // 1024), else 8.
 __host__ __device__ constexpr int mac_group(int threads, int minb) { return threads * minb >= 1024 ? 4 : 8; }
 
+// Register tile: every thread holds R = 2^RB coefficients; passes of RB
+// butterfly stages run in registers between shared-memory exchanges.  RB = 4
+// at every ring degree: a 32-coefficient tile (RB = 5, two exchanges instead
+// of three at N = 8192) made the forward transform 3% faster but halved the
+// resident warps, and the multiply-accumulate kernels, which wait on their
+// operand loads, lost 54%.
 template <int LOGN>
 struct Cfg {
     static constexpr int N = 1 << LOGN;
-    static constexpr int T = N / 16;
-    static constexpr int NP = (LOGN + 3) / 4;
-    static constexpr int RL = LOGN - 4 * (NP - 1);
-    static constexpr int SMEM = (N + N / 16) * 8;
-    static constexpr int MINB = LOGN >= 14 ? 1 : 2;  // resident CTAs per SM the register budget targets
+    static constexpr int RB = 4;
+    static constexpr int R = 1 << RB;
+    static constexpr int T = N / R;
+    static constexpr int NP = (LOGN + RB - 1) / RB;
+    static constexpr int RL = LOGN - RB * (NP - 1);
+    static constexpr int SMEM = (N + N / R) * 8;
+    // resident CTAs per SM the register budget targets (64 registers per
+    // thread at N = 8192; N = 16384 runs one 1024-thread CTA per SM)
+    static constexpr int MINB = LOGN >= 14 ? 1 : 2;
 };
 
-__device__ __forceinline__ int padi(int j) { return j + (j >> 4); }
-// element index of register k of thread tau when the 4-bit register window
+// one pad word per R elements: exchanges are conflict-free for every window
+template <int RB>
+__device__ __forceinline__ int padi(int j) { return j + (j >> RB); }
+// element index of register k of thread tau when the RB-bit register window
 // starts at bit lo
+template <int RB>
 __device__ __forceinline__ int jidx(int tau, int k, int lo) {
-    return ((tau >> lo) << (lo + 4)) | (k << lo) | (tau & ((1 << lo) - 1));
+    return ((tau >> lo) << (lo + RB)) | (k << lo) | (tau & ((1 << lo) - 1));
 }
 
-template <int LOGN, int R, bool LAZY>
-__device__ __forceinline__ void fwd_pass(u64 (&v)[16], int tau, int lo, int s0, const ModDev &M) {
+// Forward pass: S stages on register bits S-1 .. 0 of the window starting at
+// element bit lo (stage s0 + st acts on bit lo + S - 1 - st); the twiddle of
+// the pair whose lower element is j is fw[2^s + (j >> (bit + 1))].
+template <int RB, int S, bool LAZY>
+__device__ __forceinline__ void fwd_pass(u64 (&v)[1 << RB], int tau, int lo, int s0, const ModDev &M) {
+    constexpr int R = 1 << RB;
     const u64 q4 = 2 * M.twoq, nq = M.nq;
 #pragma unroll
-    for (int st = 0; st < R; st++) {
-        const int kb = R - 1 - st;
+    for (int st = 0; st < S; st++) {
+        const int kb = S - 1 - st;
         const int s = s0 + st;
-        const int base = (1 << s) + ((tau >> lo) << (3 - kb));
+        const int base = (1 << s) + ((tau >> lo) << (RB - 1 - kb));
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
+        for (int k = 0; k < R; k++) {
             if (k & (1 << kb)) continue;
             const int widx = base + (k >> (kb + 1));
             const ulonglong2 Wp = __ldg(M.fw + widx);
@@ -75,16 +93,17 @@ __device__ __forceinline__ void fwd_pass(u64 (&v)[16], int tau, int lo, int s0, 
 // Decimation-in-time pass of the inverse: stages s0 .. s0+R-1 act on element
 // bits lo+kb0 .. lo+kb0+R-1; the factor of the pair whose lower element is e
 // is iw[2^s + (e mod 2^s)].
-template <int R, int KB0, bool LAZY>
-__device__ __forceinline__ void inv_pass(u64 (&v)[16], int tau, int lo, int s0, const ModDev &M) {
+template <int RB, int S, int KB0, bool LAZY>
+__device__ __forceinline__ void inv_pass(u64 (&v)[1 << RB], int tau, int lo, int s0, const ModDev &M) {
+    constexpr int R = 1 << RB;
     const u64 q4 = 2 * M.twoq, nq = M.nq;
 #pragma unroll
-    for (int st = 0; st < R; st++) {
+    for (int st = 0; st < S; st++) {
         const int kb = KB0 + st;
         const int s = s0 + st;
         const int base = (1 << s) + (tau & ((1 << lo) - 1));
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
+        for (int k = 0; k < R; k++) {
             if (k & (1 << kb)) continue;
             const int widx = base + ((k & ((1 << kb) - 1)) << lo);
             const ulonglong2 Wp = __ldg(M.iw + widx);
@@ -97,12 +116,13 @@ __device__ __forceinline__ void inv_pass(u64 (&v)[16], int tau, int lo, int s0, 
     }
 }
 
-__device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[16], int tau, int lo_from, int lo_to) {
+template <int RB>
+__device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[1 << RB], int tau, int lo_from, int lo_to) {
 #pragma unroll
-    for (int k = 0; k < 16; k++) sm[padi(jidx(tau, k, lo_from))] = v[k];
+    for (int k = 0; k < (1 << RB); k++) sm[padi<RB>(jidx<RB>(tau, k, lo_from))] = v[k];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 16; k++) v[k] = sm[padi(jidx(tau, k, lo_to))];
+    for (int k = 0; k < (1 << RB); k++) v[k] = sm[padi<RB>(jidx<RB>(tau, k, lo_to))];
     __syncthreads();
 }
 
@@ -110,20 +130,20 @@ __device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[16], int tau, int lo_
 // Load one limb polynomial into the first register window (bits [LOGN-4,
 // LOGN): element k*T + tau, coalesced), reducing / lifting it into [0, q).
 template <int LOGN>
-__device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const ModDev &M, int tau, u64 (&v)[16]) {
-    constexpr int T = Cfg<LOGN>::T;
+__device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const ModDev &M, int tau, u64 (&v)[Cfg<LOGN>::R]) {
+    constexpr int T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
     switch (kind) {
     case SRC_RNS: {
         const u64 *s = (const u64 *)src;
 #pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = s[k * T + tau];
+        for (int k = 0; k < R; k++) v[k] = s[k * T + tau];
         break;
     }
     case SRC_T_LIFT: {
         const u64 *s = (const u64 *)src;
         const u64 half = (t - 1) / 2;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
+        for (int k = 0; k < R; k++) {
             u64 x = s[k * T + tau];
             x = x >= t ? x % t : x;
             v[k] = x <= half ? x : M.q - (t - x);
@@ -133,7 +153,7 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
     case SRC_I8: {
         const int8_t *s = (const int8_t *)src;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
+        for (int k = 0; k < R; k++) {
             const int x = s[k * T + tau];
             v[k] = x >= 0 ? (u64)x : M.q - (u64)(-x);
         }
@@ -142,34 +162,35 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
     case SRC_U32: {
         const uint32_t *s = (const uint32_t *)src;
 #pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = s[k * T + tau];
+        for (int k = 0; k < R; k++) v[k] = s[k * T + tau];
         break;
     }
     default: {  // SRC_T_RAW
         const u64 *s = (const u64 *)src;
 #pragma unroll
-        for (int k = 0; k < 16; k++) v[k] = reduce64(s[k * T + tau], M.q, M.one_s);
+        for (int k = 0; k < R; k++) v[k] = reduce64(s[k * T + tau], M.q, M.one_s);
         break;
     }
     }
 }
 
-// Forward transform of a loaded polynomial and its store in perm16 order
-// (position k*T + tau), fully reduced.
+// Forward transform of a loaded polynomial and its store in register-tile
+// order (position k*T + tau), fully reduced.
 template <int LOGN, bool LAZY>
-__device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int tau, const ModDev &M, u64 *d) {
-    constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
-    int lo = LOGN - 4;
+__device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 *sm, int tau, const ModDev &M,
+                                                    u64 *d) {
+    constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL, RB = Cfg<LOGN>::RB, R = Cfg<LOGN>::R;
+    int lo = LOGN - RB;
 #pragma unroll
     for (int pass = 0; pass < NP - 1; pass++) {
-        fwd_pass<LOGN, 4, LAZY>(v, tau, lo, 4 * pass, M);
-        const int lo_next = pass == NP - 2 ? 0 : lo - 4;
-        exchange(sm, v, tau, lo, lo_next);
+        fwd_pass<RB, RB, LAZY>(v, tau, lo, RB * pass, M);
+        const int lo_next = pass == NP - 2 ? 0 : lo - RB;
+        exchange<RB>(sm, v, tau, lo, lo_next);
         lo = lo_next;
     }
-    fwd_pass<LOGN, RL, LAZY>(v, tau, 0, 4 * (NP - 1), M);
+    fwd_pass<RB, RL, LAZY>(v, tau, 0, RB * (NP - 1), M);
 #pragma unroll
-    for (int k = 0; k < 16; k++) d[k * T + tau] = reduce_small(v[k], M);  // from [0, 57q) or [0, 8q)
+    for (int k = 0; k < R; k++) d[k * T + tau] = reduce_small(v[k], M);  // from [0, 57q) or [0, 8q)
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
@@ -177,10 +198,10 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[16], u64 *sm, int t
 template <int LOGN, int CH>
 __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const u64 *__restrict__ B,
                                                const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int t0,
-                                               int t1, int limb, const ModDev &M, int tau, u64 (&v)[16]) {
-    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T;
+                                               int t1, int limb, const ModDev &M, int tau, u64 (&v)[Cfg<LOGN>::R]) {
+    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
 #pragma unroll
-    for (int part = 0; part < 16 / CH; part++) {
+    for (int part = 0; part < R / CH; part++) {
         u64 lo[CH], hi[CH];
 #pragma unroll
         for (int kk = 0; kk < CH; kk++) { lo[kk] = 0; hi[kk] = 0; }
@@ -206,23 +227,23 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
     }
 }
 
-// Inverse transform: bits 0-3 first (the perm16 register tile), then upward;
-// the last window is the top four bits [LOGN-4, LOGN) holding the remaining
-// RL stages, and leaves every thread with the natural-order elements k*T + tau
+// Inverse transform: the register-tile bits [0, RB) first, then upward; the
+// last window is the top RB bits [LOGN-RB, LOGN) holding the remaining RL
+// stages, and leaves every thread with the natural-order elements k*T + tau
 // (before the untwist / N^-1 scaling).
 template <int LOGN, bool LAZY>
-__device__ __forceinline__ void inv_transform(u64 (&v)[16], u64 *sm, int tau, const ModDev &M) {
-    constexpr int NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL;
-    inv_pass<4, 0, LAZY>(v, tau, 0, 0, M);
+__device__ __forceinline__ void inv_transform(u64 (&v)[Cfg<LOGN>::R], u64 *sm, int tau, const ModDev &M) {
+    constexpr int NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL, RB = Cfg<LOGN>::RB;
+    inv_pass<RB, RB, 0, LAZY>(v, tau, 0, 0, M);
     int lo = 0;
 #pragma unroll
     for (int pass = 1; pass < NP - 1; pass++) {
-        exchange(sm, v, tau, lo, 4 * pass);
-        lo = 4 * pass;
-        inv_pass<4, 0, LAZY>(v, tau, lo, 4 * pass, M);
+        exchange<RB>(sm, v, tau, lo, RB * pass);
+        lo = RB * pass;
+        inv_pass<RB, RB, 0, LAZY>(v, tau, lo, RB * pass, M);
     }
-    exchange(sm, v, tau, lo, LOGN - 4);
-    inv_pass<RL, 4 - RL, LAZY>(v, tau, LOGN - 4, 4 * (NP - 1), M);
+    exchange<RB>(sm, v, tau, lo, LOGN - RB);
+    inv_pass<RB, RL, RB - RL, LAZY>(v, tau, LOGN - RB, RB * (NP - 1), M);
 }
 
 // ---------------------------------------------------------------- grid kernels (one CTA per limb polynomial)
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJobs J
         src = (const uint32_t *)J.src + (long long)p * J.src_stride;
     else
         src = (const u64 *)J.src + (long long)p * J.src_stride;
-    u64 v[16];
+    u64 v[Cfg<LOGN>::R];
     fwd_load<LOGN>(J.kind, src, J.t, M, tau, v);
     fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, J.dst + (long long)p * J.dst_stride + (long long)limb * N);
 }
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const int limb = local / J.n_out;
     const int o = local - limb * J.n_out;
     const ModDev M = mods[J.mod_base + limb];
-    u64 v[16];
+    u64 v[Cfg<LOGN>::R];
     mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
     inv_transform<LOGN, LAZY>(v, sm, tau, M);
     // natural order: element j = k*T + tau
@@ -293,7 +314,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     if (msg) { dl = J.E->delta_q[J.mod_base + limb]; dls = J.E->delta_qs[J.mod_base + limb]; }
     const u64 t = msg ? J.E->t : 0;
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
+    for (int k = 0; k < Cfg<LOGN>::R; k++) {
         const int x = k * T + tau;
         const ulonglong2 zp = __ldg(M.z + x);
         u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
@@ -356,7 +377,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const ItemSeg 
     FwdItem I;
     while (next_item<FwdItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
-        u64 v[16];
+        u64 v[Cfg<LOGN>::R];
         fwd_load<LOGN>(I.kind, I.src, I.t, M, tau, v);
         fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, I.dst);
     }
@@ -372,12 +393,12 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg 
     MacItem I;
     while (next_item<MacItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
-        u64 v[16];
+        u64 v[Cfg<LOGN>::R];
         mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
         inv_transform<LOGN, LAZY>(v, sm, tau, M);
         const u64 q = M.q;
 #pragma unroll
-        for (int k = 0; k < 16; k++) {
+        for (int k = 0; k < Cfg<LOGN>::R; k++) {
             const int x = k * T + tau;
             const ulonglong2 zp = __ldg(M.z + x);
             u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
