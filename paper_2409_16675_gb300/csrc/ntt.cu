@@ -194,18 +194,24 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
-// in groups of CH coefficients (128-bit sums), result fully reduced
+// in groups of CH coefficients (128-bit sums), result fully reduced.  The
+// finished groups wait in shared memory (the exchange buffer is idle until
+// the inverse transform; thread tau owns slots k*T + tau), so the registers go
+// to loads in flight: the term loop is unrolled by two.  The caller's shared
+// buffer must be free on entry (no thread still reading a previous exchange).
 template <int LOGN, int CH>
 __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const u64 *__restrict__ B,
                                                const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int t0,
-                                               int t1, int limb, const ModDev &M, int tau, u64 (&v)[Cfg<LOGN>::R]) {
+                                               int t1, int limb, const ModDev &M, int tau, u64 (&v)[Cfg<LOGN>::R],
+                                               u64 *sm) {
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
-#pragma unroll
+#pragma unroll 1
     for (int part = 0; part < R / CH; part++) {
         u64 lo[CH], hi[CH];
 #pragma unroll
         for (int kk = 0; kk < CH; kk++) { lo[kk] = 0; hi[kk] = 0; }
         int cnt = 0;
+#pragma unroll 2
         for (int tk = t0; tk < t1; tk++) {
             const u64 *a = A + ((long long)ta[tk] + limb) * N + part * CH * T + tau;
             const u64 *b = B + ((long long)tb[tk] + limb) * N + part * CH * T + tau;
@@ -223,8 +229,11 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
             }
         }
 #pragma unroll
-        for (int kk = 0; kk < CH; kk++) v[part * CH + kk] = reduce128(lo[kk], hi[kk], M);
+        for (int kk = 0; kk < CH; kk++) sm[(part * CH + kk) * T + tau] = reduce128(lo[kk], hi[kk], M);
     }
+#pragma unroll
+    for (int k = 0; k < R; k++) v[k] = sm[k * T + tau];
+    __syncthreads();  // every stash is read before the transform's first exchange reuses the buffer
 }
 
 // Inverse transform: the register-tile bits [0, RB) first, then upward; the
@@ -300,7 +309,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const int o = local - limb * J.n_out;
     const ModDev M = mods[J.mod_base + limb];
     u64 v[Cfg<LOGN>::R];
-    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau, v);
+    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau,
+                                                                   v, sm);
     inv_transform<LOGN, LAZY>(v, sm, tau, M);
     // natural order: element j = k*T + tau
     const u64 q = M.q;
@@ -394,7 +404,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg 
     while (next_item<MacItem>(segs, nseg, total, counter, s_meta, I)) {
         const ModDev M = *I.mod;
         u64 v[Cfg<LOGN>::R];
-        mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v);
+        mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v, sm);
         inv_transform<LOGN, LAZY>(v, sm, tau, M);
         const u64 q = M.q;
 #pragma unroll
