@@ -271,12 +271,14 @@ int he_decode(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt, c
  * form of he_cpmul_conv; the paper has no counterpart).  Jobs may use
  * different contexts (ring degree, limbs, primes) and plans on one device.
  *   plain       one he_cpmul_conv call per job (three launches per job);
- *   persistent  per ring degree present, one persistent forward-NTT kernel
- *               and one persistent multiply-accumulate/inverse-NTT kernel
- *               whose CTAs pull work items (one limb polynomial each, the
- *               heaviest first) from a device counter;
- *   graph       the persistent launch sequence captured once in a CUDA graph
- *               and replayed (needs a non-default stream).
+ *   persistent  per ring degree present, one forward-NTT launch and one
+ *               multiply-accumulate/inverse-NTT launch over device work lists
+ *               (one limb polynomial per item, the heaviest first): either
+ *               persistent CTAs that pull items from a device counter, or one
+ *               CTA per item in list order, as he_batch_autotune measures best
+ *               (default: persistent, 2 CTAs per SM);
+ *   graph       that launch sequence captured once in a CUDA graph and
+ *               replayed (needs a non-default stream).
  * Results are bit-identical in every form and to a job run alone.  The batch
  * owns one device allocation (made by he_batch_prepare) holding every job's
  * NTT-form operands, term tables and work lists; input and output pointers
@@ -291,7 +293,7 @@ typedef struct he_batch he_batch;
 typedef struct he_batch_tuning {
     int32_t logN;
     int32_t regs_ctas_per_sm;  /* register budget: resident CTAs per SM the kernels are compiled for */
-    int32_t grid_ctas_per_sm;  /* persistent CTAs launched per SM */
+    int32_t grid_ctas_per_sm;  /* persistent CTAs launched per SM; 0: one CTA per work item instead */
     float ms;                  /* best time of the ring degree's two launches */
     int32_t fwd_items, mac_items;
 } he_batch_tuning;
@@ -316,8 +318,9 @@ int he_batch_prepare(he_batch *batch);
 /* Run the batch in `mode` on `stream` (asynchronous). */
 int he_batch_run(he_batch *batch, int mode, cudaStream_t stream);
 /* Time every candidate launch configuration of each ring degree on the
- * prepared batch (register budget 1 or 2 CTAs per SM, 1..4 persistent CTAs
- * per SM; three runs each, best kept), keep the fastest, and report it in
+ * prepared batch (register budget 1 or 2 CTAs per SM; 1..4 persistent CTAs
+ * per SM or one CTA per item; three runs each, best kept), keep the fastest,
+ * and report it in
  * out[0 .. min(max_out, n)) with n = number of ring degrees.  Overwrites the
  * jobs' outputs; synchronises; invalidates a captured graph. */
 int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out, int max_out, int *n);
@@ -331,7 +334,7 @@ int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out
  * and operands stay resident in caller memory) waits until its scratch fits
  * in the arena and fewer than max_inflight launch groups are running; the
  * worker then launches up to max_group admitted requests together as
- * persistent queue kernels on the next of n_streams streams, so requests
+ * work-list kernels (one CTA per item) on the next of n_streams streams, so requests
  * arriving while others run join the next group and groups overlap on the
  * device.  Each result is bit-identical to he_cpmul_conv on the same
  * arguments.  Latency is measured from submission to the worker observing

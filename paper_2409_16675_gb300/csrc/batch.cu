@@ -5,9 +5,11 @@
 // NTT-form scratch in one device allocation and turns the whole batch into
 // two device work lists per ring degree: the limb polynomials to forward
 // transform, and the output limb polynomials to multiply-accumulate, inverse
-// transform and add.  The persistent form runs each list with one persistent
-// kernel whose CTAs pull items from an atomic counter (heaviest items first);
-// the graph form replays that launch sequence from a captured CUDA graph.
+// transform and add.  The persistent form runs each list with one launch:
+// persistent CTAs pulling items from an atomic counter (heaviest items
+// first), or one CTA per item in list order, whichever the autotuner
+// measures faster; the graph form replays that launch sequence from a
+// captured CUDA graph.
 // The plain form calls he_cpmul_conv once per job, for comparison.
 #include <algorithm>
 #include <cstdio>
@@ -324,7 +326,7 @@ int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int ma
         int bm = k.minb, bg = k.grid_mult;
         for (int mb : minbs) {
             if (k.logN >= 14 && mb == 2) continue;
-            for (int gm = 1; gm <= 4; gm++) {
+            for (int gm = 0; gm <= 4; gm++) {  // 0: one CTA per item; else persistent CTAs per SM
                 float tmin = 1e30f;
                 for (int rep = 0; rep < 3; rep++) {
                     cudaMemsetAsync(b->counters + 2 * i, 0, 2 * sizeof(int), st);

@@ -260,8 +260,9 @@ struct ItemSeg {
 // Persistent kernel over `total` items (fwd: FwdItem, else MacItem) held in
 // nseg segments sorted by begin (device table), ring degree 2^logN; minb
 // selects the register budget (resident CTAs per SM the kernel is compiled
-// for); lazy only when every item's modulus is below 2^57; grid CTAs;
-// *counter must be 0.
+// for); lazy only when every item's modulus is below 2^57; grid > 0: that
+// many persistent CTAs pulling items from *counter (which must be 0);
+// grid <= 0: one CTA per item, in list order (counter unused).
 int launch_queue(int logN, int minb, bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter,
                  int grid, cudaStream_t st);
 // true when every limb modulus of the context is below 2^57

@@ -351,9 +351,44 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
 // several independently built work lists.  Items of one launch share the ring
 // degree but may use any modulus of any context.  The counter must be zero
 // at launch.
+// Multiply-accumulate, inverse transform and store of one item.  The item is
+// read through its pointer where each field is needed (the output pointers
+// only after the transform's barriers), so no field stays live in registers
+// across the transform.
+template <int LOGN, int MINB, bool LAZY>
+__device__ __forceinline__ void mac_item(const MacItem *__restrict__ ip, u64 *sm, int tau) {
+    constexpr int T = Cfg<LOGN>::T;
+    const ModDev *__restrict__ mp = ip->mod;  // read-only: fields may be re-read rather than kept live
+    const ModDev M = *mp;
+    u64 v[Cfg<LOGN>::R];
+    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(ip->A, ip->B, ip->ta, ip->tb, ip->t0, ip->t1, ip->limb, M, tau,
+                                                        v, sm);
+    inv_transform<LOGN, LAZY>(v, sm, tau, M);
+    u64 *out = ip->out;
+    const u64 *add = ip->add;
+    const u64 q = M.q;
+#pragma unroll
+    for (int k = 0; k < Cfg<LOGN>::R; k++) {
+        const int x = k * T + tau;
+        const ulonglong2 zp = __ldg(M.z + x);
+        u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
+        if (add) r = addm(r, add[x], q);
+        out[x] = r;
+    }
+}
+
+template <int LOGN, bool LAZY>
+__device__ __forceinline__ void fwd_item(const FwdItem *__restrict__ ip, u64 *sm, int tau) {
+    const ModDev *__restrict__ mp = ip->mod;
+    const ModDev M = *mp;
+    u64 v[Cfg<LOGN>::R];
+    fwd_load<LOGN>(ip->kind, ip->src, ip->t, M, tau, v);
+    fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, ip->dst);
+}
+
 template <typename ITEM>
-__device__ __forceinline__ bool next_item(const ItemSeg *segs, int nseg, int total, int *counter, int *s_meta,
-                                          ITEM &out) {
+__device__ __forceinline__ const ITEM *next_item(const ItemSeg *segs, int nseg, int total, int *counter,
+                                                 int *s_meta) {
     if (threadIdx.x == 0) {
         const int it = atomicAdd(counter, 1);
         int sidx = 0;
@@ -372,9 +407,8 @@ __device__ __forceinline__ bool next_item(const ItemSeg *segs, int nseg, int tot
     __syncthreads();
     const int it = s_meta[0], sidx = s_meta[1];
     __syncthreads();
-    if (it >= total) return false;
-    out = ((const ITEM *)segs[sidx].items)[it - segs[sidx].begin];
-    return true;
+    if (it >= total) return nullptr;
+    return (const ITEM *)segs[sidx].items + (it - segs[sidx].begin);
 }
 
 // LAZY: every item's modulus is below 2^57 (checked by the host per launch)
@@ -383,14 +417,8 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_queue(const ItemSeg 
                                                                   int total, int *counter) {
     extern __shared__ u64 sm[];
     __shared__ int s_meta[2];
-    const int tau = threadIdx.x;
-    FwdItem I;
-    while (next_item<FwdItem>(segs, nseg, total, counter, s_meta, I)) {
-        const ModDev M = *I.mod;
-        u64 v[Cfg<LOGN>::R];
-        fwd_load<LOGN>(I.kind, I.src, I.t, M, tau, v);
-        fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, I.dst);
-    }
+    while (const FwdItem *ip = next_item<FwdItem>(segs, nseg, total, counter, s_meta))
+        fwd_item<LOGN, LAZY>(ip, sm, threadIdx.x);
 }
 
 template <int LOGN, int MINB, bool LAZY>
@@ -398,24 +426,34 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_queue(const ItemSeg 
                                                                   int total, int *counter) {
     extern __shared__ u64 sm[];
     __shared__ int s_meta[2];
-    constexpr int T = Cfg<LOGN>::T;
-    const int tau = threadIdx.x;
-    MacItem I;
-    while (next_item<MacItem>(segs, nseg, total, counter, s_meta, I)) {
-        const ModDev M = *I.mod;
-        u64 v[Cfg<LOGN>::R];
-        mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(I.A, I.B, I.ta, I.tb, I.t0, I.t1, I.limb, M, tau, v, sm);
-        inv_transform<LOGN, LAZY>(v, sm, tau, M);
-        const u64 q = M.q;
-#pragma unroll
-        for (int k = 0; k < Cfg<LOGN>::R; k++) {
-            const int x = k * T + tau;
-            const ulonglong2 zp = __ldg(M.z + x);
-            u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
-            if (I.add) r = addm(r, I.add[x], q);
-            I.out[x] = r;
-        }
+    while (const MacItem *ip = next_item<MacItem>(segs, nseg, total, counter, s_meta))
+        mac_item<LOGN, MINB, LAZY>(ip, sm, threadIdx.x);
+}
+
+// One CTA per item (no loop): CTA b takes item b of the segment table.  The
+// hardware block scheduler then hands out items in list order (heaviest
+// first), and each CTA has the register picture of the grid kernels.
+template <typename ITEM>
+__device__ __forceinline__ const ITEM *item_at(const ItemSeg *segs, int nseg, int it) {
+    int lo = 0, hi = nseg - 1;  // last segment whose begin <= it
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].begin <= it) lo = mid;
+        else hi = mid - 1;
     }
+    return (const ITEM *)segs[lo].items + (it - segs[lo].begin);
+}
+
+template <int LOGN, int MINB, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_fwd_items(const ItemSeg *__restrict__ segs, int nseg) {
+    extern __shared__ u64 sm[];
+    fwd_item<LOGN, LAZY>(item_at<FwdItem>(segs, nseg, (int)blockIdx.x), sm, threadIdx.x);
+}
+
+template <int LOGN, int MINB, bool LAZY>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_items(const ItemSeg *__restrict__ segs, int nseg) {
+    extern __shared__ u64 sm[];
+    mac_item<LOGN, MINB, LAZY>(item_at<MacItem>(segs, nseg, (int)blockIdx.x), sm, threadIdx.x);
 }
 
 // true when every modulus of the launch is below 2^57 (no in-transform corrections)
@@ -519,10 +557,17 @@ static int queue_l(bool fwd, const ItemSeg *segs, int nseg, int total, int *coun
     if (!attr_set) {
         cudaFuncSetAttribute(k_fwd_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_mac_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_fwd_items<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mac_items<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    if (fwd) k_fwd_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
-    else k_mac_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+    if (grid <= 0) {  // one CTA per item
+        if (fwd) k_fwd_items<LOGN, MINB, LAZY><<<total, Cfg<LOGN>::T, smem, st>>>(segs, nseg);
+        else k_mac_items<LOGN, MINB, LAZY><<<total, Cfg<LOGN>::T, smem, st>>>(segs, nseg);
+    } else {
+        if (fwd) k_fwd_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+        else k_mac_queue<LOGN, MINB, LAZY><<<grid, Cfg<LOGN>::T, smem, st>>>(segs, nseg, total, counter);
+    }
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ERR_CUDA;
 }
 

@@ -9,10 +9,10 @@
 //      operands and term table) fits in the arena and the number of groups in
 //      flight is below the limit -- requests that arrived while others run on
 //      the GPU join as soon as memory and a slot free up;
-//   3. launches the admitted group as persistent queue kernels (one forward
-//      and one multiply-accumulate/inverse launch per ring degree, each over
-//      a table of the requests' item arrays) on the next of several streams,
-//      so consecutive groups overlap on the device.
+//   3. launches the admitted group as work-list kernels (one forward and one
+//      multiply-accumulate/inverse launch per ring degree, each over a table
+//      of the requests' item arrays, one CTA per item) on the next of several
+//      streams, so consecutive groups overlap on the device.
 // A request's arena block holds its operands, term table and work items, so
 // admission is the only point where memory can run short: a launch never
 // waits for memory, and the oldest waiting request always fits once the
@@ -217,8 +217,10 @@ int launch_group(he_server *s, std::vector<int64_t> &ids, he_server::Flight &f) 
             const int k = 2 * (int)i + pass;
             const int mb = degrees[i] >= 14 ? 1 : 2;
             const he::ItemSeg *segs = (const he::ItemSeg *)(ctl + seg_base + k * per_table);
+            // one CTA per item, heaviest first within each request (the form the
+            // batch autotuner measures fastest on these kernels)
             int rc = he::launch_queue(degrees[i], mb, pass == 0, lazy[i] != 0, segs, nseg[k], total[k], counters + k,
-                                      s->n_sms * 2, st);
+                                      0, st);
             if (rc) return rc;
         }
     if (cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming) != cudaSuccess) return HE_ERR_CUDA;
