@@ -324,6 +324,12 @@ int he_batch_run(he_batch *batch, int mode, cudaStream_t stream);
  * out[0 .. min(max_out, n)) with n = number of ring degrees.  Overwrites the
  * jobs' outputs; synchronises; invalidates a captured graph. */
 int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out, int max_out, int *n);
+/* Set the launch configuration of the listed ring degrees (logN,
+ * regs_ctas_per_sm 1..2 -- 1 only for logN >= 14 --, grid_ctas_per_sm 0..16;
+ * ms and the item counts are ignored), e.g. to reuse an earlier tuning.
+ * INVALID_ARG for a value out of range or a degree with no job; invalidates
+ * a captured graph. */
+int he_batch_set_tuning(he_batch *batch, const he_batch_tuning *tuning, int n);
 
 /* ------------------------------------------------------------------
  * Continuous-batching request server for CPMul convolution layers (the

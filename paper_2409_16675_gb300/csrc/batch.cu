@@ -311,6 +311,28 @@ int he_batch_run(he_batch *b, int mode, cudaStream_t st) {
     return HE_OK;
 }
 
+int he_batch_set_tuning(he_batch *b, const he_batch_tuning *t, int n) {
+    if (!b || (n > 0 && !t) || n < 0) return HE_ERR_INVALID_ARG;
+    if (!b->prepared) return bfail(b, HE_ERR_INVALID_ARG, "he_batch_prepare first");
+    for (int i = 0; i < n; i++) {
+        if (t[i].regs_ctas_per_sm < 1 || t[i].regs_ctas_per_sm > 2 || t[i].grid_ctas_per_sm < 0 ||
+            t[i].grid_ctas_per_sm > 16)
+            return bfail(b, HE_ERR_INVALID_ARG, "tuning out of range (regs 1..2, grid 0..16)");
+        if (t[i].logN >= 14 && t[i].regs_ctas_per_sm == 2)
+            return bfail(b, HE_ERR_INVALID_ARG, "ring degrees >= 2^14 run one CTA per SM");
+        bool found = false;
+        for (auto &k : b->classes)
+            if (k.logN == t[i].logN) {
+                k.minb = t[i].regs_ctas_per_sm;
+                k.grid_mult = t[i].grid_ctas_per_sm;
+                found = true;
+            }
+        if (!found) return bfail(b, HE_ERR_INVALID_ARG, "no job of that ring degree");
+    }
+    drop_graph(b);
+    return HE_OK;
+}
+
 int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int max_out, int *n_out) {
     if (!b || !st) return HE_ERR_INVALID_ARG;
     if (!b->prepared) return bfail(b, HE_ERR_INVALID_ARG, "he_batch_prepare first");

@@ -116,6 +116,7 @@ def _load():
         "he_batch_run": [vp, i32, vp],
         "he_batch_autotune": [vp, vp, ctypes.POINTER(he_batch_tuning), i32, ctypes.POINTER(i32)],
         "he_batch_add_cpmul2": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp],
+        "he_batch_set_tuning": [vp, ctypes.POINTER(he_batch_tuning), i32],
         "he_server_create": [ctypes.POINTER(he_server_config), pp],
         "he_server_submit": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)],
         "he_server_poll": [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
@@ -341,6 +342,14 @@ def he_batch_prepare(b):
 
 def he_batch_run(b, mode):
     _bcheck(lib.he_batch_run(b, mode, _stream()), b)
+
+
+def he_batch_set_tuning(b, tunings):
+    """tunings: dicts with logN, regs_ctas_per_sm, grid_ctas_per_sm."""
+    arr = (he_batch_tuning * len(tunings))()
+    for i, t in enumerate(tunings):
+        arr[i].logN, arr[i].regs_ctas_per_sm, arr[i].grid_ctas_per_sm = t["logN"], t["regs_ctas_per_sm"], t["grid_ctas_per_sm"]
+    _bcheck(lib.he_batch_set_tuning(b, arr, len(tunings)), b)
 
 
 def he_batch_autotune(b):

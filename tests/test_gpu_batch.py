@@ -85,3 +85,38 @@ def test_batch_forms_identical_and_equal_alone():
         assert np.array_equal(r.cpu().numpy(), want)
     for c in ctxs.values():
         c.close()
+
+
+def test_every_launch_configuration_gives_the_same_bits():
+    """The work-list launch of each ring degree in every configuration the
+    autotuner can choose (register budget 1 or 2 CTAs per SM; persistent with
+    1..4 CTAs per SM, or one CTA per item) gives the plain form's bits, and
+    out-of-range tunings are refused."""
+    jobs = wl.batched_jobs(seed=321, n_jobs=8, channels=(3, 16), sizes=(8, 12), kernels=(1, 3), degrees=(4096, 8192))
+    ctxs, items = build(jobs, B=1)
+    b = nv.he_batch_create(0)
+    for (c, p, ct, pt, out) in items:
+        nv.he_batch_add_cpmul(b, c.h, p.h, 1, ct, pt, None, out)
+    nv.he_batch_prepare(b)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nv.he_batch_run(b, nv.HE_BATCH_PLAIN)
+        s.synchronize()
+        ref = [it[4].clone() for it in items]
+        degrees = sorted({c.N.bit_length() - 1 for c in ctxs.values()})
+        for regs in (1, 2):
+            for grid in range(0, 5):
+                for it in items:
+                    it[4].zero_()
+                nv.he_batch_set_tuning(b, [dict(logN=d, regs_ctas_per_sm=regs, grid_ctas_per_sm=grid) for d in degrees])
+                nv.he_batch_run(b, nv.HE_BATCH_GRAPH if grid % 2 else nv.HE_BATCH_PERSISTENT)
+                s.synchronize()
+                for it, r in zip(items, ref):
+                    assert torch.equal(it[4], r), (regs, grid)
+    with pytest.raises(nv.HEError):
+        nv.he_batch_set_tuning(b, [dict(logN=12, regs_ctas_per_sm=3, grid_ctas_per_sm=0)])
+    with pytest.raises(nv.HEError):
+        nv.he_batch_set_tuning(b, [dict(logN=15, regs_ctas_per_sm=1, grid_ctas_per_sm=0)])
+    nv.he_batch_destroy(b)
+    for c in ctxs.values():
+        c.close()
