@@ -45,11 +45,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve"],
+    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve", "plancount"],
                     help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
                          "train: one CNN training step's eight linear operations, batch 64; "
                          "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph; "
-                         "serve: 64 clients, Poisson arrivals swept over --rates, p50/p99 latency")
+                         "serve: 64 clients, Poisson arrivals swept over --rates, p50/p99 latency; "
+                         "plancount: polynomial products of both packings over input and kernel sizes (no GPU)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000,6000", help="serve: arrival rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: measured seconds per rate")
     ap.add_argument("--serve-warmup", type=float, default=1.0, help="serve: warm-up seconds per rate")
@@ -528,6 +529,38 @@ def run_serve(args):
         ctx.close()
 
 
+def run_plancount(args):
+    """Multiply-count sweep of Section 3.3 / Fig. 8: polynomial products per
+    image (MG * G * T) of the conventional and the correlated packing for a
+    C = 3 input of H x H, kernels h x h with same and valid padding, M = 3
+    output channels, at N = 2048, 4096, 8192.  Host-only plan search."""
+    from paper_2409_16675_gb300 import native as nv
+    rows, best = [], None
+    for N in (2048, 4096, 8192):
+        for H in (8, 16, 32, 64):
+            for h in (1, 3, 5, 7, 9, 11):
+                if h > H:
+                    continue
+                for pad in sorted({0, h // 2}):
+                    cnt = {}
+                    for name, enc in (("conv", nv.HE_ENC_CONVENTIONAL), ("corr", nv.HE_ENC_CORRELATED)):
+                        try:
+                            i = nv.he_plan_search(N, 3, H, H, 3, h, pad, enc)
+                            cnt[name] = i.MG * i.G * i.T
+                        except nv.HEError:
+                            cnt[name] = None
+                    r = (cnt["conv"] / cnt["corr"]) if cnt["conv"] and cnt["corr"] else None
+                    rows.append({"N": N, "H": H, "h": h, "pad": pad, "conventional": cnt["conv"],
+                                 "correlated": cnt["corr"], "ratio": r})
+                    if r is not None and (best is None or r > best["ratio"]):
+                        best = rows[-1]
+    print(json.dumps({"metric": "polynomial products per image, conventional vs correlated packing (Fig. 8 sweep)",
+                      "unit": "products", "value": best["ratio"] if best else None, "max_ratio_at": best,
+                      "rows": rows, "data": "plan search only",
+                      "config": {"workload": "C=3, M=3, H in {8,16,32,64}, h in {1..11}, N in {2048,4096,8192}"}}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched":
@@ -535,6 +568,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "plancount":
+        run_plancount(args)
         return
     if args.impl == "reference":
         run_reference(args)

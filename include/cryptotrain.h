@@ -185,6 +185,12 @@ int he_pt_sub(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int64_t n, uint
  * matrix rows), so a layer has MG = ceil(M / Mn) kernel polynomials per
  * channel group; the plan minimises the products MG * G * T per image. */
 int he_conv_plan(he_ctx *ctx, const he_conv_shape *shape, int encoding, he_plan **plan);
+/* he_plan_search: the same window and output-packing search for ring degree
+ * N without a context (host only, no device memory): fills *info exactly as
+ * he_plan_query would for the plan he_conv_plan builds.  Used to count
+ * polynomial products per image (MG * G * T, Section 3.3 and Fig. 8) for any
+ * shape.  Errors as he_conv_plan; INVALID_ARG also for N not a power of two. */
+int he_plan_search(int N, const he_conv_shape *shape, int encoding, he_plan_info *info);
 int he_plan_destroy(he_plan *plan);
 int he_plan_query(const he_plan *plan, he_plan_info *info);
 

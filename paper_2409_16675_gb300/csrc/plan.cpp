@@ -177,22 +177,32 @@ static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vec
     return true;
 }
 
-int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std::string &err) {
+// The window and output-packing search alone (no maps).
+static int search_plan(int N, const he_conv_shape &s, int encoding, he_plan_info &I, std::vector<Tile> &tiles,
+                       std::string &err) {
     if (s.C < 1 || s.H < 1 || s.W < 1 || s.M < 1 || s.h < 1 || s.pad < 0 || s.pad > s.h - 1 ||
         s.H + 2 * s.pad - s.h + 1 < 1 || s.W + 2 * s.pad - s.h + 1 < 1) {
         err = "bad convolution shape";
         return HE_ERR_INVALID_ARG;
     }
     if (encoding != HE_ENC_CONVENTIONAL && encoding != HE_ENC_CORRELATED) { err = "bad encoding"; return HE_ERR_INVALID_ARG; }
-    const int N = c->N;
-    he_plan_info I;
+    if (N < 2 || (N & (N - 1))) { err = "N must be a power of two"; return HE_ERR_INVALID_ARG; }
     memset(&I, 0, sizeof I);
     I.encoding = encoding;
     I.Ho = s.H + 2 * s.pad - s.h + 1;
     I.Wo = s.W + 2 * s.pad - s.h + 1;
-    std::vector<Tile> tiles;
     const bool ok = encoding == HE_ENC_CONVENTIONAL ? conv_search(N, s, I, tiles) : corr_search(N, s, I, tiles);
     if (!ok) { err = "no partition window fits the ring"; return HE_ERR_PLAN_DOES_NOT_FIT; }
+    I.MG = (s.M + I.Mn - 1) / I.Mn;
+    return HE_OK;
+}
+
+int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std::string &err) {
+    const int N = c->N;
+    he_plan_info I;
+    std::vector<Tile> tiles;
+    const int rc = search_plan(N, s, encoding, I, tiles, err);
+    if (rc) return rc;
     p->s = s;
     p->info = I;
     p->N = N;
@@ -271,3 +281,13 @@ int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std:
 }
 
 }  // namespace he
+
+extern "C" int he_plan_search(int N, const he_conv_shape *shape, int encoding, he_plan_info *info) {
+    if (!shape || !info) return HE_ERR_INVALID_ARG;
+    he_plan_info I;
+    std::vector<he::Tile> tiles;
+    std::string err;
+    const int rc = he::search_plan(N, *shape, encoding, I, tiles, err);
+    if (!rc) *info = I;
+    return rc;
+}

@@ -98,6 +98,7 @@ def _load():
         "he_conv_plan": [vp, ctypes.POINTER(he_conv_shape), i32, pp],
         "he_plan_destroy": [vp],
         "he_plan_query": [vp, ctypes.POINTER(he_plan_info)],
+        "he_plan_search": [i32, ctypes.POINTER(he_conv_shape), i32, ctypes.POINTER(he_plan_info)],
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
@@ -242,6 +243,14 @@ def he_conv_plan(ctx, C, H, W, M, h, pad, encoding):
     p = ctypes.c_void_p()
     _check(lib.he_conv_plan(ctx, ctypes.byref(s), encoding, ctypes.byref(p)), ctx)
     return p
+
+
+def he_plan_search(N, C, H, W, M, h, pad, encoding) -> "he_plan_info":
+    """Plan search without a context or a GPU (host only)."""
+    s = he_conv_shape(C, H, W, M, h, pad)
+    info = he_plan_info()
+    _check(lib.he_plan_search(N, ctypes.byref(s), encoding, ctypes.byref(info)))
+    return info
 
 
 def he_plan_destroy(plan):
