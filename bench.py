@@ -45,12 +45,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve", "plancount"],
+    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve", "plancount", "protocols"],
                     help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
                          "train: one CNN training step's eight linear operations, batch 64; "
                          "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph; "
                          "serve: 64 clients, Poisson arrivals swept over --rates, p50/p99 latency; "
-                         "plancount: polynomial products of both packings over input and kernel sizes (no GPU)")
+                         "plancount: polynomial products of both packings over input and kernel sizes (no GPU); "
+                         "protocols: CryptoTrain-B vs CryptoTrain-P on the same layer (online server time, step)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000,6000", help="serve: arrival rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: measured seconds per rate")
     ap.add_argument("--serve-warmup", type=float, default=1.0, help="serve: warm-up seconds per rate")
@@ -561,6 +562,59 @@ def run_plancount(args):
           flush=True)
 
 
+def run_protocols(args):
+    """CryptoTrain-B (Section 3.1) against CryptoTrain-P (Section 3.2) on the
+    3x32x32 -> 16 layer at N = 8192, batch 64: the server's online work (B: the
+    [x][w] CCMul with relinearisation; P: the fused two-CPMul + CCAdd and the
+    PPMul), the offline work of P (CCMul-Precompute), and whole steps.  The
+    paper reports CCMul at about 7x a CPMul on its CPU (Section 3.2)."""
+    import torch
+
+    from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
+
+    w_ = wl.CONV_MID
+    B = args.batch
+    ctx = layer.Context(w_.ring)
+    keys = layer.Keys(ctx, w_.seed * 7 + 1, True)
+    plan = layer.Plan(ctx, w_.shape, w_.encoding)
+    pl, bl = layer.PLayer(ctx, keys, plan, B), layer.BLayer(ctx, keys, plan, B)
+    x_h, k_h = wl.layer_inputs(w_, B)
+    x, k = torch.from_numpy(x_h).cuda(), torch.from_numpy(k_h).cuda()
+    seeds = wl.protocol_seeds(w_.seed)
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    pl.client_prepare(x, k, seeds)
+    bl.client_prepare(x, k, seeds)
+    reps = max(3, args.steps)
+    p_offline = timed(pl.offline, reps)
+    p_online = timed(pl.online, reps)
+    b_online = timed(bl.online, reps)
+    p_step = timed(lambda: pl.step(x, k, seeds), reps)
+    b_step = timed(lambda: bl.step(x, k, seeds), reps)
+    same = bool(torch.equal(pl.client_finish(), bl.client_finish()))
+    print(json.dumps({
+        "metric": "CryptoTrain-B vs CryptoTrain-P linear layer (3x32x32 -> 16, N=8192, batch %d)" % B,
+        "unit": "ms", "value": b_online / p_online, "higher_is_better": False, "n_gpus": 1, "dtype": "u64",
+        "data": "synthetic", "steps": reps, "warmup": args.warmup,
+        "online_ms": {"B_ccmul": b_online, "P_cpmul_ppmul": p_online}, "P_offline_ms": p_offline,
+        "step_ms": {"B": b_step, "P": p_step}, "online_ratio_B_over_P": b_online / p_online,
+        "layers_per_s": {"B": B / (b_step / 1000.0), "P": B / (p_step / 1000.0)},
+        "same_decoded_outputs": same,
+        "config": {"workload": w_.name, "batch": B, "N": w_.ring.N, "L": w_.ring.L, "t": w_.ring.t}}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched":
@@ -571,6 +625,9 @@ def main():
         return
     if args.workload == "plancount":
         run_plancount(args)
+        return
+    if args.workload == "protocols":
+        run_protocols(args)
         return
     if args.impl == "reference":
         run_reference(args)

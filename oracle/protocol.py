@@ -116,6 +116,42 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0) 
     return LayerRun(plan, keys, xp, wp, r_x, r_w, ct_x, ct_w, ct_rx, ct_rw, rr, out, p, y)
 
 
+@dataclass
+class LayerRunB:
+    plan: packing.Plan
+    keys: he.Keys
+    x_polys: np.ndarray
+    w_polys: np.ndarray
+    ct_x: np.ndarray
+    ct_w: np.ndarray
+    out: np.ndarray          # [B*MG*T][2][L][N] relinearised [x][w]
+    y: np.ndarray
+
+
+def run_layer_b(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRunB:
+    """CryptoTrain-B linear layer (Section 3.1): encrypt x and w, multiply the
+    ciphertexts (CCMul with relinearisation; the G channel groups of an output
+    summed before the rounding), decrypt and decode.  Object indices as in
+    run_layer (enc_x, enc_w streams)."""
+    t = P.t
+    x = np.asarray(x)
+    if x.ndim == 3:
+        x = x[None]
+    B = x.shape[0]
+    if keys is None:
+        keys = he.keygen(P, seeds.keys, True)
+    xp = np.concatenate([packing.encode_input(plan, x[b], t).reshape(-1, P.N) for b in range(B)])
+    wp = packing.encode_kernel(plan, w, t).reshape(-1, P.N)
+    ct_x = he.encrypt(P, keys, xp, seeds.enc_x)
+    ct_w = he.encrypt(P, keys, wp, seeds.enc_w)
+    out = he.ccmul(P, keys, ct_x, ct_w, precompute_pairs(plan, B), plan.G)
+    dec = he.decrypt(P, keys, out).reshape(B, plan.MG, plan.T, P.N)
+    y = np.stack([packing.decode(plan, dec[b], t) for b in range(B)])
+    if B == 1:
+        y = y[0]
+    return LayerRunB(plan, keys, xp, wp, ct_x, ct_w, out, y)
+
+
 def conv_reference(x, w, pad):
     """Direct integer cross-correlation (what a CNN layer computes), used as
     the brute-force check of the whole protocol: y[m,a,b] = sum_{c,k,l}

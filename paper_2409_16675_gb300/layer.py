@@ -158,3 +158,45 @@ class PLayer:
         self.offline()
         self.online()
         return self.client_finish()
+
+
+class BLayer:
+    """One CryptoTrain-B linear layer over a batch of B images (Section 3.1,
+    the baseline protocol that CryptoTrain-P improves on): the client encrypts
+    x and w; the server multiplies the two ciphertexts online (CCMul with
+    relinearisation, the products of a kernel's channel groups summed before
+    the one rounding); the client decrypts and decodes x w directly."""
+
+    def __init__(self, ctx: Context, keys: Keys, plan: Plan, batch: int):
+        self.ctx, self.keys, self.plan, self.B = ctx, keys, plan, batch
+        c, s = ctx, plan.shape
+        nx, nw, no = batch * plan.T * plan.G, plan.MG * plan.G, batch * plan.MG * plan.T
+        self.nx, self.nw, self.no = nx, nw, no
+        self.xp, self.wp = c.u64(nx, c.N), c.u64(nw, c.N)
+        self.ct_x, self.ct_w, self.out = c.ct(nx), c.ct(nw), c.ct(no)
+        self.dec = c.u64(no, c.N)
+        self.y = torch.empty((batch, s.M, plan.info.Ho, plan.info.Wo), dtype=torch.int64, device=c.device)
+
+    def client_prepare(self, x, w, seeds: ProtocolSeeds):
+        """Client: encode and encrypt x and w."""
+        c = self.ctx
+        self.plan.encode_input(x, self.B, self.xp)
+        self.plan.encode_kernel(w, self.wp)
+        nv.he_encrypt_many(c.h, self.keys.h, [(self.xp, self.nx, seeds.enc_x, self.ct_x),
+                                              (self.wp, self.nw, seeds.enc_w, self.ct_w)])
+
+    def online(self):
+        """Server, online: [x][w] by CCMul + relinearisation."""
+        nv.he_ccmul_conv_precompute(self.ctx.h, self.keys.h, self.plan.h, self.B, self.ct_x, self.ct_w, self.out)
+
+    def client_finish(self):
+        """Client: Dec([x][w]) decoded to [B, M, Ho, Wo]."""
+        c = self.ctx
+        nv.he_decrypt(c.h, self.keys.h, self.out, self.no, self.dec)
+        nv.he_decode(c.h, self.plan.h, self.B, self.dec, None, self.y)
+        return self.y
+
+    def step(self, x, w, seeds: ProtocolSeeds):
+        self.client_prepare(x, w, seeds)
+        self.online()
+        return self.client_finish()

@@ -330,6 +330,29 @@ def test_layer_bench_configuration_batch64_sampled():
     plan.close()
 
 
+@pytest.mark.parametrize("name,shape_of,enc", [("n4096", wl.CONV_SMALL, "conv"), ("n8192", wl.CONV_MID, "corr")])
+def test_layer_b_protocol_bits(name, shape_of, enc):
+    """CryptoTrain-B (Section 3.1): the online [x][w] CCMul of the GPU equals
+    the oracle's bit for bit, and decodes to the exact convolution."""
+    c = ctx_for(name)
+    s = shape_of.shape
+    seeds = wl.protocol_seeds(shape_of.seed + 5)
+    x = wl.activations(shape_of.seed + 6, (1, s.C, s.H, s.W))
+    w = wl.weights(shape_of.seed + 7, (s.M, s.C, s.h, s.h))
+    keys = layer.Keys(c, seeds.keys, True)
+    plan = layer.Plan(c, s, enc)
+    bl = layer.BLayer(c, keys, plan, 1)
+    y = to_np(bl.step(cuda(x), cuda(w), seeds))
+    op = packing.make_plan(enc, c.N, s.C, s.H, s.W, s.M, s.h, s.pad)
+    ref = protocol.run_layer_b(oparams(c), op, x, w, seeds)
+    assert np.array_equal(to_np(bl.ct_x), ref.ct_x)
+    assert np.array_equal(to_np(bl.out), ref.out)
+    assert np.array_equal(y[0], ref.y)
+    assert np.array_equal(ref.y, protocol.conv_reference(x[0], w, s.pad))
+    keys.close()
+    plan.close()
+
+
 def test_layer_batched_ragged_tiles():
     """batch 3, several tiles and channel groups with ragged tails at N = 1024."""
     shape = wl.ConvShape(8, 24, 17, 3, 3, 2)

@@ -203,3 +203,19 @@ def test_protocol_images_of_a_batch_one_at_a_time():
     # a wrong offset gives other ciphertexts (the index really enters the streams)
     other = protocol.run_layer(P, plan, x[2], w, seeds, keys=full.keys, first_image=1)
     assert not np.array_equal(other.ct_x, full.ct_x[2 * nx:3 * nx])
+
+
+@pytest.mark.parametrize("enc,pad", [("corr", 1), ("conv", 0)])
+def test_protocol_b_decodes_to_conv(enc, pad):
+    """CryptoTrain-B (Section 3.1): Dec([x][w]) decodes to the integer
+    convolution and equals the plaintext product x^ w^ in R_t."""
+    spec = wl.RingSpec(1024, (40, 40, 40), 65537)
+    P = he.Params.from_spec(spec)
+    plan = packing.make_plan(enc, P.N, 3, 10, 9, 2, 3, pad)
+    x = wl.activations(7, (3, 10, 9))
+    w = wl.weights(8, (2, 3, 3, 3))
+    run = protocol.run_layer_b(P, plan, x, w, wl.protocol_seeds(21))
+    assert np.array_equal(run.y, protocol.conv_reference(x, w, pad))
+    dec = he.decrypt(P, run.keys, run.out)
+    xw = he.ppmul_terms(P, run.x_polys, run.w_polys, packing.product_terms(plan))
+    assert np.array_equal(dec, xw)
