@@ -169,6 +169,17 @@ int he_encrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *pt, int n, uint
  * [1, 4], a negative count or a missing pointer of a non-empty group. */
 int he_encrypt_many(he_ctx *ctx, const he_keys *keys, int n_groups, const uint64_t *const *pts, const int *counts,
                     const uint64_t *seeds, uint64_t *const *cts, cudaStream_t stream);
+/* Seed-compressed secret-key encryption (the client of Section 3 holds the
+ * secret key; no paper counterpart beyond eps).  he_encrypt_symmetric:
+ * pt [n][N] in [0,t) -> c0 [n][L][N] with c0_k = -(a_k s + e_k) + Delta m_k,
+ * a_k uniform mod q from the streams (seed, 10, k, limb) and e_k CBD from
+ * (seed, 11, k); the ciphertext is (c0_k, a_k), of which only c0 and the
+ * 8-byte seed travel (half the bytes of a full ciphertext).
+ * he_expand_symmetric: (seed, c0 [n][L][N]) -> ct [n][2][L][N], regenerating
+ * a_k on the device.  Both INVALID_ARG for n < 0 or missing buffers. */
+int he_encrypt_symmetric(he_ctx *ctx, const he_keys *keys, const uint64_t *pt, int n, uint64_t seed, uint64_t *c0,
+                         cudaStream_t stream);
+int he_expand_symmetric(he_ctx *ctx, uint64_t seed, int n, const uint64_t *c0, uint64_t *ct, cudaStream_t stream);
 /* he_decrypt, sigma(c, sk) of Section 2: m = floor((t [c0 + c1 s]_q +
  * floor(q/2)) / q) mod t, exactly.  ct [n][2][L][N] -> pt [n][N]. */
 int he_decrypt(he_ctx *ctx, const he_keys *keys, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t stream);

@@ -25,6 +25,7 @@ import numpy as np
 from . import _clib
 
 TAG_SK, TAG_PK_A, TAG_PK_E, TAG_ENC_U, TAG_ENC_E1, TAG_ENC_E2, TAG_RLK_A, TAG_RLK_E, TAG_MASK = range(1, 10)
+TAG_SYM_A, TAG_SYM_E = 10, 11
 
 
 def _u64(a):
@@ -175,6 +176,41 @@ def encrypt(P: Params, keys: Keys, m, seed: int, first: int = 0) -> np.ndarray:
     pc = P.c()
     for k in range(m.shape[0]):
         _clib.lib().orc_encrypt(ctypes.byref(pc), _u64(keys.pk), _u64(m[k]), seed, first + k, _u64(ct[k]))
+    return ct
+
+
+def encrypt_symmetric(P: Params, keys: Keys, m, seed: int, first: int = 0) -> np.ndarray:
+    """Seed-compressed secret-key encryption: c0_k = -(a_k s + e_k) + Delta m_k
+    with a_k uniform mod q from streams (seed, SYM_A, first + k, limb) and e_k
+    CBD from (seed, SYM_E, first + k); returns c0 [n][L][N] (the ciphertext
+    is (c0_k, a_k), see expand_symmetric).  Written from the definitions with
+    the oracle's samplers and polymul, limb by limb."""
+    m = np.atleast_2d(np.asarray(m, dtype=np.uint64))
+    Q = 1
+    for q in P.q:
+        Q *= q
+    delta = Q // P.t
+    out = np.zeros((m.shape[0], P.L, P.N), dtype=np.uint64)
+    for k in range(m.shape[0]):
+        e = sample_cbd(seed, TAG_SYM_E, first + k, P.eta, P.N).astype(object)
+        mk = [int(v) % P.t for v in m[k]]
+        for i, q in enumerate(P.q):
+            a = sample_uniform(seed, TAG_SYM_A, first + k, i, q, P.N)
+            s_i = np.array([int(v) % q for v in keys.sk], dtype=np.uint64)
+            a_s = polymul(a, s_i, q)
+            d = delta % q
+            out[k, i] = [(-(int(x) + int(ee)) + d * mm) % q for x, ee, mm in zip(a_s, e, mk)]
+    return out
+
+
+def expand_symmetric(P: Params, seed: int, c0, first: int = 0) -> np.ndarray:
+    """(seed, c0 [n][L][N]) -> ct [n][2][L][N] with ct_k = (c0_k, a_k)."""
+    c0 = np.asarray(c0, dtype=np.uint64).reshape(-1, P.L, P.N)
+    ct = np.zeros((c0.shape[0], 2, P.L, P.N), dtype=np.uint64)
+    for k in range(c0.shape[0]):
+        ct[k, 0] = c0[k]
+        for i, q in enumerate(P.q):
+            ct[k, 1, i] = sample_uniform(seed, TAG_SYM_A, first + k, i, q, P.N)
     return ct
 
 

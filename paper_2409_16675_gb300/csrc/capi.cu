@@ -380,6 +380,56 @@ int he_encrypt_many(he_ctx *c, const he_keys *k, int n_groups, const uint64_t *c
     return encrypt_groups(c, k, n_groups, pts, counts, seeds, cts, st);
 }
 
+// ------------------------------------------------------------------ seed-compressed symmetric encryption
+// ct_k = (c0, c1) = (-(a_k s + e_k) + Delta m_k, a_k) with a_k uniform mod q
+// from the stream (seed, 10, k, limb) and e_k CBD from (seed, 11, k): the
+// client keeps the secret key, sends c0 and the seed, and the receiver
+// regenerates c1 = a_k from the seed -- half the bytes of a full ciphertext.
+int he_encrypt_symmetric(he_ctx *c, const he_keys *k, const uint64_t *pt, int n, uint64_t seed, uint64_t *c0,
+                         cudaStream_t st) {
+    if (!c || !k || n < 0 || (n && (!pt || !c0))) return HE_ERR_INVALID_ARG;
+    if (!n) return HE_OK;
+    TRY(set_device(c));
+    const int N = c->N, L = c->L;
+    const size_t LN = (size_t)L * N;
+    TRY(ws_reserve(c, 2 * Carver::round((size_t)n * LN * 8) + Carver::round((size_t)n * N) + 4096));
+    Carver cv(c->ws);
+    u64 *a = cv.take<u64>((size_t)n * LN);
+    u64 *an = cv.take<u64>((size_t)n * LN);
+    int8_t *e8 = cv.take<int8_t>((size_t)n * N);
+    TRY(launch_sample(c, SAMPLE_UNIFORM_Q, seed, 10, 0, n, L, a, st));
+    TRY(launch_sample(c, SAMPLE_CBD, seed, 11, 0, n, 1, e8, st));
+    FwdJob f = fwd_job();
+    f.src = a; f.kind = SRC_RNS; f.src_stride = LN; f.dst = an; f.dst_stride = LN; f.n_polys = n; f.n_limbs = L;
+    TRY(launch_fwd(c, f, st));
+    Terms T;
+    for (int i = 0; i < n; i++) { T.add(i * L, 0); T.close(); }
+    MacJob m = mac_job();
+    TRY(upload_terms(c, T, m));
+    m.A = an; m.B = k->s_ntt; m.out = c0; m.out_stride = LN;
+    m.err = e8; m.err_stride = N; m.negate = 1;
+    m.msg = pt; m.msg_stride = N; m.msg_div = 1; m.E = c->d_exact;
+    m.n_out = n; m.n_limbs = L;
+    return launch_mac_intt(c, m, st);
+}
+
+int he_expand_symmetric(he_ctx *c, uint64_t seed, int n, const uint64_t *c0, uint64_t *ct, cudaStream_t st) {
+    if (!c || n < 0 || (n && (!c0 || !ct))) return HE_ERR_INVALID_ARG;
+    if (!n) return HE_OK;
+    TRY(set_device(c));
+    const int N = c->N, L = c->L;
+    const size_t LN = (size_t)L * N;
+    TRY(ws_reserve(c, Carver::round((size_t)n * LN * 8) + 4096));
+    Carver cv(c->ws);
+    u64 *a = cv.take<u64>((size_t)n * LN);
+    TRY(launch_sample(c, SAMPLE_UNIFORM_Q, seed, 10, 0, n, L, a, st));
+    // ct[k] = (c0[k], a[k]): two strided copies into the [n][2][L][N] layout
+    TRY(cuda_check(c, cudaMemcpy2DAsync(ct, 2 * LN * 8, c0, LN * 8, LN * 8, n, cudaMemcpyDeviceToDevice, st),
+                   "c0 copy"));
+    return cuda_check(c, cudaMemcpy2DAsync(ct + LN, 2 * LN * 8, a, LN * 8, LN * 8, n, cudaMemcpyDeviceToDevice, st),
+                      "c1 copy");
+}
+
 int he_decrypt(he_ctx *c, const he_keys *k, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t st) {
     if (!c || !k || n < 0 || (n && (!pt || !ct))) return HE_ERR_INVALID_ARG;
     if (!n) return HE_OK;

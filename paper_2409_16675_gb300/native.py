@@ -102,6 +102,8 @@ def _load():
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
+        "he_encrypt_symmetric": [vp, vp, vp, i32, u64, vp, vp],
+        "he_expand_symmetric": [vp, u64, i32, vp, vp, vp],
         "he_encrypt_many": [vp, vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64),
                             ctypes.POINTER(vp), vp],
         "he_cpmul_conv_noalloc": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
@@ -224,6 +226,14 @@ def he_encrypt_many(ctx, keys, groups):
     seeds = (ctypes.c_uint64 * k)(*[int(g[2]) for g in groups])
     cts = (ctypes.c_void_p * k)(*[_ptr(g[3]) for g in groups])
     _check(lib.he_encrypt_many(ctx, keys, k, pts, counts, seeds, cts, _stream()), ctx)
+
+
+def he_encrypt_symmetric(ctx, keys, pt, n: int, seed: int, c0):
+    _check(lib.he_encrypt_symmetric(ctx, keys, _ptr(pt), n, seed, _ptr(c0), _stream()), ctx)
+
+
+def he_expand_symmetric(ctx, seed: int, n: int, c0, ct):
+    _check(lib.he_expand_symmetric(ctx, seed, n, _ptr(c0), _ptr(ct), _stream()), ctx)
 
 
 def he_decrypt(ctx, keys, ct: torch.Tensor, n: int, pt: torch.Tensor):

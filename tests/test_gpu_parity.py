@@ -101,6 +101,29 @@ def test_encrypt_many_equals_separate_calls():
     keys.close()
 
 
+@pytest.mark.parametrize("name", ["n4096", "n8192", "n16384"])
+def test_symmetric_encryption_bits(name):
+    """Seed-compressed secret-key encryption: c0 and the expanded ciphertext
+    equal the oracle's bit for bit and decrypt to the message."""
+    c = ctx_for(name)
+    P = oparams(c)
+    keys = layer.Keys(c, 31, False)
+    okeys = he.keygen(P, 31, False)
+    n, seed = 3, 4242
+    m = wl.uniform_mod(55, (n, c.N), c.t)
+    c0 = c.u64(n, c.L, c.N)
+    nv.he_encrypt_symmetric(c.h, keys.h, cuda(m), n, seed, c0)
+    ct = c.ct(n)
+    nv.he_expand_symmetric(c.h, seed, n, c0, ct)
+    ref_c0 = he.encrypt_symmetric(P, okeys, m, seed)
+    assert np.array_equal(to_np(c0), ref_c0)
+    assert np.array_equal(to_np(ct), he.expand_symmetric(P, seed, ref_c0))
+    dec = c.u64(n, c.N)
+    nv.he_decrypt(c.h, keys.h, ct, n, dec)
+    assert np.array_equal(to_np(dec), m)
+    keys.close()
+
+
 def test_decrypt_rounding_edges():
     # ciphertexts (x, 0) with x at the rounding boundaries of floor((t x + q/2)/q)
     c = ctx_for("n4096")

@@ -176,3 +176,24 @@ def test_ppmul_equals_schoolbook_mod_t():
         got = he.ppmul_terms(P, a, b, [[(0, 0), (1, 1)]])[0]
         want = [(x + y) % t for x, y in zip(negacyclic_mod(a[0], b[0], t), negacyclic_mod(a[1], b[1], t))]
         assert [int(v) for v in got] == want
+
+
+@pytest.mark.parametrize("N,bits,t", [(64, (40, 41), 257), (1024, (50, 50, 50), 65537)])
+def test_symmetric_encryption_round_trip_and_compression(N, bits, t):
+    """Seed-compressed secret-key encryption: the expanded ciphertext
+    decrypts to the message with fresh-encryption noise, c1 is exactly the
+    seeded uniform stream (so only c0 and the seed need to travel), and the
+    noise c0 + c1 s - Delta m equals -e."""
+    P = he.Params(N, he.gen_primes(N, list(bits)), t)
+    keys = he.keygen(P, 5, False)
+    m = np.random.default_rng(3).integers(0, t, (3, N), dtype=np.uint64)
+    c0 = he.encrypt_symmetric(P, keys, m, seed=99)
+    ct = he.expand_symmetric(P, 99, c0)
+    assert c0.nbytes * 2 == ct.nbytes
+    assert np.array_equal(he.decrypt(P, keys, ct), m)
+    assert max(he.noise_bits(P, keys, ct[k], m[k]) for k in range(3)) <= 5   # |e| <= eta = 21
+    for i, q in enumerate(P.q):
+        assert np.array_equal(ct[1, 1, i], he.sample_uniform(99, he.TAG_SYM_A, 1, i, q, N))
+    # a different seed gives a different ciphertext of the same message
+    ct2 = he.expand_symmetric(P, 98, he.encrypt_symmetric(P, keys, m, seed=98))
+    assert not np.array_equal(ct2, ct) and np.array_equal(he.decrypt(P, keys, ct2), m)
