@@ -45,13 +45,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve", "plancount", "protocols"],
+    ap.add_argument("--workload", default="layer", choices=["layer", "train", "batched", "serve", "plancount", "protocols", "alexnet"],
                     help="layer: the 3x32x32 -> 16 CryptoTrain-P layer (default); "
                          "train: one CNN training step's eight linear operations, batch 64; "
                          "batched: 256 uneven ct x pt convolution jobs, plain vs persistent vs graph; "
                          "serve: 64 clients, Poisson arrivals swept over --rates, p50/p99 latency; "
                          "plancount: polynomial products of both packings over input and kernel sizes (no GPU); "
-                         "protocols: CryptoTrain-B vs CryptoTrain-P on the same layer (online server time, step)")
+                         "protocols: CryptoTrain-B vs CryptoTrain-P on the same layer (online server time, step); "
+                         "alexnet: AlexNet-shaped first convolution and batch norm (64x64x3 input)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000,6000", help="serve: arrival rates (req/s)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serve: measured seconds per rate")
     ap.add_argument("--serve-warmup", type=float, default=1.0, help="serve: warm-up seconds per rate")
@@ -615,6 +616,59 @@ def run_protocols(args):
         "config": {"workload": w_.name, "batch": B, "N": w_.ring.N, "L": w_.ring.L, "t": w_.ring.t}}), flush=True)
 
 
+def run_alexnet(args):
+    """AlexNet-shaped layers on a 64x64x3 (Tiny-ImageNet-sized) input as
+    CryptoTrain-P layers, whole steps (encode, masks, encryptions, offline
+    CCMul-Precompute, online, PPMul, decryption, decoding): the first
+    convolution 3 -> 64 with an 11x11 kernel (same padding, stride 1) and a
+    batch norm over its 64 channels (diagonal 1x1 kernel and bias; the
+    generic plan spends a product on every (output channel, channel group)
+    pair, so a dense-diagonal batch norm costs 2048 products per image here).
+    Ring N = 8192 with 4 x 50-bit limbs and a 40-bit t (no wrap of the sums);
+    batch at most 16.""" 
+    import torch
+
+    from paper_2409_16675_gb300 import layer, workloads as wl
+
+    B = min(args.batch, 16)
+    ctx = layer.Context(wl.RING_TRAIN)
+    keys = layer.Keys(ctx, 77, True)
+    out = {}
+    specs = [("conv1_3x64x64_64_k11", wl.ConvShape(3, 64, 64, 64, 11, 5), False),
+             ("bn1_64x64x64", wl.ConvShape(64, 64, 64, 64, 1, 0), True)]
+    for name, shape, bn in specs:
+        cands = [layer.Plan(ctx, shape, e) for e in ("corr", "conv")]
+        plan = min(cands, key=lambda p: p.MG * p.G * p.T)
+        pl = layer.PLayer(ctx, keys, plan, B, with_bias=bn)
+        x = torch.from_numpy(wl.activations(5, (B, shape.C, shape.H, shape.W))).cuda()
+        if bn:
+            gamma = torch.from_numpy(wl.weights(6, (shape.C,)).astype("int64")).cuda()
+            w, beta = layer.batch_norm_weights(gamma), torch.arange(shape.C, device="cuda") - 32
+        else:
+            w, beta = torch.from_numpy(wl.weights(6, (shape.M, shape.C, shape.h, shape.h))).cuda(), None
+        seeds = wl.protocol_seeds(9)
+        for _ in range(max(1, args.warmup)):
+            pl.step(x, w, seeds, beta)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, args.steps)
+        e0.record()
+        for _ in range(reps):
+            pl.step(x, w, seeds, beta)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "images_per_s": B / (ms / 1000.0), "encoding": plan.encoding,
+                     "products_per_image": plan.MG * plan.G * plan.T}
+        for p in cands:
+            p.close()
+    print(json.dumps({"metric": "AlexNet-shaped CryptoTrain-P layers, images/s (batch %d)" % B, "unit": "images/s",
+                      "value": out["conv1_3x64x64_64_k11"]["images_per_s"], "higher_is_better": True, "n_gpus": 1,
+                      "dtype": "u64", "data": "synthetic", "layers": out, "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": "64x64x3 input, conv 11x11 -> 64, batch norm 64; N=8192, 4x50-bit, 40-bit t",
+                                 "batch": B}}), flush=True)
+
+
 def main():
     args = parse()
     if args.workload == "batched":
@@ -628,6 +682,9 @@ def main():
         return
     if args.workload == "protocols":
         run_protocols(args)
+        return
+    if args.workload == "alexnet":
+        run_alexnet(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -97,6 +97,8 @@ typedef struct he_params {
     int32_t eta;
     int32_t max_ccmul_group;
     int32_t device;
+    double max_ccmul_scratch_bytes;  /* per-call CCMul scratch; larger calls run in chunks of
+                                        outputs (0: 4 GiB) */
 } he_params;
 
 /* Read-only description of a context (filled by he_ctx_query). */
@@ -282,6 +284,19 @@ int he_ppmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *p
  * [batch][MG][T][N] (sub may be NULL); out [batch][M][Ho][Wo]. */
 int he_decode(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *pt, const uint64_t *sub, int64_t *out,
               cudaStream_t stream);
+
+/* he_encode_output: the inverse of he_decode's gather (Section 3.3 output
+ * positions): polys [batch][MG][T][N] = 0 except
+ * polys[b][m / Mn][tile(a,c)][coef(a,c) + (m mod Mn) Sout] = values[b][m][a][c]
+ * mod t (values int64 [batch][M][Ho][Wo], negative values as t - |v| mod t).
+ * Places a per-output plaintext -- a bias, the beta of a batch-norm layer --
+ * where the layer's products land, so that its encryption can be added to
+ * the layer's ciphertexts (he_ct_add). */
+int he_encode_output(he_ctx *ctx, const he_plan *plan, int batch, const int64_t *values, uint64_t *polys,
+                     cudaStream_t stream);
+/* he_ct_add (CCAdd, Section 3.2): out = a + b mod q_i over n ciphertexts
+ * [n][2][L][N]; out may alias a or b. */
+int he_ct_add(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int n, uint64_t *out, cudaStream_t stream);
 
 /* ------------------------------------------------------------------
  * Batched execution of many heterogeneous CPMul convolutions (an execution

@@ -327,6 +327,19 @@ def decode(p: Plan, polys, t_mod) -> np.ndarray:
     return out
 
 
+def encode_output(p: Plan, values, t_mod) -> np.ndarray:
+    """values: [M, Ho, Wo] integers -> [MG][T][N] uint64 mod t holding each
+    value where decode reads that output (zero elsewhere): a per-output
+    plaintext such as a bias, placed on the layer's product positions."""
+    values = np.asarray(values)
+    out = np.zeros((p.MG, p.T, p.N), dtype=np.uint64)
+    for t in range(p.T):
+        for (k, a, b) in output_slots(p, t):
+            for m in range(p.M):
+                out[m // p.Mn, t, k + (m % p.Mn) * p.Sout] = int(values[m, a, b]) % t_mod
+    return out
+
+
 def product_terms(p: Plan):
     """Term lists of the polynomial products: output (mg, t) = sum_g in(t,g) *
     ker(mg,g).  Returns, per output o = mg*T + t, the list of (input poly

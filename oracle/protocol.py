@@ -74,13 +74,18 @@ def ppmul_terms(plan, batch=1):
     return terms
 
 
-def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0) -> LayerRun:
+def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0, bias=None) -> LayerRun:
     """x: [C,H,W] or [B,C,H,W] ints, w: [M,C,h,h] ints; seeds:
     workloads.ProtocolSeeds.  Every random object of the batch is drawn from
     one stream per kind, object index = position in the flattened batch.
     first_image: the batch position of x's first image, so that images of a
     large batch can be recomputed one at a time (the weight-side objects do
-    not depend on it)."""
+    not depend on it).
+    bias: optional per-output-channel integers [M] (a batch-norm beta): each
+    image's encode_output of the bias broadcast over [M, Ho, Wo] is encrypted
+    on the enc_w stream after the kernel polynomials (row k of image b is
+    object MG*G + b*MG*T + k) and added to the precomputed [r^x r^w] (CCAdd),
+    so the layer decodes to conv + bias."""
     t = P.t
     x = np.asarray(x)
     if x.ndim == 3:
@@ -99,6 +104,18 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0) 
     ct_rw = he.encrypt(P, keys, r_w, seeds.enc_rw)
     # offline: [r^x r^w] summed over channel groups
     rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan, B), plan.G)
+    if bias is not None:
+        nw = plan.MG * plan.G
+        bv = np.broadcast_to(np.asarray(bias, dtype=np.int64)[:, None, None], (plan.M, plan.Ho, plan.Wo))
+        no = plan.MG * plan.T
+        for b in range(B):
+            bp = packing.encode_output(plan, bv, t).reshape(-1, P.N)
+            cb = he.encrypt(P, keys, bp, seeds.enc_w, nw + (first_image + b) * no)
+            for o in range(no):
+                for comp in range(2):
+                    for i, q in enumerate(P.q):
+                        row = rr[b * no + o, comp, i]
+                        rr[b * no + o, comp, i] = [(int(u) + int(v)) % q for u, v in zip(row, cb[o, comp, i])]
     # online
     tt = np.uint64(t)
     wm = (wp + (tt - r_w)) % tt

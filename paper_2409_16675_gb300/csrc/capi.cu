@@ -591,23 +591,29 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     const int N = c->N, L = c->L, K = c->K, LK = L + K, ell = c->ell;
     const size_t LN = (size_t)L * N, KN = (size_t)K * N, LKN = (size_t)LK * N;
     const int n_out = n_pairs / group;
+    // per-output scratch: tensor d (3 polys over Q u B), rescaled d0, d1, digits, digit NTTs
+    const size_t per_out = 3 * LKN * 8 + 2 * LN * 8 + (size_t)ell * N * 4 + (size_t)ell * LN * 8;
+    // outputs are processed in chunks whose scratch fits the context's budget (default 4 GiB)
+    const size_t chunk_budget =
+        c->P.max_ccmul_scratch_bytes > 0 ? (size_t)c->P.max_ccmul_scratch_bytes : (size_t)4 << 30;
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_out, chunk_budget / per_out));
     size_t need = Carver::round((size_t)(n_a + n_b) * 2 * KN * 8) + Carver::round((size_t)(n_a + n_b) * 2 * LKN * 8) +
-                  Carver::round((size_t)n_out * 3 * LKN * 8) + Carver::round((size_t)n_out * 2 * LN * 8) +
-                  Carver::round((size_t)n_out * ell * N * 4) + Carver::round((size_t)n_out * ell * LN * 8) + 8192;
+                  Carver::round((size_t)chunk * 3 * LKN * 8) + Carver::round((size_t)chunk * 2 * LN * 8) +
+                  Carver::round((size_t)chunk * ell * N * 4) + Carver::round((size_t)chunk * ell * LN * 8) + 8192;
     TRY(ws_reserve(c, need));
     Carver cv(c->ws);
     u64 *aux_a = cv.take<u64>((size_t)n_a * 2 * KN);
     u64 *aux_b = cv.take<u64>((size_t)n_b * 2 * KN);
     u64 *An = cv.take<u64>((size_t)n_a * 2 * LKN);
     u64 *Bn = cv.take<u64>((size_t)n_b * 2 * LKN);
-    u64 *d = cv.take<u64>((size_t)n_out * 3 * LKN);
-    u64 *dq = cv.take<u64>((size_t)n_out * 2 * LN);
-    uint32_t *dig = cv.take<uint32_t>((size_t)n_out * ell * N);
-    u64 *dign = cv.take<u64>((size_t)n_out * ell * LN);
+    u64 *d = cv.take<u64>((size_t)chunk * 3 * LKN);
+    u64 *dq = cv.take<u64>((size_t)chunk * 2 * LN);
+    uint32_t *dig = cv.take<uint32_t>((size_t)chunk * ell * N);
+    u64 *dign = cv.take<u64>((size_t)chunk * ell * LN);
     // 1. exact base extension Q -> B of both operands
     TRY(launch_base_extend(c, ct_a, (long long)n_a * 2, aux_a, st));
     TRY(launch_base_extend(c, ct_b, (long long)n_b * 2, aux_b, st));
-    // 2. forward NTT over Q u B
+    // 2. forward NTT over Q u B (both operand sets in one launch)
     FwdJob fab[2];
     FwdJob f = fwd_job();
     f.kind = SRC_RNS; f.split = L; f.n_limbs = LK; f.dst_stride = LKN;
@@ -616,40 +622,45 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     f.src = ct_b; f.src2 = aux_b; f.dst = Bn; f.n_polys = n_b * 2;
     fab[1] = f;
     TRY(launch_fwd_multi(c, fab, 2, st));
-    // 3. tensor product (summed over the group) + inverse NTT, output o*3 + j
-    Terms Tt;
-    for (int o = 0; o < n_out; o++)
-        for (int j = 0; j < 3; j++) {
-            for (int pi = o * group; pi < (o + 1) * group; pi++) {
-                const int a0 = pair_a[pi] * 2 * LK, a1 = a0 + LK, b0 = pair_b[pi] * 2 * LK, b1 = b0 + LK;
-                if (j == 0) Tt.add(a0, b0);
-                else if (j == 1) { Tt.add(a0, b1); Tt.add(a1, b0); }
-                else Tt.add(a1, b1);
+    for (int o0 = 0; o0 < n_out; o0 += chunk) {
+        const int nc = std::min(chunk, n_out - o0);
+        // 3. tensor product (summed over the group) + inverse NTT, output o*3 + j
+        Terms Tt;
+        for (int o = o0; o < o0 + nc; o++)
+            for (int j = 0; j < 3; j++) {
+                for (int pi = o * group; pi < (o + 1) * group; pi++) {
+                    const int a0 = pair_a[pi] * 2 * LK, a1 = a0 + LK, b0 = pair_b[pi] * 2 * LK, b1 = b0 + LK;
+                    if (j == 0) Tt.add(a0, b0);
+                    else if (j == 1) { Tt.add(a0, b1); Tt.add(a1, b0); }
+                    else Tt.add(a1, b1);
+                }
+                Tt.close();
             }
-            Tt.close();
-        }
-    MacJob mt = mac_job();
-    TRY(upload_terms(c, Tt, mt));
-    mt.A = An; mt.B = Bn; mt.out = d; mt.out_stride = LKN; mt.n_out = n_out * 3; mt.n_limbs = LK;
-    TRY(launch_mac_intt(c, mt, st));
-    // 4. exact rescaling by t/q and digits of d2
-    TRY(launch_scale_round(c, d, n_out, dq, dig, st));
-    // 5. digits to the NTT domain over Q
-    f = fwd_job();
-    f.kind = SRC_U32; f.src = dig; f.src_stride = N; f.dst = dign; f.dst_stride = LN; f.n_polys = n_out * ell; f.n_limbs = L;
-    TRY(launch_fwd(c, f, st));
-    // 6. key switch: (c0, c1) = (d0, d1) + sum_j D_j rlk_j
-    Terms Tk;
-    for (int o = 0; o < n_out; o++)
-        for (int comp = 0; comp < 2; comp++) {
-            for (int j = 0; j < ell; j++) Tk.add((o * ell + j) * L, (j * 2 + comp) * L);
-            Tk.close();
-        }
-    MacJob mk = mac_job();
-    TRY(upload_terms(c, Tk, mk));
-    mk.A = dign; mk.B = k->rlk_ntt; mk.out = ct_out; mk.out_stride = LN; mk.add = dq; mk.add_stride = LN;
-    mk.n_out = n_out * 2; mk.n_limbs = L;
-    return launch_mac_intt(c, mk, st);
+        MacJob mt = mac_job();
+        TRY(upload_terms(c, Tt, mt));
+        mt.A = An; mt.B = Bn; mt.out = d; mt.out_stride = LKN; mt.n_out = nc * 3; mt.n_limbs = LK;
+        TRY(launch_mac_intt(c, mt, st));
+        // 4. exact rescaling by t/q and digits of d2
+        TRY(launch_scale_round(c, d, nc, dq, dig, st));
+        // 5. digits to the NTT domain over Q
+        f = fwd_job();
+        f.kind = SRC_U32; f.src = dig; f.src_stride = N; f.dst = dign; f.dst_stride = LN; f.n_polys = nc * ell;
+        f.n_limbs = L;
+        TRY(launch_fwd(c, f, st));
+        // 6. key switch: (c0, c1) = (d0, d1) + sum_j D_j rlk_j
+        Terms Tk;
+        for (int o = 0; o < nc; o++)
+            for (int comp = 0; comp < 2; comp++) {
+                for (int j = 0; j < ell; j++) Tk.add((o * ell + j) * L, (j * 2 + comp) * L);
+                Tk.close();
+            }
+        MacJob mk = mac_job();
+        TRY(upload_terms(c, Tk, mk));
+        mk.A = dign; mk.B = k->rlk_ntt; mk.out = ct_out + (size_t)o0 * 2 * LN; mk.out_stride = LN; mk.add = dq;
+        mk.add_stride = LN; mk.n_out = nc * 2; mk.n_limbs = L;
+        TRY(launch_mac_intt(c, mk, st));
+    }
+    return HE_OK;
 }
 
 int he_ccmul_conv_precompute(he_ctx *c, const he_keys *k, const he_plan *p, int batch, const uint64_t *ct_rx,
@@ -706,6 +717,21 @@ int he_decode(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt, const 
     TRY(set_device(c));
     return launch_decode(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.MG * p->info.T, batch, pt, sub, out,
                          st);
+}
+
+int he_encode_output(he_ctx *c, const he_plan *p, int batch, const int64_t *values, uint64_t *polys,
+                     cudaStream_t st) {
+    if (!c || !p || batch < 0 || (batch && (!values || !polys))) return HE_ERR_INVALID_ARG;
+    if (p->N != c->N) return fail(c, HE_ERR_INVALID_ARG, "plan of another ring");
+    TRY(set_device(c));
+    return launch_encode_output(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.MG * p->info.T, batch, values,
+                                polys, st);
+}
+
+int he_ct_add(he_ctx *c, const uint64_t *a, const uint64_t *b, int n, uint64_t *out, cudaStream_t st) {
+    if (!c || n < 0 || (n && (!a || !b || !out))) return HE_ERR_INVALID_ARG;
+    TRY(set_device(c));
+    return launch_ct_add(c, a, b, (long long)n * 2, out, st);
 }
 
 int he_trace_enable(he_ctx *c, int on) {

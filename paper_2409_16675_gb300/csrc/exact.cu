@@ -345,6 +345,27 @@ __global__ void k_decode(const int32_t *__restrict__ map, int HW, int M, int pol
     out[gid] = v > (t - 1) / 2 ? (long long)v - (long long)t : (long long)v;
 }
 
+// inverse of k_decode: out[b*polys*N + map[m*HW + i]] = values[(b*M + m)*HW + i] mod t
+// (out zeroed by the caller; every (m, i) owns a distinct coefficient)
+__global__ void k_encode_output(const int32_t *__restrict__ map, int HW, int M, int polys, int N, int batch,
+                                const long long *__restrict__ values, u64 *__restrict__ out, u64 t) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)batch * M * HW) return;
+    const long long mi = gid % ((long long)M * HW);
+    const long long b = gid / ((long long)M * HW);
+    const long long v = values[gid];
+    out[b * polys * N + map[mi]] = v >= 0 ? (u64)v % t : t - 1 - (u64)(-(v + 1)) % t;
+}
+
+// ciphertext addition (CCAdd): out = a + b mod q_limb over n polynomials of L limbs
+__global__ void k_ct_add(const u64 *__restrict__ a, const u64 *__restrict__ b, long long total, int N, int L,
+                         u64 *__restrict__ out, const ModDev *__restrict__ mods) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const u64 q = mods[(gid / N) % L].q;
+    out[gid] = addm(a[gid], b[gid], q);
+}
+
 __global__ void k_pt_sub(const u64 *__restrict__ a, const u64 *__restrict__ b, long long n, u64 *__restrict__ out,
                          u64 t) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -386,6 +407,23 @@ int launch_decode(he_ctx *c, const int32_t *map, int HW, int M, int polys, int b
     k_decode<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, HW, M, polys, c->N, batch, pt, sub,
                                                                (long long *)out, c->P.t);
     return cuda_check(c, cudaGetLastError(), "k_decode");
+}
+
+int launch_encode_output(he_ctx *c, const int32_t *map, int HW, int M, int polys, int batch, const int64_t *values,
+                         u64 *out, cudaStream_t st) {
+    const long long total = (long long)batch * M * HW;
+    const int rc = cuda_check(c, cudaMemsetAsync(out, 0, (size_t)batch * polys * c->N * 8, st), "output encode clear");
+    if (rc || !total) return rc;
+    k_encode_output<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(map, HW, M, polys, c->N, batch,
+                                                                      (const long long *)values, out, c->P.t);
+    return cuda_check(c, cudaGetLastError(), "k_encode_output");
+}
+
+int launch_ct_add(he_ctx *c, const u64 *a, const u64 *b, long long n_polys, u64 *out, cudaStream_t st) {
+    const long long total = n_polys * c->L * c->N;
+    if (!total) return HE_OK;
+    k_ct_add<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, b, total, c->N, c->L, out, c->d_mods);
+    return cuda_check(c, cudaGetLastError(), "k_ct_add");
 }
 
 int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, cudaStream_t st) {

@@ -26,10 +26,11 @@ ENC = {"conv": nv.HE_ENC_CONVENTIONAL, "corr": nv.HE_ENC_CORRELATED}
 class Context:
     """A he_ctx for one ring."""
 
-    def __init__(self, spec: RingSpec, device: int = 0, max_ccmul_group: int = 64):
+    def __init__(self, spec: RingSpec, device: int = 0, max_ccmul_group: int = 64, max_ccmul_scratch_bytes: float = 0):
         self.spec = spec
         self.params = nv.make_params(spec.N, prime_bits=spec.prime_bits, t=spec.t, base_log2=spec.base_log2,
-                                     eta=spec.eta, max_ccmul_group=max_ccmul_group, device=device)
+                                     eta=spec.eta, max_ccmul_group=max_ccmul_group, device=device,
+                                     max_ccmul_scratch_bytes=max_ccmul_scratch_bytes)
         self.h = nv.he_setup(self.params)
         self.info = nv.he_ctx_query(self.h)
         self.N, self.L, self.t = spec.N, spec.L, spec.t
@@ -110,26 +111,41 @@ class LayerBuffers:
 class PLayer:
     """One CryptoTrain-P linear layer over a batch of B images."""
 
-    def __init__(self, ctx: Context, keys: Keys, plan: Plan, batch: int):
+    def __init__(self, ctx: Context, keys: Keys, plan: Plan, batch: int, with_bias: bool = False):
+        """with_bias: the layer adds a per-output-channel bias (a batch-norm
+        beta): its per-image plaintexts sit on the product positions
+        (he_encode_output), are encrypted on the weights' stream after the
+        kernel polynomials and are added to [r^x r^w] offline."""
         self.ctx, self.keys, self.plan, self.B = ctx, keys, plan, batch
         c, s = ctx, plan.shape
         nx, nw, no = batch * plan.T * plan.G, plan.MG * plan.G, batch * plan.MG * plan.T
         self.nx, self.nw, self.no = nx, nw, no
+        self.with_bias = with_bias
+        nb = no if with_bias else 0
+        self.wp_all, self.ct_w_all = c.u64(nw + nb, c.N), c.ct(nw + nb)   # kernel rows, then bias rows
         self.buf = LayerBuffers(
-            xp=c.u64(nx, c.N), wp=c.u64(nw, c.N), r_x=c.u64(nx, c.N), r_w=c.u64(nw, c.N),
-            ct_x=c.ct(nx), ct_w=c.ct(nw), ct_rx=c.ct(nx), ct_rw=c.ct(nw), rr=c.ct(no),
+            xp=c.u64(nx, c.N), wp=self.wp_all[:nw], r_x=c.u64(nx, c.N), r_w=c.u64(nw, c.N),
+            ct_x=c.ct(nx), ct_w=self.ct_w_all[:nw], ct_rx=c.ct(nx), ct_rw=c.ct(nw), rr=c.ct(no),
             xm=c.u64(nx, c.N), wm=c.u64(nw, c.N), out=c.ct(no), p=c.u64(no, c.N), dec=c.u64(no, c.N),
             y=torch.empty((batch, s.M, plan.info.Ho, plan.info.Wo), dtype=torch.int64, device=c.device))
 
-    def client_prepare(self, x, w, seeds: ProtocolSeeds):
-        """Client side: encode, draw masks, encrypt x, w and the masks."""
+    def client_prepare(self, x, w, seeds: ProtocolSeeds, bias=None):
+        """Client side: encode, draw masks, encrypt x, w (and the bias) and
+        the masks.  bias: int64 [M] when the layer was built with_bias."""
         c, b = self.ctx, self.buf
         self.plan.encode_input(x, self.B, b.xp)
         self.plan.encode_kernel(w, b.wp)
+        nwb = self.nw
+        if self.with_bias:
+            info = self.plan.info
+            vals = bias.to(device=c.device, dtype=torch.int64).reshape(1, -1, 1, 1).expand(
+                self.B, self.plan.shape.M, info.Ho, info.Wo).contiguous()
+            nv.he_encode_output(c.h, self.plan.h, self.B, vals, self.wp_all[self.nw:])
+            nwb += self.no
         nv.he_sample_masks(c.h, seeds.mask_x, self.nx, b.r_x)
         nv.he_sample_masks(c.h, seeds.mask_w, self.nw, b.r_w)
         nv.he_encrypt_many(c.h, self.keys.h, [(b.xp, self.nx, seeds.enc_x, b.ct_x),
-                                               (b.wp, self.nw, seeds.enc_w, b.ct_w),
+                                               (self.wp_all, nwb, seeds.enc_w, self.ct_w_all),
                                                (b.r_x, self.nx, seeds.enc_rx, b.ct_rx),
                                                (b.r_w, self.nw, seeds.enc_rw, b.ct_rw)])
         nv.he_pt_sub(c.h, b.xp, b.r_x, self.nx * c.N, b.xm)
@@ -139,6 +155,8 @@ class PLayer:
         """Server, preprocessing: [r^x r^w] by CCMul + relinearisation."""
         b = self.buf
         nv.he_ccmul_conv_precompute(self.ctx.h, self.keys.h, self.plan.h, self.B, b.ct_rx, b.ct_rw, b.rr)
+        if self.with_bias:   # CCAdd of the encrypted bias into [r^x r^w]
+            nv.he_ct_add(self.ctx.h, b.rr, self.ct_w_all[self.nw:], self.no, b.rr)
 
     def online(self):
         """Server, online: c = [x](w - r^w) + [w](x - r^x) + [r^x r^w]; p = PPMul."""
@@ -153,11 +171,21 @@ class PLayer:
         nv.he_decode(c.h, self.plan.h, self.B, b.dec, b.p, b.y)
         return b.y
 
-    def step(self, x, w, seeds: ProtocolSeeds):
-        self.client_prepare(x, w, seeds)
+    def step(self, x, w, seeds: ProtocolSeeds, bias=None):
+        self.client_prepare(x, w, seeds, bias)
         self.offline()
         self.online()
         return self.client_finish()
+
+
+def batch_norm_weights(gamma):
+    """The batch-norm scale as a 1x1 convolution: int [C] -> diagonal [C, C, 1, 1]
+    (output channel c sees only input channel c, with weight gamma_c)."""
+    C = gamma.shape[0]
+    w = torch.zeros((C, C, 1, 1), dtype=gamma.dtype, device=gamma.device)
+    idx = torch.arange(C, device=gamma.device)
+    w[idx, idx, 0, 0] = gamma
+    return w
 
 
 class BLayer:

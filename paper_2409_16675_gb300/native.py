@@ -36,7 +36,8 @@ class HEError(RuntimeError):
 class he_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int32), ("prime_bits", ctypes.c_int32 * HE_MAX_LIMBS),
                 ("q", ctypes.c_uint64 * HE_MAX_LIMBS), ("t", ctypes.c_uint64), ("base_log2", ctypes.c_int32),
-                ("eta", ctypes.c_int32), ("max_ccmul_group", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("eta", ctypes.c_int32), ("max_ccmul_group", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("max_ccmul_scratch_bytes", ctypes.c_double)]
 
 
 class he_ctx_info(ctypes.Structure):
@@ -111,6 +112,8 @@ def _load():
         "he_ccmul_conv_precompute": [vp, vp, vp, i32, vp, vp, vp, vp],
         "he_ppmul_conv": [vp, vp, i32, vp, vp, vp, vp],
         "he_decode": [vp, vp, i32, vp, vp, vp, vp],
+        "he_encode_output": [vp, vp, i32, vp, vp, vp],
+        "he_ct_add": [vp, vp, vp, i32, vp, vp],
         "he_batch_create": [i32, pp],
         "he_batch_destroy": [vp],
         "he_batch_last_error": [vp, ctypes.c_char_p, i32],
@@ -168,7 +171,8 @@ def _check(rc, ctx=None):
         raise HEError(rc, last_error(ctx))
 
 
-def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=21, max_ccmul_group=64, device=0):
+def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=21, max_ccmul_group=64, device=0,
+                max_ccmul_scratch_bytes=0.0):
     p = he_params()
     p.N = N
     if q:
@@ -180,6 +184,7 @@ def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=2
         for i, b in enumerate(prime_bits):
             p.prime_bits[i] = b
     p.t, p.base_log2, p.eta, p.max_ccmul_group, p.device = t, base_log2, eta, max_ccmul_group, device
+    p.max_ccmul_scratch_bytes = float(max_ccmul_scratch_bytes)
     return p
 
 
@@ -317,6 +322,14 @@ def he_ppmul_conv(ctx, plan, batch, pt_x, pt_w, out):
 
 def he_decode(ctx, plan, batch, pt, sub, out):
     _check(lib.he_decode(ctx, plan, batch, _ptr(pt), _ptr(sub), _ptr(out), _stream()), ctx)
+
+
+def he_encode_output(ctx, plan, batch, values, polys):
+    _check(lib.he_encode_output(ctx, plan, batch, _ptr(values), _ptr(polys), _stream()), ctx)
+
+
+def he_ct_add(ctx, a, b, n, out):
+    _check(lib.he_ct_add(ctx, _ptr(a), _ptr(b), n, _ptr(out), _stream()), ctx)
 
 
 def he_trace_enable(ctx, on: bool):

@@ -260,6 +260,30 @@ def test_ccmul_bits(name, group):
     k.close()
 
 
+def test_ccmul_in_chunks_gives_the_same_bits():
+    """A CCMul-Precompute whose scratch exceeds the context's budget runs in
+    chunks of outputs; a budget of one output per chunk gives the bits of the
+    single-chunk call (a 3x16x16 -> 6 layer at N = 4096, batch 2)."""
+    c = ctx_for("n4096")
+    small = layer.Context(c.spec, max_ccmul_scratch_bytes=1.0)
+    shape = wl.ConvShape(3, 16, 16, 6, 3, 1)
+    outs = []
+    for ctx in (c, small):
+        keys = layer.Keys(ctx, 12, True)
+        plan = layer.Plan(ctx, shape, "corr")
+        pl = layer.PLayer(ctx, keys, plan, 2)
+        x = torch.from_numpy(wl.activations(13, (2, 3, 16, 16))).cuda()
+        w = torch.from_numpy(wl.weights(14, (6, 3, 3, 3))).cuda()
+        pl.client_prepare(x, w, wl.protocol_seeds(15))
+        pl.offline()
+        outs.append(to_np(pl.buf.rr))
+        assert pl.no > 1
+        keys.close()
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
+    small.close()
+
+
 @pytest.mark.parametrize("name", ["n1024", "n8192", "n2048_t40"])
 def test_ppmul_bits(name):
     c = ctx_for(name)
@@ -374,6 +398,51 @@ def test_layer_b_protocol_bits(name, shape_of, enc):
     assert np.array_equal(ref.y, protocol.conv_reference(x[0], w, s.pad))
     keys.close()
     plan.close()
+
+
+@pytest.mark.parametrize("enc", ["corr", "conv"])
+def test_batch_norm_layer_bits(enc):
+    """The batch-norm linear protocol as a CryptoTrain-P layer: the diagonal
+    1x1 kernel gamma and the bias beta added to [r^x r^gamma] offline.  Bits of
+    the precomputed and online ciphertexts equal the oracle's; every image
+    decodes to gamma_c x_c + beta_c (16 channels of 16x16, batch 2, N = 8192)."""
+    c = ctx_for("n8192")
+    C, H, B = 16, 16, 2
+    shape = wl.ConvShape(C, H, H, C, 1, 0)
+    seeds = wl.protocol_seeds(606)
+    x = wl.activations(607, (B, C, H, H))
+    gamma = torch.from_numpy(wl.weights(608, (C,)).astype(np.int64))
+    beta = torch.from_numpy(wl.rng(609).integers(-1000, 1000, C))
+    w = layer.batch_norm_weights(gamma)
+    keys = layer.Keys(c, seeds.keys, True)
+    plan = layer.Plan(c, shape, enc)
+    pl = layer.PLayer(c, keys, plan, B, with_bias=True)
+    y = to_np(pl.step(cuda(x), w.cuda(), seeds, beta))
+    op = packing.make_plan(enc, c.N, C, H, H, C, 1, 0)
+    ref = protocol.run_layer(oparams(c), op, x, w.numpy(), seeds, bias=beta.numpy())
+    assert np.array_equal(to_np(pl.buf.rr), ref.rr)
+    assert np.array_equal(to_np(pl.buf.out), ref.out)
+    g, bt = gamma.numpy()[:, None, None], beta.numpy()[:, None, None]
+    for b in range(B):
+        assert np.array_equal(y[b], ref.y[b])
+        assert np.array_equal(y[b], g * x[b].astype(np.int64) + bt)
+    keys.close()
+    plan.close()
+
+
+def test_layer_alexnet_shaped_first_layer():
+    """An AlexNet-shaped first layer on a 64x64x3 input with an 11x11 kernel
+    (same padding, 16 of its output channels) at N = 8192: bit-exact against
+    the oracle and decoded to the exact convolution."""
+    c = ctx_for("n8192")
+    shape = wl.ConvShape(3, 64, 64, 16, 11, 5)
+    c2, pl, y, ref, x, w, hs = run_layer_both("n8192", shape, "corr", 1, 4711)
+    assert pl.plan.T * pl.plan.G * pl.plan.MG == 48
+    assert np.array_equal(to_np(pl.buf.rr), ref.rr)
+    assert np.array_equal(to_np(pl.buf.out), ref.out)
+    assert np.array_equal(to_np(y)[0], protocol.conv_reference(x[0], w, 5))
+    for h in hs:
+        h.close()
 
 
 def test_layer_batched_ragged_tiles():

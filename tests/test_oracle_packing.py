@@ -219,3 +219,26 @@ def test_protocol_b_decodes_to_conv(enc, pad):
     dec = he.decrypt(P, run.keys, run.out)
     xw = he.ppmul_terms(P, run.x_polys, run.w_polys, packing.product_terms(plan))
     assert np.array_equal(dec, xw)
+
+
+@pytest.mark.parametrize("enc", ["corr", "conv"])
+def test_protocol_with_bias_and_batch_norm(enc):
+    """A bias (batch-norm beta) placed by encode_output on the product
+    positions and added to [r^x r^w] shifts every decoded output of channel m
+    by beta_m; with a diagonal 1x1 kernel gamma the layer is the batch-norm
+    affine map y_c = gamma_c x_c + beta_c."""
+    spec = wl.RingSpec(1024, (40, 40, 40), 65537)
+    P = he.Params.from_spec(spec)
+    C = 4
+    gamma = np.array([3, -2, 5, 1])
+    beta = np.array([100, -7, 0, 2024])
+    w = np.zeros((C, C, 1, 1), dtype=np.int64)
+    w[np.arange(C), np.arange(C), 0, 0] = gamma
+    plan = packing.make_plan(enc, P.N, C, 6, 5, C, 1, 0)
+    x = wl.activations(9, (2, C, 6, 5))
+    run = protocol.run_layer(P, plan, x, w, wl.protocol_seeds(17), bias=beta)
+    for b in range(2):
+        assert np.array_equal(run.y[b], gamma[:, None, None] * x[b].astype(np.int64) + beta[:, None, None])
+    # encode_output is the exact inverse of decode on the output positions
+    vals = np.arange(C * 6 * 5).reshape(C, 6, 5) - 50
+    assert np.array_equal(packing.decode(plan, packing.encode_output(plan, vals, P.t), P.t), vals)
