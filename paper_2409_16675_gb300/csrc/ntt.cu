@@ -22,6 +22,7 @@
 // is exactly what the last forward pass and the first inverse pass hold in
 // registers, so both the forward store and the multiply-accumulate loads are
 // coalesced.  This order never leaves the library.
+#include <atomic>
 #include <cstring>
 
 #include "arith.cuh"
@@ -456,6 +457,19 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, MINB) k_mac_items(const ItemSeg 
     mac_item<LOGN, MINB, LAZY>(item_at<MacItem>(segs, nseg, (int)blockIdx.x), sm, threadIdx.x);
 }
 
+// True the first time a call site runs on the current device: kernel
+// attributes (the dynamic shared-memory limit) are per device, and several
+// threads may launch (the request server's worker); setting them twice is
+// harmless.
+static bool first_on_device(std::atomic<unsigned long long> &mask) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (mask.load(std::memory_order_acquire) & bit) return false;
+    mask.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
+
 // true when every modulus of the launch is below 2^57 (no in-transform corrections)
 static bool lazy_ok(const he_ctx *c, int mod_base, int n_limbs) {
     for (int i = 0; i < n_limbs; i++)
@@ -468,11 +482,10 @@ bool ctx_lazy(const he_ctx *c) { return lazy_ok(c, 0, c->L); }
 template <int LOGN>
 static int fwd_t(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (first_on_device(attr_mask)) {
         cudaFuncSetAttribute(k_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
     }
     FwdJobs JS;
     memset(&JS, 0, sizeof JS);
@@ -503,11 +516,10 @@ static int fwd_t(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
 template <int LOGN>
 static int mac_t(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (first_on_device(attr_mask)) {
         cudaFuncSetAttribute(k_mac_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_mac_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
     }
     MacJobs JS;
     memset(&JS, 0, sizeof JS);
@@ -553,13 +565,12 @@ int launch_fwd(he_ctx *c, const FwdJob &j, cudaStream_t st) { return launch_fwd_
 template <int LOGN, int MINB, bool LAZY>
 static int queue_l(bool fwd, const ItemSeg *segs, int nseg, int total, int *counter, int grid, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (first_on_device(attr_mask)) {
         cudaFuncSetAttribute(k_fwd_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_mac_queue<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_fwd_items<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_mac_items<LOGN, MINB, LAZY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
     }
     if (grid <= 0) {  // one CTA per item
         if (fwd) k_fwd_items<LOGN, MINB, LAZY><<<total, Cfg<LOGN>::T, smem, st>>>(segs, nseg);
