@@ -621,11 +621,10 @@ def run_alexnet(args):
     CryptoTrain-P layers, whole steps (encode, masks, encryptions, offline
     CCMul-Precompute, online, PPMul, decryption, decoding): the first
     convolution 3 -> 64 with an 11x11 kernel (same padding, stride 1) and a
-    batch norm over its 64 channels (diagonal 1x1 kernel and bias; the
-    generic plan spends a product on every (output channel, channel group)
-    pair, so a dense-diagonal batch norm costs 2048 products per image here).
-    Ring N = 8192 with 4 x 50-bit limbs and a 40-bit t (no wrap of the sums);
-    batch at most 16.""" 
+    batch norm over its 64 channels (diagonal 1x1 kernel and bias, under the
+    depthwise plan: one product per kernel polynomial and tile).  Ring
+    N = 8192 with 4 x 50-bit limbs and a 40-bit t (no wrap of the sums);
+    batch at most 16."""
     import torch
 
     from paper_2409_16675_gb300 import layer, workloads as wl
@@ -637,8 +636,8 @@ def run_alexnet(args):
     specs = [("conv1_3x64x64_64_k11", wl.ConvShape(3, 64, 64, 64, 11, 5), False),
              ("bn1_64x64x64", wl.ConvShape(64, 64, 64, 64, 1, 0), True)]
     for name, shape, bn in specs:
-        cands = [layer.Plan(ctx, shape, e) for e in ("corr", "conv")]
-        plan = min(cands, key=lambda p: p.MG * p.G * p.T)
+        cands = [layer.Plan(ctx, shape, e, depthwise=bn) for e in ("corr", "conv")]
+        plan = min(cands, key=lambda p: p.products)
         pl = layer.PLayer(ctx, keys, plan, B, with_bias=bn)
         x = torch.from_numpy(wl.activations(5, (B, shape.C, shape.H, shape.W))).cuda()
         if bn:
@@ -659,7 +658,7 @@ def run_alexnet(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms_per_step": ms, "images_per_s": B / (ms / 1000.0), "encoding": plan.encoding,
-                     "products_per_image": plan.MG * plan.G * plan.T}
+                     "depthwise": plan.depthwise, "products_per_image": plan.products}
         for p in cands:
             p.close()
     print(json.dumps({"metric": "AlexNet-shaped CryptoTrain-P layers, images/s (batch %d)" % B, "unit": "images/s",

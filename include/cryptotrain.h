@@ -54,6 +54,13 @@ extern "C" {
 /* encodings (Section 3.3) */
 #define HE_ENC_CONVENTIONAL 0 /* row-major packing of the zero-padded input (left half of Fig. 7) */
 #define HE_ENC_CORRELATED 1   /* Eq. 1 and Eq. 2: x^[iO+j] = x[i,j], w^[(h-i-1)O+(h-j-1)] = w[i,j] */
+/* OR-ed into the encoding of he_conv_plan / he_plan_search: a depthwise layer
+ * (M = C, output channel m reads input channel m only: weights diagonal in
+ * the channel indices, e.g. the gamma of a batch norm).  The plan keeps the
+ * output channels of a kernel polynomial in one channel group and every
+ * product call skips the (kernel polynomial, channel group) pairs whose
+ * weights are all zero: MG * T products per image instead of MG * G * T. */
+#define HE_PLAN_DEPTHWISE 16
 
 /* roles of a tensor in an encoding */
 #define HE_ROLE_INPUT 0  /* activations x [batch][C][H][W] */
@@ -131,6 +138,7 @@ typedef struct he_plan_info {
     int32_t Ho, Wo;
     int32_t Mn, Sout;   /* output channels per kernel polynomial and their stride */
     int32_t MG;         /* kernel polynomials per channel group: ceil(M / Mn) */
+    int32_t depthwise;  /* 1: only pair (mg, g = mg * Mn / Cn) is multiplied */
 } he_plan_info;
 
 typedef struct he_ctx he_ctx;

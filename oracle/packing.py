@@ -71,6 +71,7 @@ class Plan:
     Mn: int = 1
     Sout: int = 0
     tiles: list = field(default_factory=list)   # (a0, a1, b0, b1, r0, r1, s0, s1) per tile
+    depthwise: bool = False   # output channel m reads input channel m only
 
     @property
     def T(self):
@@ -90,13 +91,29 @@ class Plan:
 
     def key(self):
         return (self.encoding, self.N, self.C, self.H, self.W, self.M, self.h, self.pad, self.Cn, self.G,
-                self.th, self.tw, self.Th, self.Tw, self.Hn, self.Wn, self.Ooff, self.O, self.S, self.Mn, self.Sout)
+                self.th, self.tw, self.Th, self.Tw, self.Hn, self.Wn, self.Ooff, self.O, self.S, self.Mn, self.Sout,
+                self.depthwise)
+
+    def pair_used(self, mg, g):
+        """Whether kernel polynomial mg meets channel group g in a product:
+        always, except in a depthwise plan, where the Mn outputs of mg (all in
+        one channel group: Mn divides Cn, or there is one group) meet only
+        that group."""
+        return (not self.depthwise) or g == (mg * self.Mn) // self.Cn
+
+    @property
+    def products(self):
+        """Polynomial products per image."""
+        return self.MG * self.T * (1 if self.depthwise else self.G)
 
 
-def _out_packing(M, N, ranges):
+def _out_packing(M, N, ranges, depthwise_cn=0):
     """(M_n, S_out) for product spans given as (r_lo, r_hi, D) per tile: r_lo, r_hi
     the lowest and highest requested coefficient of one kernel's product,
-    D its highest possible degree (before any wrap)."""
+    D its highest possible degree (before any wrap).  For a depthwise layer
+    with several channel groups (depthwise_cn = C_n) M_n is the largest
+    fitting divisor of C_n, so that a kernel polynomial's outputs lie in one
+    channel group (with a single group any M_n does)."""
     Sout = max(max(rhi, D - rlo) for (rlo, rhi, D) in ranges) + 1
     def fits(k):
         for (rlo, rhi, D) in ranges:
@@ -109,6 +126,10 @@ def _out_packing(M, N, ranges):
     k = 1
     while k < M and fits(k + 1):
         k += 1
+    if depthwise_cn:
+        while depthwise_cn % k:
+            k -= 1
+        return k, Sout
     G = -(-M // k)
     return -(-M // G), Sout
 
@@ -128,7 +149,7 @@ def _conv_ranges(Cn, Hn, Wn, h, th_list):
     return [(O, O + (a - 1) * Wn + (b - 1), D) for (a, b) in th_list]
 
 
-def plan_conventional(N, C, H, W, M, h, pad) -> Plan:
+def plan_conventional(N, C, H, W, M, h, pad, depthwise=False) -> Plan:
     _check_shape(C, H, W, M, h, pad)
     Hp, Wp = H + 2 * pad, W + 2 * pad
     Ho, Wo = Hp - h + 1, Wp - h + 1
@@ -144,16 +165,16 @@ def plan_conventional(N, C, H, W, M, h, pad) -> Plan:
             th, tw = Hn - h + 1, Wn - h + 1
             Th, Tw = -(-Ho // th), -(-Wo // tw)
             sizes = {(min(th, Ho - i * th), min(tw, Wo - j * tw)) for i in range(Th) for j in range(Tw)}
-            Mn, Sout = _out_packing(M, N, _conv_ranges(Cn, Hn, Wn, h, sizes))
+            Mn, Sout = _out_packing(M, N, _conv_ranges(Cn, Hn, Wn, h, sizes), Cn if depthwise and G > 1 else 0)
             MG = -(-M // Mn)
-            key = (MG * G * Th * Tw, G * Th * Tw, G, -Hn, -Wn)
+            key = (MG * (1 if depthwise else G) * Th * Tw, G * Th * Tw, G, -Hn, -Wn)
             if best is None or key < best[0]:
                 best = (key, (Cn, G, Hn, Wn, th, tw, Th, Tw, Mn, Sout))
     if best is None:
         raise ValueError("plan does not fit")
     Cn, G, Hn, Wn, th, tw, Th, Tw, Mn, Sout = best[1]
     p = Plan("conv", N, C, H, W, M, h, pad, Cn, G, th, tw, Th, Tw, Hn=Hn, Wn=Wn,
-             Ooff=(Cn - 1) * Hn * Wn + (h - 1) * Wn + h - 1, Mn=Mn, Sout=Sout)
+             Ooff=(Cn - 1) * Hn * Wn + (h - 1) * Wn + h - 1, Mn=Mn, Sout=Sout, depthwise=depthwise)
     for ti in range(Th):
         for tj in range(Tw):
             a0, b0 = ti * th, tj * tw
@@ -199,7 +220,7 @@ def _corr_fits(c, S, geo, N):
     return True
 
 
-def plan_correlated(N, C, H, W, M, h, pad) -> Plan:
+def plan_correlated(N, C, H, W, M, h, pad, depthwise=False) -> Plan:
     _check_shape(C, H, W, M, h, pad)
     Ho, Wo = H + 2 * pad - h + 1, W + 2 * pad - h + 1
     best = None
@@ -216,23 +237,28 @@ def plan_correlated(N, C, H, W, M, h, pad) -> Plan:
             Cn = -(-C // G)
             T = len(tiles)
             ranges = [((Cn - 1) * S + rlo, (Cn - 1) * S + rhi, 2 * (Cn - 1) * S + D1) for (rlo, rhi, D1) in geo]
-            Mn, Sout = _out_packing(M, N, ranges)
+            Mn, Sout = _out_packing(M, N, ranges, Cn if depthwise and G > 1 else 0)
             MG = -(-M // Mn)
-            key = (MG * G * T, G * T, G, -th, -tw)
+            key = (MG * (1 if depthwise else G) * T, G * T, G, -th, -tw)
             if best is None or key < best[0]:
                 best = (key, (Cn, G, th, tw, O, S, tiles, Mn, Sout))
     if best is None:
         raise ValueError("plan does not fit")
     Cn, G, th, tw, O, S, tiles, Mn, Sout = best[1]
     return Plan("corr", N, C, H, W, M, h, pad, Cn, G, th, tw, -(-Ho // th), -(-Wo // tw), O=O, S=S, Mn=Mn,
-                Sout=Sout, tiles=tiles)
+                Sout=Sout, tiles=tiles, depthwise=depthwise)
 
 
-def make_plan(encoding, N, C, H, W, M, h, pad) -> Plan:
+def make_plan(encoding, N, C, H, W, M, h, pad, depthwise=False) -> Plan:
+    """depthwise: output channel m reads input channel m only (M = C; the
+    weights are diagonal in the channel indices, as the gamma of a batch
+    norm): the search minimises MG * T, the products actually needed."""
+    if depthwise and M != C:
+        raise ValueError("a depthwise layer has M = C")
     if encoding == "conv":
-        return plan_conventional(N, C, H, W, M, h, pad)
+        return plan_conventional(N, C, H, W, M, h, pad, depthwise)
     if encoding == "corr":
-        return plan_correlated(N, C, H, W, M, h, pad)
+        return plan_correlated(N, C, H, W, M, h, pad, depthwise)
     raise ValueError(encoding)
 
 
@@ -347,5 +373,5 @@ def product_terms(p: Plan):
     terms = []
     for mg in range(p.MG):
         for t in range(p.T):
-            terms.append([(t * p.G + g, mg * p.G + g) for g in range(p.G)])
+            terms.append([(t * p.G + g, mg * p.G + g) for g in range(p.G) if p.pair_used(mg, g)])
     return terms

@@ -37,15 +37,22 @@ class LayerRun:
 
 
 def precompute_pairs(plan, batch=1):
-    """CCMul pairs (rx index, rw index), G consecutive pairs per output
-    (b, m, t) in that order; rx index (b*T + t)*G + g, rw index m*G + g."""
+    """CCMul pairs (rx index, rw index), consecutive per output (b, m, t) in
+    that order (G per output; one in a depthwise plan); rx index
+    (b*T + t)*G + g, rw index m*G + g."""
     pairs = []
     for b in range(batch):
         for m in range(plan.MG):
             for t in range(plan.T):
                 for g in range(plan.G):
-                    pairs.append(((b * plan.T + t) * plan.G + g, m * plan.G + g))
+                    if plan.pair_used(m, g):
+                        pairs.append(((b * plan.T + t) * plan.G + g, m * plan.G + g))
     return pairs
+
+
+def ccmul_group(plan):
+    """Pairs summed into one CCMul output."""
+    return 1 if plan.depthwise else plan.G
 
 
 def online_terms(plan, batch=1):
@@ -58,6 +65,8 @@ def online_terms(plan, batch=1):
             for t in range(plan.T):
                 tl = []
                 for g in range(plan.G):
+                    if not plan.pair_used(m, g):
+                        continue
                     xi = (b * plan.T + t) * plan.G + g
                     tl.append((xi, m * plan.G + g))
                     tl.append((batch * TG + m * plan.G + g, MG + xi))
@@ -70,7 +79,8 @@ def ppmul_terms(plan, batch=1):
     for b in range(batch):
         for m in range(plan.MG):
             for t in range(plan.T):
-                terms.append([((b * plan.T + t) * plan.G + g, m * plan.G + g) for g in range(plan.G)])
+                terms.append([((b * plan.T + t) * plan.G + g, m * plan.G + g) for g in range(plan.G)
+                              if plan.pair_used(m, g)])
     return terms
 
 
@@ -103,7 +113,7 @@ def run_layer(P: he.Params, plan, x, w, seeds, keys=None, first_image: int = 0, 
     ct_rx = he.encrypt(P, keys, r_x, seeds.enc_rx, first)
     ct_rw = he.encrypt(P, keys, r_w, seeds.enc_rw)
     # offline: [r^x r^w] summed over channel groups
-    rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan, B), plan.G)
+    rr = he.ccmul(P, keys, ct_rx, ct_rw, precompute_pairs(plan, B), ccmul_group(plan))
     if bias is not None:
         nw = plan.MG * plan.G
         bv = np.broadcast_to(np.asarray(bias, dtype=np.int64)[:, None, None], (plan.M, plan.Ho, plan.Wo))
@@ -161,7 +171,7 @@ def run_layer_b(P: he.Params, plan, x, w, seeds, keys=None) -> LayerRunB:
     wp = packing.encode_kernel(plan, w, t).reshape(-1, P.N)
     ct_x = he.encrypt(P, keys, xp, seeds.enc_x)
     ct_w = he.encrypt(P, keys, wp, seeds.enc_w)
-    out = he.ccmul(P, keys, ct_x, ct_w, precompute_pairs(plan, B), plan.G)
+    out = he.ccmul(P, keys, ct_x, ct_w, precompute_pairs(plan, B), ccmul_group(plan))
     dec = he.decrypt(P, keys, out).reshape(B, plan.MG, plan.T, P.N)
     y = np.stack([packing.decode(plan, dec[b], t) for b in range(B)])
     if B == 1:

@@ -54,6 +54,7 @@ void job_items(const JobDesc &J, char *dev, std::vector<int32_t> &terms, std::ve
                 for (int comp = 0; comp < 2; comp++) {
                     t0.push_back((int)ta.size());
                     for (int g = 0; g < G; g++) {
+                        if (!plan_pair(J.p, m, g)) continue;
                         const long long xi = (long long)(bb * T + t) * G + g;
                         if (J.ct_x) {
                             ta.push_back((int32_t)((xi * 2 + comp) * L));

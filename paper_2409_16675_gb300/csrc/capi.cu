@@ -560,6 +560,7 @@ int he_cpmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x, 
             for (int t = 0; t < T; t++)
                 for (int comp = 0; comp < 2; comp++) {
                     for (int g = 0; g < G; g++) {
+                        if (!plan_pair(p, m, g)) continue;
                         if (ct_x) Tm.add((int)((((long long)(b * T + t) * G + g) * 2 + comp) * L), (m * G + g) * L);
                         if (ct_w) Tm.add((int)((nX + (long long)(m * G + g) * 2 + comp) * L),
                                          (int)((nWp + (long long)(b * T + t) * G + g) * L));
@@ -672,9 +673,11 @@ int he_ccmul_conv_precompute(he_ctx *c, const he_keys *k, const he_plan *p, int 
     for (int b = 0; b < batch; b++)
         for (int m = 0; m < M; m++)
             for (int t = 0; t < T; t++)
-                for (int g = 0; g < G; g++) { pa.push_back((b * T + t) * G + g); pb.push_back(m * G + g); }
-    return he_ccmul_precompute(c, k, ct_rx, batch * T * G, ct_rw, M * G, pa.data(), pb.data(), (int)pa.size(), G,
-                               ct_out, st);
+                for (int g = 0; g < G; g++)
+                    if (plan_pair(p, m, g)) { pa.push_back((b * T + t) * G + g); pb.push_back(m * G + g); }
+    // pairs per output: G, or one in a depthwise plan
+    return he_ccmul_precompute(c, k, ct_rx, batch * T * G, ct_rw, M * G, pa.data(), pb.data(), (int)pa.size(),
+                               p->info.depthwise ? 1 : G, ct_out, st);
 }
 
 // ------------------------------------------------------------------ PPMul / decode
@@ -702,7 +705,8 @@ int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, 
     for (int b = 0; b < batch; b++)
         for (int m = 0; m < M; m++)
             for (int t = 0; t < T; t++) {
-                for (int g = 0; g < G; g++) Tm.add((b * T + t) * G + g, m * G + g);
+                for (int g = 0; g < G; g++)
+                    if (plan_pair(p, m, g)) Tm.add((b * T + t) * G + g, m * G + g);
                 Tm.close();
             }
     MacJob mj = mac_job();

@@ -126,6 +126,13 @@ struct he_plan {
     // host copies for tests of the plan
     std::vector<int32_t> h_in_map, h_ker_map, h_out_map;
 };
+// Whether product pair (kernel polynomial group mg, channel group g) of a plan
+// is multiplied: always, except in a depthwise plan, where only the channel
+// group holding the Mn outputs of mg is.
+inline bool plan_pair(const he_plan *p, int mg, int g) {
+    return !p->info.depthwise || g == (mg * p->info.Mn) / p->info.Cn;
+}
+
 
 namespace he {
 

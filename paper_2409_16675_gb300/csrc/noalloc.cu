@@ -54,6 +54,7 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
             for (int t = 0; t < T; t++)
                 for (int comp = 0; comp < 2; comp++) {
                     for (int g = 0; g < G; g++) {
+                        if (!plan_pair(p, m, g)) continue;
                         if (ct_x) {
                             ta.push_back((int32_t)((((long long)(b * T + t) * G + g) * 2 + comp) * L));
                             tb.push_back((m * G + g) * L);

@@ -35,8 +35,12 @@ namespace he {
 struct Tile { int a0, a1, b0, b1, r0, r1, s0, s1; };
 struct Span { long long rlo, rhi, D; };  // requested range and highest degree of one product
 
-// (Mn, Sout) for the given product spans
-static void out_packing(int M, long long N, const std::vector<Span> &sp, int &Mn, long long &Sout) {
+// (Mn, Sout) for the given product spans.  Depthwise layers (output channel m
+// reads input channel m only) with several channel groups keep Mn a divisor
+// of Cn, so the Mn outputs of a kernel polynomial lie in one channel group and
+// every output takes exactly one (kernel polynomial, channel group) product
+// (with one group that holds for any Mn).
+static void out_packing(int M, long long N, const std::vector<Span> &sp, int &Mn, long long &Sout, int depthwise_cn) {
     Sout = 0;
     for (const Span &e : sp) Sout = std::max(Sout, std::max(e.rhi, e.D - e.rlo));
     Sout += 1;
@@ -50,11 +54,22 @@ static void out_packing(int M, long long N, const std::vector<Span> &sp, int &Mn
     };
     int k = 1;
     while (k < M && fits(k + 1)) k++;
+    if (depthwise_cn > 0) {
+        while (depthwise_cn % k) k--;
+        Mn = k;
+        return;
+    }
     const int G = (M + k - 1) / k;
     Mn = (M + G - 1) / G;
 }
 
-static bool conv_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
+// products per image: every (kernel polynomial, channel group) pair, or one
+// per kernel polynomial for a depthwise layer
+static long long plan_products(bool depthwise, long long MG, long long G, long long T) {
+    return depthwise ? MG * T : MG * G * T;
+}
+
+static bool conv_search(int N, const he_conv_shape &s, bool dw, he_plan_info &I, std::vector<Tile> &tiles) {
     const int Hp = s.H + 2 * s.pad, Wp = s.W + 2 * s.pad;
     const int Ho = Hp - s.h + 1, Wo = Wp - s.h + 1;
     long long best[5] = {LLONG_MAX, 0, 0, 0, 0};
@@ -77,9 +92,9 @@ static bool conv_search(int N, const he_conv_shape &s, he_plan_info &I, std::vec
                 }
             int Mn;
             long long Sout;
-            out_packing(s.M, N, sp, Mn, Sout);
+            out_packing(s.M, N, sp, Mn, Sout, dw && G > 1 ? Cn : 0);
             const long long MG = (s.M + Mn - 1) / Mn;
-            long long key[5] = {MG * G * Th * Tw, (long long)G * Th * Tw, G, -Hn, -Wn};
+            long long key[5] = {plan_products(dw, MG, G, (long long)Th * Tw), (long long)G * Th * Tw, G, -Hn, -Wn};
             if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
                 std::copy(key, key + 5, best);
                 found = true;
@@ -139,7 +154,7 @@ static bool corr_fits(long long c, long long S, const std::vector<Geo> &g, long 
     return true;
 }
 
-static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vector<Tile> &tiles) {
+static bool corr_search(int N, const he_conv_shape &s, bool dw, he_plan_info &I, std::vector<Tile> &tiles) {
     const int Ho = s.H + 2 * s.pad - s.h + 1, Wo = s.W + 2 * s.pad - s.h + 1;
     long long best[5] = {LLONG_MAX, 0, 0, 0, 0};
     bool found = false;
@@ -160,9 +175,10 @@ static bool corr_search(int N, const he_conv_shape &s, he_plan_info &I, std::vec
                 sp.push_back({(Cn - 1) * S + e.rlo, (Cn - 1) * S + e.rhi, 2 * (long long)(Cn - 1) * S + e.D1});
             int Mn;
             long long Sout;
-            out_packing(s.M, N, sp, Mn, Sout);
+            out_packing(s.M, N, sp, Mn, Sout, dw && G > 1 ? Cn : 0);
             const long long MG = (s.M + Mn - 1) / Mn;
-            long long key[5] = {MG * G * (long long)tl.size(), (long long)G * (long long)tl.size(), G, -th, -tw};
+            long long key[5] = {plan_products(dw, MG, G, (long long)tl.size()), (long long)G * (long long)tl.size(), G,
+                                -th, -tw};
             if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
                 std::copy(key, key + 5, best);
                 found = true;
@@ -185,13 +201,17 @@ static int search_plan(int N, const he_conv_shape &s, int encoding, he_plan_info
         err = "bad convolution shape";
         return HE_ERR_INVALID_ARG;
     }
+    const bool dw = (encoding & HE_PLAN_DEPTHWISE) != 0;
+    encoding &= ~HE_PLAN_DEPTHWISE;
     if (encoding != HE_ENC_CONVENTIONAL && encoding != HE_ENC_CORRELATED) { err = "bad encoding"; return HE_ERR_INVALID_ARG; }
+    if (dw && s.M != s.C) { err = "a depthwise layer has as many output channels as input channels"; return HE_ERR_INVALID_ARG; }
     if (N < 2 || (N & (N - 1))) { err = "N must be a power of two"; return HE_ERR_INVALID_ARG; }
     memset(&I, 0, sizeof I);
     I.encoding = encoding;
+    I.depthwise = dw ? 1 : 0;
     I.Ho = s.H + 2 * s.pad - s.h + 1;
     I.Wo = s.W + 2 * s.pad - s.h + 1;
-    const bool ok = encoding == HE_ENC_CONVENTIONAL ? conv_search(N, s, I, tiles) : corr_search(N, s, I, tiles);
+    const bool ok = encoding == HE_ENC_CONVENTIONAL ? conv_search(N, s, dw, I, tiles) : corr_search(N, s, dw, I, tiles);
     if (!ok) { err = "no partition window fits the ring"; return HE_ERR_PLAN_DOES_NOT_FIT; }
     I.MG = (s.M + I.Mn - 1) / I.Mn;
     return HE_OK;
@@ -203,6 +223,7 @@ int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std:
     std::vector<Tile> tiles;
     const int rc = search_plan(N, s, encoding, I, tiles, err);
     if (rc) return rc;
+    encoding = I.encoding;  // without the depthwise flag
     p->s = s;
     p->info = I;
     p->N = N;

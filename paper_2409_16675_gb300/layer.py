@@ -69,11 +69,19 @@ class Keys:
 
 
 class Plan:
-    def __init__(self, ctx: Context, shape: ConvShape, encoding: str):
-        self.ctx, self.shape, self.encoding = ctx, shape, encoding
-        self.h = nv.he_conv_plan(ctx.h, shape.C, shape.H, shape.W, shape.M, shape.h, shape.pad, ENC[encoding])
+    def __init__(self, ctx: Context, shape: ConvShape, encoding: str, depthwise: bool = False):
+        """depthwise: output channel m reads input channel m only (M = C, weights
+        diagonal in the channel indices); only the needed products run."""
+        self.ctx, self.shape, self.encoding, self.depthwise = ctx, shape, encoding, depthwise
+        enc = ENC[encoding] | (nv.HE_PLAN_DEPTHWISE if depthwise else 0)
+        self.h = nv.he_conv_plan(ctx.h, shape.C, shape.H, shape.W, shape.M, shape.h, shape.pad, enc)
         self.info = nv.he_plan_query(self.h)
         self.T, self.G, self.MG = self.info.T, self.info.G, self.info.MG
+
+    @property
+    def products(self):
+        """Polynomial products per image."""
+        return self.MG * self.T * (1 if self.depthwise else self.G)
 
     def encode_input(self, x, batch, out):
         f = nv.he_encode_conventional if self.encoding == "conv" else nv.he_encode_correlated

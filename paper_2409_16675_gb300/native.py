@@ -23,6 +23,7 @@ HE_MAX_LIMBS = 16
 HE_ENC_CONVENTIONAL, HE_ENC_CORRELATED = 0, 1
 HE_ROLE_INPUT, HE_ROLE_KERNEL = 0, 1
 HE_DTYPE_U8, HE_DTYPE_I8, HE_DTYPE_I64 = 0, 1, 2
+HE_PLAN_DEPTHWISE = 16
 HE_KEY_SK, HE_KEY_PK, HE_KEY_RLK = 0, 1, 2
 HE_BATCH_PLAIN, HE_BATCH_PERSISTENT, HE_BATCH_GRAPH = 0, 1, 2
 
@@ -74,7 +75,7 @@ class he_server_report(ctypes.Structure):
 
 class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("encoding", "Cn", "G", "th", "tw", "Th", "Tw", "T", "Hn", "Wn",
-                                              "Ooff", "O", "S", "Ho", "Wo", "Mn", "Sout", "MG")]
+                                              "Ooff", "O", "S", "Ho", "Wo", "Mn", "Sout", "MG", "depthwise")]
 
 
 def _load():

@@ -400,12 +400,13 @@ def test_layer_b_protocol_bits(name, shape_of, enc):
     plan.close()
 
 
-@pytest.mark.parametrize("enc", ["corr", "conv"])
-def test_batch_norm_layer_bits(enc):
+@pytest.mark.parametrize("enc,depthwise", [("corr", False), ("conv", False), ("corr", True), ("conv", True)])
+def test_batch_norm_layer_bits(enc, depthwise):
     """The batch-norm linear protocol as a CryptoTrain-P layer: the diagonal
-    1x1 kernel gamma and the bias beta added to [r^x r^gamma] offline.  Bits of
-    the precomputed and online ciphertexts equal the oracle's; every image
-    decodes to gamma_c x_c + beta_c (16 channels of 16x16, batch 2, N = 8192)."""
+    1x1 kernel gamma and the bias beta added to [r^x r^gamma] offline, under
+    the dense and the depthwise plan.  Bits of the precomputed and online
+    ciphertexts equal the oracle's; every image decodes to gamma_c x_c + beta_c
+    (16 channels of 16x16, batch 2, N = 8192)."""
     c = ctx_for("n8192")
     C, H, B = 16, 16, 2
     shape = wl.ConvShape(C, H, H, C, 1, 0)
@@ -415,10 +416,11 @@ def test_batch_norm_layer_bits(enc):
     beta = torch.from_numpy(wl.rng(609).integers(-1000, 1000, C))
     w = layer.batch_norm_weights(gamma)
     keys = layer.Keys(c, seeds.keys, True)
-    plan = layer.Plan(c, shape, enc)
+    plan = layer.Plan(c, shape, enc, depthwise=depthwise)
     pl = layer.PLayer(c, keys, plan, B, with_bias=True)
     y = to_np(pl.step(cuda(x), w.cuda(), seeds, beta))
-    op = packing.make_plan(enc, c.N, C, H, H, C, 1, 0)
+    op = packing.make_plan(enc, c.N, C, H, H, C, 1, 0, depthwise=depthwise)
+    assert plan.products == op.products
     ref = protocol.run_layer(oparams(c), op, x, w.numpy(), seeds, bias=beta.numpy())
     assert np.array_equal(to_np(pl.buf.rr), ref.rr)
     assert np.array_equal(to_np(pl.buf.out), ref.out)
@@ -426,6 +428,32 @@ def test_batch_norm_layer_bits(enc):
     for b in range(B):
         assert np.array_equal(y[b], ref.y[b])
         assert np.array_equal(y[b], g * x[b].astype(np.int64) + bt)
+    keys.close()
+    plan.close()
+
+
+def test_depthwise_convolution_bits():
+    """A depthwise 3x3 convolution (each channel with its own kernel) under the
+    depthwise plan at N = 4096: bit-exact against the oracle, decoded to the
+    per-channel convolution."""
+    c = ctx_for("n4096")
+    C, H = 12, 20
+    shape = wl.ConvShape(C, H, H, C, 3, 1)
+    seeds = wl.protocol_seeds(707)
+    x = wl.activations(708, (1, C, H, H))
+    kern = wl.weights(709, (C, 3, 3)).astype(np.int64)
+    w = np.zeros((C, C, 3, 3), dtype=np.int64)
+    for ch in range(C):
+        w[ch, ch] = kern[ch]
+    keys = layer.Keys(c, seeds.keys, True)
+    plan = layer.Plan(c, shape, "corr", depthwise=True)
+    pl = layer.PLayer(c, keys, plan, 1)
+    y = to_np(pl.step(cuda(x), cuda(w), seeds))
+    op = packing.make_plan("corr", c.N, C, H, H, C, 3, 1, depthwise=True)
+    ref = protocol.run_layer(oparams(c), op, x, w, seeds)
+    assert np.array_equal(to_np(pl.buf.rr), ref.rr)
+    assert np.array_equal(to_np(pl.buf.out), ref.out)
+    assert np.array_equal(y[0], protocol.conv_reference(x[0], w, 1))
     keys.close()
     plan.close()
 

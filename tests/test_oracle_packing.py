@@ -242,3 +242,25 @@ def test_protocol_with_bias_and_batch_norm(enc):
     # encode_output is the exact inverse of decode on the output positions
     vals = np.arange(C * 6 * 5).reshape(C, 6, 5) - 50
     assert np.array_equal(packing.decode(plan, packing.encode_output(plan, vals, P.t), P.t), vals)
+
+
+@pytest.mark.parametrize("enc,h,pad", [("corr", 1, 0), ("conv", 1, 0), ("corr", 3, 1), ("conv", 3, 1)])
+def test_depthwise_layer_decodes_exactly(enc, h, pad):
+    """A depthwise layer (batch norm for h = 1, a per-channel 3x3 convolution
+    otherwise) under the depthwise plan: only MG * T products per image, and
+    the decoded outputs equal the per-channel convolution (plus the bias)."""
+    spec = wl.RingSpec(1024, (40, 40, 40), 65537)
+    P = he.Params.from_spec(spec)
+    C, H, W = 6, 7, 6
+    dw = np.zeros((C, C, h, h), dtype=np.int64)
+    kern = wl.weights(31, (C, h, h)).astype(np.int64)
+    for c in range(C):
+        dw[c, c] = kern[c]
+    beta = np.arange(C) * 37 - 80
+    plan = packing.make_plan(enc, P.N, C, H, W, C, h, pad, depthwise=True)
+    dense = packing.make_plan(enc, P.N, C, H, W, C, h, pad)
+    assert plan.products < dense.products or dense.G == 1
+    x = wl.activations(32, (2, C, H, W))
+    run = protocol.run_layer(P, plan, x, dw, wl.protocol_seeds(33), bias=beta)
+    for b in range(2):
+        assert np.array_equal(run.y[b], protocol.conv_reference(x[b], dw, pad) + beta[:, None, None])

@@ -69,3 +69,39 @@ def test_fig8_sweep_correlated_never_needs_more_products():
                     i = nv.he_plan_search(N, 3, H, H, 3, h, h // 2, ENC[enc])
                     cnt[enc] = i.MG * i.G * i.T
                 assert cnt["corr"] <= cnt["conv"], (N, H, h, cnt)
+
+
+@pytest.mark.parametrize("enc", ["conv", "corr"])
+def test_library_depthwise_plans_equal_the_oracle(enc):
+    """Depthwise plans (M = C, one product per kernel polynomial and tile):
+    the library's search equals the oracle's, keeps Mn a divisor of Cn, and
+    needs no more products than the dense plan of the same shape."""
+    r = wl.rng(99)
+    cases = [(8192, 64, 64, 64, 1, 0), (8192, 16, 16, 16, 1, 0), (4096, 32, 8, 8, 3, 1), (1024, 5, 9, 7, 3, 1)]
+    for _ in range(25):
+        N = int(r.choice([1024, 4096, 8192]))
+        h = int(r.choice([1, 3, 5]))
+        C = int(r.integers(1, 40))
+        H = int(r.integers(h, 33))
+        cases.append((N, C, H, int(r.integers(h, 33)), h, int(r.integers(0, h))))
+    for (N, C, H, W, h, pad) in cases:
+        try:
+            op = packing.make_plan(enc, N, C, H, W, C, h, pad, depthwise=True)
+        except ValueError:
+            with pytest.raises(nv.HEError):
+                nv.he_plan_search(N, C, H, W, C, h, pad, ENC[enc] | nv.HE_PLAN_DEPTHWISE)
+            continue
+        li = nv.he_plan_search(N, C, H, W, C, h, pad, ENC[enc] | nv.HE_PLAN_DEPTHWISE)
+        assert li.depthwise == 1 and li.encoding == ENC[enc]
+        assert (li.Cn, li.G, li.T, li.Mn, li.MG, li.Sout) == (op.Cn, op.G, op.T, op.Mn, op.MG, op.Sout)
+        assert op.G == 1 or op.Cn % op.Mn == 0
+        dense = packing.make_plan(enc, N, C, H, W, C, h, pad)
+        assert op.products <= dense.products
+    # the batch-norm case of the AlexNet-shaped bench: 64 channels of 64x64
+    bn = packing.make_plan(enc, 8192, 64, 64, 64, 64, 1, 0, depthwise=True)
+    assert bn.products == 64
+
+
+def test_depthwise_requires_as_many_outputs_as_inputs():
+    with pytest.raises(nv.HEError):
+        nv.he_plan_search(1024, 4, 8, 8, 5, 1, 0, nv.HE_ENC_CORRELATED | nv.HE_PLAN_DEPTHWISE)
