@@ -12,7 +12,7 @@ A_{N,t} = Z_t[x]/(x^N+1):
   w^[(h-1-i)O + (h-1-j)] = w[i,j], O = max(W, H) + h - 1; no coefficient is
   spent on padding.  Partition windows per Section 3.3 ("For large input ...").
 
-Readings where the paper is silent or garbled (each is listed in the design doc):
+Readings where the paper is silent or garbled:
   R1  conventional windows are square with side s, clipped to the padded
       image (H_n = min(s, H'), W_n = min(s, W')); this is the only reading that
       gives the toy example's 4 products at a degree cap of 8.

@@ -152,7 +152,7 @@ def test_fig8_sweep_correlated_never_needs_more_products():
     8..64, then kernels at 64x64).  The figure is missing from the source and
     its 4x / 5.1x ratios are not reproduced by the plans here; what holds is
     that the correlated plan never needs more products than the conventional
-    one.  The computed counts are recorded in the design doc."""
+    one."""
     for N in (4096, 8192):
         for H in (8, 16, 32, 64):
             a = packing.make_plan("conv", N, 3, H, H, 3, 5, 2)
