@@ -57,8 +57,8 @@ def test_plan_search_rejects_bad_arguments():
 def test_fig8_sweep_correlated_never_needs_more_products():
     """Fig. 8 (Section 4): multiply counts of the two packings over input sizes
     and kernel sizes at C = 3; the correlated packing never needs more
-    polynomial products than the conventional one (the printed 4x / 5.1x
-    ratios are not reproduced by these plans; see the readings)."""
+    polynomial products than the conventional one with same padding (the
+    printed 4x / 5.1x ratios are not reproduced by these plans)."""
     for N in (2048, 4096, 8192):
         for H in (8, 16, 32, 64):
             for h in (1, 3, 5, 7, 9, 11):
