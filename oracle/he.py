@@ -14,6 +14,11 @@ Parameter readings (the paper states none): Delta = floor(q / t); ternary
 secret; centred-binomial errors with eta = 21; relinearisation digits of
 base_log2 bits, ell = ceil(bitlen(q) / base_log2); pt operands centre-lifted
 before CPMul.
+
+Parity unpinned for the random objects (keys, encryption randomness, masks,
+the symmetric-encryption a and e): the paper fixes no generator, so their
+exact bits follow this project's stream convention (ChaCha20, pinned to RFC
+8439; words to samples as stated at each sampler).
 """
 from __future__ import annotations
 

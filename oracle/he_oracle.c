@@ -19,7 +19,11 @@
  *   - PPMul: negacyclic product mod t (Section 3.2, online phase).
  * Randomness: ChaCha20 block function (RFC 8439, section 2.3) used as a
  * counter-based generator; the sampling conventions are stated at each
- * sampler.
+ * sampler.  Parity unpinned for the samplers: the paper fixes no generator,
+ * so the mapping from stream words to samples -- and with it the exact bits
+ * of keys, ciphertexts and masks -- is a convention both sides implement from
+ * its written definition; the block function itself is pinned by the RFC test
+ * vector and the sample distributions by statistics tests.
  *
  * Integer products that exceed 64 bits use unsigned __int128 with the '%'
  * operator; big integers are fixed-width two's-complement arrays of 32-bit
