@@ -230,7 +230,10 @@ int he_encode_correlated(he_ctx *ctx, const he_plan *plan, int role, const void 
  *                 + sum_g ct_w[mg][g]    * pt_x[b][t][g]
  *                 + ct_add[b][mg][t]
  * Each family is skipped when its ciphertext pointer is NULL (at least one
- * must be given); ct_add may be NULL.  Plaintexts in [0,t) are centre-lifted.
+ * must be given); ct_add may be NULL or equal to ct_out (in place; any other
+ * overlap between inputs and ct_out is undefined).  Plaintexts in [0,t) are
+ * centre-lifted.  In a depthwise plan (HE_PLAN_DEPTHWISE) only the pairs
+ * g = mg * Mn / Cn enter the sums.
  * Shapes: ct_x [batch][T][G][2][L][N], pt_w [MG][G][N], ct_w [MG][G][2][L][N],
  * pt_x [batch][T][G][N], ct_add / ct_out [batch][MG][T][2][L][N].
  * Runs as one batched forward NTT and one fused MAC -> inverse NTT -> add. */
@@ -270,13 +273,16 @@ int he_cpmul_conv_noalloc(he_ctx *ctx, const he_plan *plan, int batch, const uin
  * floor(q/2)) / q) mod q, (c0, c1) = (d0, d1) + sum_j D_j rlk_j with D_j the
  * base-2^base_log2 digits of d2.  ct_a [n_a][2][L][N], ct_b [n_b][2][L][N];
  * pair_a, pair_b: HOST int32 [n_pairs] indices; out [n_pairs/group][2][L][N].
- * Needs keys made with_relin.  group <= max_ccmul_group. */
+ * Needs keys made with_relin.  group <= max_ccmul_group.  Outputs run in
+ * chunks whose device scratch fits max_ccmul_scratch_bytes (he_params). */
 int he_ccmul_precompute(he_ctx *ctx, const he_keys *keys, const uint64_t *ct_a, int n_a, const uint64_t *ct_b,
                         int n_b, const int32_t *pair_a, const int32_t *pair_b, int n_pairs, int group,
                         uint64_t *ct_out, cudaStream_t stream);
 /* The same over a plan: out[b][mg][t] = sum_g [r^x][b][t][g] (x) [r^w][mg][g]
- * (the precomputed [r^x r^w] of Section 3.2).  ct_rx [batch][T][G][2][L][N],
- * ct_rw [MG][G][2][L][N], out [batch][MG][T][2][L][N]. */
+ * (the precomputed [r^x r^w] of Section 3.2; also the online [x][w] of the
+ * CryptoTrain-B layer, Section 3.1).  ct_rx [batch][T][G][2][L][N],
+ * ct_rw [MG][G][2][L][N], out [batch][MG][T][2][L][N].  In a depthwise plan
+ * only the pair g = mg * Mn / Cn enters each sum. */
 int he_ccmul_conv_precompute(he_ctx *ctx, const he_keys *keys, const he_plan *plan, int batch,
                              const uint64_t *ct_rx, const uint64_t *ct_rw, uint64_t *ct_out, cudaStream_t stream);
 
