@@ -163,6 +163,18 @@ int he_keygen(he_ctx *ctx, uint64_t seed, int with_relin, he_keys **keys, cudaSt
 int he_keys_destroy(he_keys *keys);
 /* Copy a key in coefficient form into device buffer dst (layouts above). */
 int he_keys_export(he_ctx *ctx, const he_keys *keys, int which, void *dst, cudaStream_t stream);
+/* Keys from their coefficient forms (device buffers in the layouts above, as
+ * written by he_keys_export; rlk may be NULL for keys without relinearisation)
+ * -- the resume half of a checkpoint of a serving process.  The NTT forms are
+ * recomputed on the device.  INVALID_ARG when sk is not ternary or a residue
+ * of pk / rlk is not below its limb modulus (checked on the device; the call
+ * synchronises the stream). */
+int he_keys_import(he_ctx *ctx, const int64_t *sk, const uint64_t *pk, const uint64_t *rlk, he_keys **keys,
+                   cudaStream_t stream);
+/* 64-bit fingerprint (FNV-1a) of the parameters that fix a context's
+ * arithmetic (N, L, primes, t, digit base, eta, ell, auxiliary primes), to
+ * check that a checkpoint is resumed on an identical context. */
+int he_ctx_fingerprint(const he_ctx *ctx, uint64_t *fingerprint);
 
 /* he_encrypt, eps(p, pk) of Section 2: pt [n][N] in [0,t) -> ct [n][2][L][N];
  * ct_k = (b u + e1 + Delta m, a u + e2), Delta = floor(q/t), u ternary and

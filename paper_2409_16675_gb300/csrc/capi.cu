@@ -288,6 +288,79 @@ int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStrea
     return HE_OK;
 }
 
+// Keys from their coefficient forms (e.g. a checkpoint written with
+// he_keys_export): the NTT forms are recomputed on the device.
+int he_keys_import(he_ctx *c, const int64_t *sk, const uint64_t *pk, const uint64_t *rlk, he_keys **out,
+                   cudaStream_t st) {
+    if (!c || !sk || !pk || !out) return HE_ERR_INVALID_ARG;
+    *out = nullptr;
+    TRY(set_device(c));
+    const int N = c->N, L = c->L, ell = rlk ? c->ell : 0;
+    const size_t LN = (size_t)L * N;
+    he_keys *k = new he_keys();
+    k->L = L; k->N = N; k->ell = ell;
+    auto alloc = [&](u64 **p, size_t n) { return cudaMalloc((void **)p, n * 8) == cudaSuccess; };
+    if (!alloc(&k->sk, N) || !alloc(&k->s_ntt, LN) || !alloc(&k->pk, 2 * LN) || !alloc(&k->pk_ntt, 2 * LN) ||
+        (ell && (!alloc(&k->rlk, (size_t)ell * 2 * LN) || !alloc(&k->rlk_ntt, (size_t)ell * 2 * LN)))) {
+        he_keys_destroy(k);
+        return fail(c, HE_ERR_OOM, "key allocation");
+    }
+    int rc = ws_reserve(c, Carver::round(N) + Carver::round(8) + 4096);
+    if (rc) { he_keys_destroy(k); return rc; }
+    Carver cv(c->ws);
+    int8_t *s8 = cv.take<int8_t>(N);
+    int *bad = cv.take<int>(2);
+    auto run = [&]() -> int {
+        TRY(cuda_check(c, cudaMemsetAsync(bad, 0, sizeof(int), st), "import flag"));
+        TRY(cuda_check(c, cudaMemcpyAsync(k->sk, sk, (size_t)N * 8, cudaMemcpyDeviceToDevice, st), "sk copy"));
+        TRY(cuda_check(c, cudaMemcpyAsync(k->pk, pk, 2 * LN * 8, cudaMemcpyDeviceToDevice, st), "pk copy"));
+        if (ell)
+            TRY(cuda_check(c, cudaMemcpyAsync(k->rlk, rlk, (size_t)ell * 2 * LN * 8, cudaMemcpyDeviceToDevice, st),
+                           "rlk copy"));
+        TRY(launch_import_sk(c, (const int64_t *)k->sk, s8, bad, st));
+        TRY(launch_check_residues(c, k->pk, 2, bad, st));
+        if (ell) TRY(launch_check_residues(c, k->rlk, 2LL * ell, bad, st));
+        int h_bad = 0;
+        TRY(cuda_check(c, cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "import flag read"));
+        TRY(cuda_check(c, cudaStreamSynchronize(st), "import sync"));
+        if (h_bad & 1) return fail(c, HE_ERR_INVALID_ARG, "secret key is not ternary");
+        if (h_bad & 2) return fail(c, HE_ERR_INVALID_ARG, "key residue not below its limb modulus");
+        FwdJob fj[3];
+        int nf = 0;
+        FwdJob f = fwd_job();
+        f.src = s8; f.kind = SRC_I8; f.src_stride = N; f.dst = k->s_ntt; f.dst_stride = LN; f.n_polys = 1; f.n_limbs = L;
+        fj[nf++] = f;
+        f = fwd_job();
+        f.src = k->pk; f.kind = SRC_RNS; f.src_stride = LN; f.dst = k->pk_ntt; f.dst_stride = LN; f.n_polys = 2;
+        f.n_limbs = L;
+        fj[nf++] = f;
+        if (ell) {
+            f.src = k->rlk; f.dst = k->rlk_ntt; f.n_polys = 2 * ell;
+            fj[nf++] = f;
+        }
+        return launch_fwd_multi(c, fj, nf, st);
+    };
+    rc = run();
+    if (rc) { he_keys_destroy(k); return rc; }
+    *out = k;
+    return HE_OK;
+}
+
+// 64-bit FNV-1a over every parameter that fixes the arithmetic of a context
+int he_ctx_fingerprint(const he_ctx *c, uint64_t *fp) {
+    if (!c || !fp) return HE_ERR_INVALID_ARG;
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; i++) { h ^= (v >> (8 * i)) & 0xff; h *= 1099511628211ull; }
+    };
+    mix((uint64_t)c->N); mix((uint64_t)c->L); mix(c->P.t); mix((uint64_t)c->P.base_log2); mix((uint64_t)c->P.eta);
+    mix((uint64_t)c->ell); mix((uint64_t)c->K);
+    for (u64 q : c->q) mix(q);
+    for (u64 b : c->aux) mix(b);
+    *fp = h;
+    return HE_OK;
+}
+
 int he_keys_destroy(he_keys *k) {
     if (!k) return HE_OK;
     cudaDeviceSynchronize();

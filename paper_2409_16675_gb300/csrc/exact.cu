@@ -432,6 +432,33 @@ int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, 
     return cuda_check(c, cudaGetLastError(), "k_pt_sub");
 }
 
+// import checks: a ternary secret key (as int8 for the forward transform) and
+// residues below their limb modulus; a violation sets *bad (never traps)
+__global__ void k_import_sk(const long long *__restrict__ sk, int N, int8_t *__restrict__ s8, int *bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long v = sk[i];
+    if (v < -1 || v > 1) atomicOr(bad, 1);
+    s8[i] = (int8_t)(v < -1 ? -1 : (v > 1 ? 1 : v));
+}
+__global__ void k_check_residues(const u64 *__restrict__ a, long long total, int N, int L,
+                                 const ModDev *__restrict__ mods, int *bad) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    if (a[gid] >= mods[(gid / N) % L].q) atomicOr(bad, 2);
+}
+
+int launch_import_sk(he_ctx *c, const int64_t *sk, int8_t *s8, int *bad, cudaStream_t st) {
+    k_import_sk<<<(c->N + 255) / 256, 256, 0, st>>>((const long long *)sk, c->N, s8, bad);
+    return cuda_check(c, cudaGetLastError(), "k_import_sk");
+}
+int launch_check_residues(he_ctx *c, const u64 *a, long long n_polys, int *bad, cudaStream_t st) {
+    const long long total = n_polys * c->L * c->N;
+    if (!total) return HE_OK;
+    k_check_residues<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a, total, c->N, c->L, c->d_mods, bad);
+    return cuda_check(c, cudaGetLastError(), "k_check_residues");
+}
+
 int launch_copy_sk(he_ctx *c, const int8_t *s8, u64 *sk, cudaStream_t st) {
     k_copy_sk<<<(c->N + 255) / 256, 256, 0, st>>>(s8, (long long *)sk, c->N);
     return cuda_check(c, cudaGetLastError(), "k_copy_sk");

@@ -283,6 +283,8 @@ enum SampleKind { SAMPLE_TERNARY = 0, SAMPLE_CBD = 1, SAMPLE_UNIFORM_Q = 2, SAMP
 int launch_encode_output(he_ctx *c, const int32_t *map, int HW, int M, int polys, int batch, const int64_t *values,
                          u64 *out, cudaStream_t st);
 int launch_ct_add(he_ctx *c, const u64 *a, const u64 *b, long long n_polys, u64 *out, cudaStream_t st);
+int launch_import_sk(he_ctx *c, const int64_t *sk, int8_t *s8, int *bad, cudaStream_t st);
+int launch_check_residues(he_ctx *c, const u64 *a, long long n_polys, int *bad, cudaStream_t st);
 int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_obj, int n_limbs,
                   void *out, cudaStream_t st);
 

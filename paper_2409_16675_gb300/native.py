@@ -104,6 +104,8 @@ def _load():
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
+        "he_keys_import": [vp, vp, vp, vp, pp, vp],
+        "he_ctx_fingerprint": [vp, ctypes.POINTER(u64)],
         "he_encrypt_symmetric": [vp, vp, vp, i32, u64, vp, vp],
         "he_expand_symmetric": [vp, u64, i32, vp, vp, vp],
         "he_encrypt_many": [vp, vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint64),
@@ -240,6 +242,18 @@ def he_encrypt_symmetric(ctx, keys, pt, n: int, seed: int, c0):
 
 def he_expand_symmetric(ctx, seed: int, n: int, c0, ct):
     _check(lib.he_expand_symmetric(ctx, seed, n, _ptr(c0), _ptr(ct), _stream()), ctx)
+
+
+def he_keys_import(ctx, sk, pk, rlk=None):
+    h = ctypes.c_void_p()
+    _check(lib.he_keys_import(ctx, _ptr(sk), _ptr(pk), _ptr(rlk), ctypes.byref(h), _stream()), ctx)
+    return h
+
+
+def he_ctx_fingerprint(ctx) -> int:
+    v = ctypes.c_uint64()
+    _check(lib.he_ctx_fingerprint(ctx, ctypes.byref(v)), ctx)
+    return v.value
 
 
 def he_decrypt(ctx, keys, ct: torch.Tensor, n: int, pt: torch.Tensor):

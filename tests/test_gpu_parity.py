@@ -504,3 +504,83 @@ def test_errors_are_reported_not_raised_on_device():
     nv.he_decrypt(c.h, k.h, a, 0, c.u64(1, c.N))
     k.close()
     torch.cuda.synchronize()
+
+
+def test_checkpoint_resume(tmp_path):
+    """Checkpoint / resume of a serving process: keys exported in coefficient
+    form and the precomputed [r^x r^w] saved with the context fingerprint;
+    a fresh context resumes them (he_keys_import recomputes the NTT forms)
+    and the online layer gives the same bits as before.  A context with other
+    parameters is refused, and so are keys that are not valid residues."""
+    from paper_2409_16675_gb300 import checkpoint
+    spec = wl.RING_SMALL
+    c1 = layer.Context(spec)
+    seeds = wl.protocol_seeds(515)
+    keys = layer.Keys(c1, seeds.keys, True)
+    shape = wl.ConvShape(3, 12, 12, 4, 3, 1)
+    plan = layer.Plan(c1, shape, "corr")
+    pl = layer.PLayer(c1, keys, plan, 2)
+    x = torch.from_numpy(wl.activations(516, (2, 3, 12, 12))).cuda()
+    w = torch.from_numpy(wl.weights(517, (4, 3, 3, 3))).cuda()
+    pl.client_prepare(x, w, seeds)
+    pl.offline()
+    pl.online()
+    want = to_np(pl.buf.out)
+    path = str(tmp_path / "state")
+    checkpoint.save(path, c1, keys, {"rr": pl.buf.rr, "ct_x": pl.buf.ct_x, "ct_w": pl.buf.ct_w,
+                                     "xm": pl.buf.xm, "wm": pl.buf.wm})
+    # resume on a new context of the same ring
+    c2 = layer.Context(spec)
+    keys2, t = checkpoint.load(path, c2)
+    for which in (nv.HE_KEY_SK, nv.HE_KEY_PK, nv.HE_KEY_RLK):
+        assert torch.equal(keys2.export(which), keys.export(which))
+    plan2 = layer.Plan(c2, shape, "corr")
+    out = c2.ct(pl.no)
+    nv.he_cpmul_conv(c2.h, plan2.h, 2, t["ct_x"], t["wm"], t["ct_w"], t["xm"], t["rr"], out)
+    assert np.array_equal(to_np(out), want)
+    # the resumed keys encrypt, relinearise and decrypt like the originals
+    m = cuda(wl.uniform_mod(518, (2, c2.N), c2.t))
+    a, b = c1.ct(2), c2.ct(2)
+    nv.he_encrypt(c1.h, keys.h, m, 2, 99, a)
+    nv.he_encrypt(c2.h, keys2.h, m, 2, 99, b)
+    assert torch.equal(a, b)
+    pa, pb = c1.ct(1), c2.ct(1)
+    nv.he_ccmul_precompute(c1.h, keys.h, a, 2, a, 2, [(0, 1)], 1, pa)
+    nv.he_ccmul_precompute(c2.h, keys2.h, b, 2, b, 2, [(0, 1)], 1, pb)
+    assert torch.equal(pa, pb)
+    # other parameters: refused
+    c3 = layer.Context(wl.RingSpec(4096, (36, 36, 40), 65537))
+    with pytest.raises(ValueError):
+        checkpoint.load(path, c3)
+    # a key residue outside its limb: refused on the device, no fault
+    bad_pk = keys.export(nv.HE_KEY_PK).clone()
+    bad_pk[0, 0, 0] = c1.q[0]
+    with pytest.raises(nv.HEError):
+        nv.he_keys_import(c1.h, keys.export(nv.HE_KEY_SK), bad_pk, None)
+    for h in (keys, keys2, plan, plan2):
+        h.close()
+    for cc in (c1, c2, c3):
+        cc.close()
+
+
+def test_determinism_same_seeds_same_bits():
+    """Same seeds, same bits: the whole layer step (keys, encryptions,
+    CCMul-Precompute, online, PPMul, decryption) repeated five times on the
+    benchmark's layer (batch 8) gives identical ciphertexts and outputs --
+    no result depends on the order in which CTAs or streams run."""
+    w_ = wl.CONV_MID
+    c = ctx_for("n8192")
+    seeds = wl.protocol_seeds(w_.seed)
+    x, k = wl.layer_inputs(w_, 8)
+    runs = []
+    for _ in range(5):
+        keys = layer.Keys(c, seeds.keys, True)
+        plan = layer.Plan(c, w_.shape, w_.encoding)
+        pl = layer.PLayer(c, keys, plan, 8)
+        y = pl.step(cuda(x), cuda(k), seeds)
+        runs.append([to_np(t) for t in (pl.buf.ct_x, pl.buf.rr, pl.buf.out, pl.buf.p, y)])
+        keys.close()
+        plan.close()
+    for r in runs[1:]:
+        for a, b in zip(r, runs[0]):
+            assert np.array_equal(a, b)
