@@ -425,7 +425,13 @@ int he_server_create(const he_server_config *cfg, he_server **server);
 int he_server_submit(he_server *server, he_ctx *ctx, const he_plan *plan, int n_images, const uint64_t *ct_x,
                      const uint64_t *pt_w, const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add,
                      uint64_t *ct_out, int64_t *request_id);
+/* *done = 1 once the request completed or was cancelled; latency_us is the
+ * submission-to-completion time of a completed request, else -1. */
 int he_server_poll(he_server *server, int64_t request_id, int *done, double *latency_us);
+/* Withdraw a request that is still waiting for admission (*cancelled = 1; its
+ * buffers are never touched); an admitted or finished request is not affected
+ * (*cancelled = 0). */
+int he_server_cancel(he_server *server, int64_t request_id, int *cancelled);
 /* Arena bytes one request would reserve (its scratch plus its share of the
  * work lists), for admission planning; has_x / has_w select the families. */
 int he_server_request_bytes(const he_ctx *ctx, const he_plan *plan, int n_images, int has_x, int has_w,

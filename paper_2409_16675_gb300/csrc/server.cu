@@ -96,7 +96,7 @@ struct he_server {
         he::JobDesc J;
         size_t bytes = 0, off = 0;  // [A][B][terms][forward items][MAC items]
         double t_submit = 0, t_admit = 0, t_done = 0;
-        int state = 0;  // 0 queued, 1 admitted, 2 done
+        int state = 0;  // 0 queued, 1 admitted, 2 done, 3 cancelled while queued
     };
     std::vector<Req> reqs;
     std::deque<int64_t> pending;
@@ -384,9 +384,25 @@ int he_server_poll(he_server *s, int64_t id, int *done, double *latency_us) {
     std::lock_guard<std::mutex> g(s->mu);
     if (id < 0 || id >= (int64_t)s->reqs.size()) return HE_ERR_INVALID_ARG;
     const auto &r = s->reqs[id];
-    *done = r.state == 2;
+    *done = r.state >= 2;
     if (latency_us) *latency_us = r.state == 2 ? r.t_done - r.t_submit : -1.0;
     return s->worker_rc;
+}
+
+int he_server_cancel(he_server *s, int64_t id, int *cancelled) {
+    if (!s || !cancelled) return HE_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(s->mu);
+    if (id < 0 || id >= (int64_t)s->reqs.size()) return HE_ERR_INVALID_ARG;
+    auto &r = s->reqs[id];
+    *cancelled = 0;
+    if (r.state != 0) return HE_OK;  // admitted requests run to completion
+    auto it = std::find(s->pending.begin(), s->pending.end(), id);
+    if (it != s->pending.end()) s->pending.erase(it);
+    r.state = 3;
+    r.t_done = now_us();
+    *cancelled = 1;
+    s->cv.notify_all();
+    return HE_OK;
 }
 
 int he_server_wait_all(he_server *s, double timeout_s) {

@@ -129,6 +129,7 @@ def _load():
         "he_server_create": [ctypes.POINTER(he_server_config), pp],
         "he_server_submit": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)],
         "he_server_poll": [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
+        "he_server_cancel": [vp, i64, ctypes.POINTER(i32)],
         "he_server_wait_all": [vp, ctypes.c_double],
         "he_server_request_bytes": [vp, vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)],
         "he_server_stats": [vp, ctypes.POINTER(he_server_report)],
@@ -441,6 +442,12 @@ def he_server_poll(s, rid):
     lat = ctypes.c_double()
     _check(lib.he_server_poll(s, rid, ctypes.byref(done), ctypes.byref(lat)))
     return bool(done.value), lat.value
+
+
+def he_server_cancel(s, rid) -> bool:
+    c = ctypes.c_int32()
+    _check(lib.he_server_cancel(s, rid, ctypes.byref(c)))
+    return bool(c.value)
 
 
 def he_server_wait_all(s, timeout_s=600.0):

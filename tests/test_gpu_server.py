@@ -92,3 +92,35 @@ def test_server_admission_under_a_small_budget():
     for l, o in outs:
         assert torch.equal(o, l.buf.out)
     nv.he_server_destroy(srv)
+
+
+def test_cancel_waiting_requests():
+    """Requests still waiting for admission can be withdrawn: with room for
+    one request at a time, the later submissions are cancelled, their output
+    buffers are never touched, and every request that was not cancelled
+    completes with the bits of the request run alone."""
+    clients = setup_clients()
+    need = [nv.he_server_request_bytes(c.h, p.h, l.B) for (c, k, p, l, _, _) in clients]
+    srv = nv.he_server_create(0, hbm_budget_bytes=1.3 * max(need) + (1 << 20), max_group=1, max_inflight=1,
+                              n_streams=1)
+    subs = []
+    for rep in range(4):
+        for (c, k, p, l, _, _) in clients:
+            o = torch.full_like(l.buf.out.view(torch.int64), 7).view(torch.uint64)
+            rid = nv.he_server_submit(srv, c.h, p.h, l.B, l.buf.ct_x, l.buf.wm, l.buf.ct_w, l.buf.xm, l.buf.rr, o)
+            subs.append((rid, l, o))
+    cancelled = {rid for (rid, l, o) in subs[-6:] if nv.he_server_cancel(srv, rid)}
+    assert cancelled, "nothing was still waiting"
+    nv.he_server_wait_all(srv, 120.0)
+    st = nv.he_server_stats(srv)
+    assert st["completed"] == len(subs) - len(cancelled)
+    for rid, l, o in subs:
+        done, lat = nv.he_server_poll(srv, rid)
+        assert done
+        if rid in cancelled:
+            assert lat < 0 and bool((o.view(torch.int64) == 7).all())
+            assert not nv.he_server_cancel(srv, rid)        # cancelling twice reports nothing
+        else:
+            assert torch.equal(o, l.buf.out)
+    assert not nv.he_server_cancel(srv, subs[0][0])      # long finished
+    nv.he_server_destroy(srv)
