@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace he {
@@ -105,7 +107,10 @@ static int upload_terms(he_ctx *c, const Terms &T, MacJob &m) {
     return upload_terms_raw(c, T, &m.ptr, &m.ta, &m.tb);
 }
 
+// Every traced launch is also an NVTX range (host side, around the enqueue),
+// so profilers can select the library's stages by name.
 TraceScope::TraceScope(he_ctx *c_, cudaStream_t st_, const char *name, double bytes, double modmuls) : c(c_), st(st_) {
+    nvtxRangePushA(name);
     if (!c || !c->trace) return;
     he_ctx::TraceRec r{name, nullptr, nullptr, bytes, modmuls};
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
@@ -115,6 +120,7 @@ TraceScope::TraceScope(he_ctx *c_, cudaStream_t st_, const char *name, double by
 }
 TraceScope::~TraceScope() {
     if (idx >= 0) cudaEventRecord(c->trace_recs[idx].b, st);
+    nvtxRangePop();
 }
 
 static MacJob mac_job() {
