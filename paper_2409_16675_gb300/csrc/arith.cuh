@@ -53,6 +53,14 @@ __device__ __forceinline__ u64 shoup3(u64 a, u64 w, u64 ws, u64 nq) {
         : "l"(a), "l"(w), "l"(ws), "l"(nq));
     return r;
 }
+// The same Shoup product for a multiplier k < 2^32 (a CRT overflow count):
+// floor(k w' / 2^64) = floor((k w'_1 + floor(k w'_0 / 2^32)) / 2^32) with
+// w' = w'_1 2^32 + w'_0, and that quotient is below k, so every partial
+// product is 32 x 32 bits.  Bit-identical to shoup(k, w, ws, q).
+__device__ __forceinline__ u64 shoup_small(uint32_t k, u64 w, u64 ws, u64 q) {
+    const u64 qh = ((u64)k * (uint32_t)(ws >> 32) + __umulhi(k, (uint32_t)ws)) >> 32;
+    return (u64)k * w - (u64)(uint32_t)qh * q;  // [0, 2q)
+}
 __device__ __forceinline__ u64 red1(u64 a, u64 q) { return a >= q ? a - q : a; }
 __device__ __forceinline__ u64 addm(u64 a, u64 b, u64 q) { return red1(a + b, q); }   // a,b < q
 __device__ __forceinline__ u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
@@ -68,6 +76,14 @@ __device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const ModDev &M) {
     u64 r = a + b;                           // [0, 4q)
     r = r >= M.twoq ? r - M.twoq : r;
     return red1(r, M.q);
+}
+// Montgomery reduction (P. L. Montgomery, Math. Comp. 44 (1985)) of
+// T = hi 2^64 + lo < q 2^64: returns T 2^-64 mod q, fully reduced.  With
+// m = lo q^-1 mod 2^64 the low word of m q equals lo, so T - m q =
+// (hi - mulhi(m, q)) 2^64 exactly, and hi - mulhi(m, q) lies in (-q, q).
+__device__ __forceinline__ u64 redc(u64 lo, u64 hi, const ModDev &M) {
+    const u64 mh = __umul64hi(lo * M.qinv, M.q);
+    return hi >= mh ? hi - mh : hi - mh + M.q;
 }
 // x mod q for x < 64 q, fully reduced, from a single-precision quotient
 // estimate: every rounding is toward zero and qf <= 2^qsh / q, so the
@@ -100,7 +116,7 @@ __device__ __forceinline__ int crt_compose(const CrtDev &B, const u64 (&y)[NM], 
         u64 carry = 0;
 #pragma unroll
         for (int k = 0; k < MW; k++) {
-            if (k < B.W) {
+            if (k < B.Wh) {  // words of hat_i
                 u64 lo, hi;
                 mul128(y[i], B.hat[i][k], lo, hi);
                 u64 s = X[k] + lo;
@@ -109,6 +125,10 @@ __device__ __forceinline__ int crt_compose(const CrtDev &B, const u64 (&y)[NM], 
                 hi += (s < carry);
                 X[k] = s;
                 carry = hi;
+            } else if (k < B.W) {  // carry into the words above
+                const u64 s = X[k] + carry;
+                carry = s < carry;
+                X[k] = s;
             }
         }
     }
@@ -205,7 +225,7 @@ __device__ __forceinline__ u64 conv_to(const u64 (&y)[NM], int n, const u64 *h, 
             acc = acc >= p2 ? acc - p2 : acc;
         }
     acc = red1(acc, p);
-    return subm(acc, red1(shoup(k, Mp, Mps, p), p), p);
+    return subm(acc, red1(shoup_small((uint32_t)k, Mp, Mps, p), p), p);
 }
 
 // ---------------------------------------------------------------- ChaCha20

@@ -130,24 +130,24 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
     const int LK = L + K;
     const u64 *src = d + ((o * 3 + j) * LK) * N + x;
     const CrtDev &Q = E->Q, &B = E->B;
-    // r = [t d + floor(q/2)]_q as residues y (CRT form)
+    // r = [t d + floor(q/2)]_q as residues y (CRT form): y_i = d_i (t inv_i)
+    // + floor(q/2) inv_i mod q_i
     u64 y[LM];
 #pragma unroll
     for (int i = 0; i < LM; i++)
         if (i < L) {
             const u64 qi = mods[i].q;
-            const u64 td = red1(shoup(src[(long long)i * N], E->t_q[i], E->t_qs[i], qi), qi);
-            y[i] = crt_y(Q, i, addm(td, E->Qhalf_q[i], qi));
+            y[i] = addm(red1(shoup(src[(long long)i * N], E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
         }
-    // r mod b_k
-    u64 rb[KM];
+    // r c_k mod b_k (c_k = q^-1 (B/b_k)^-1 mod b_k folded into the conversion)
+    u64 rc[KM];
     int v;
     u64 fr;
     if (crt_overflow<LM>(E->Qc, y, L, v, fr)) {
 #pragma unroll
         for (int k = 0; k < KM; k++)
             if (k < K)
-                rb[k] = conv_to<LM>(y, L, E->QhatB[k], E->QhatBs[k], (u64)v, E->Q_b[k], E->Q_bs[k], mods[L + k].q);
+                rc[k] = conv_to<LM>(y, L, E->QhatBc[k], E->QhatBcs[k], (u64)v, E->Q_bc[k], E->Q_bcs[k], mods[L + k].q);
     } else {
         u64 R[MW];
         crt_compose<MW>(Q, y, R);
@@ -155,26 +155,33 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
         for (int k = 0; k < KM; k++)
             if (k < K) {
                 const ModDev &M = mods[L + k];
-                rb[k] = mw_mod<MW>(R, Q.W, M.q, M.r64, M.r64s, M.one_s);
+                const u64 rb = mw_mod<MW>(R, Q.W, M.q, M.r64, M.r64s, M.one_s);
+                rc[k] = red1(shoup(rb, E->f_cb[k], E->f_cbs[k], M.q), M.q);
             }
     }
-    // F = (t d + h - r) / q modulo each aux prime, as residues yb (CRT form over B)
+    // F = (t d + h - r) / q modulo each aux prime, as CRT residues over B:
+    // yb_k = (t d + h - r) c_k mod b_k
     u64 yb[KM];
 #pragma unroll
     for (int k = 0; k < KM; k++)
         if (k < K) {
             const u64 b = mods[L + k].q;
-            const u64 td = red1(shoup(src[(long long)(L + k) * N], E->t_b[k], E->t_bs[k], b), b);
-            const u64 num = subm(addm(td, E->Qhalf_b[k], b), rb[k], b);
-            yb[k] = crt_y(B, k, red1(shoup(num, E->Qinv_b[k], E->Qinv_bs[k], b), b));
+            const u64 td = red1(shoup(src[(long long)(L + k) * N], E->f_tb[k], E->f_tbs[k], b), b);
+            yb[k] = subm(addm(td, E->f_hb[k], b), rc[k], b);
         }
-    // centred F mod q_i
+    // centred F mod q_i; for the digit component (j = 2) directly its CRT
+    // residue F inv_i mod q_i (the constants carry the inv_i factor)
+    const bool dig = j == 2;
+    const u64(*H)[MAXP] = dig ? E->BhatQi : E->BhatQ;
+    const u64(*Hs)[MAXP] = dig ? E->BhatQis : E->BhatQs;
+    const u64 *Bq = dig ? E->B_qi : E->B_q;
+    const u64 *Bqs = dig ? E->B_qis : E->B_qs;
     u64 f[LM];
     if (crt_overflow<KM>(E->Bc, yb, K, v, fr) && half_certain(fr)) {
         const u64 k = (u64)v + (fr >= (1ull << 57));
 #pragma unroll
         for (int i = 0; i < LM; i++)
-            if (i < L) f[i] = conv_to<KM>(yb, K, E->BhatQ[i], E->BhatQs[i], k, E->B_q[i], E->B_qs[i], mods[i].q);
+            if (i < L) f[i] = conv_to<KM>(yb, K, H[i], Hs[i], k, Bq[i], Bqs[i], mods[i].q);
     } else {
         u64 F[MW];
         crt_compose<MW>(B, yb, F);
@@ -183,11 +190,12 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
         for (int i = 0; i < LM; i++)
             if (i < L) {
                 const ModDev &M = mods[i];
-                const u64 a = mw_mod<MW>(F, B.W, M.q, M.r64, M.r64s, M.one_s);
-                f[i] = neg ? subm(a, E->B_q[i], M.q) : a;
+                u64 a = mw_mod<MW>(F, B.W, M.q, M.r64, M.r64s, M.one_s);
+                if (neg) a = subm(a, E->B_q[i], M.q);
+                f[i] = dig ? crt_y(Q, i, a) : a;
             }
     }
-    if (j < 2) {
+    if (!dig) {
         u64 *out = dq + ((o * 2 + j) * L) * N + x;
 #pragma unroll
         for (int i = 0; i < LM; i++)
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
     // digits of [F]_q in [0, q): exact multi-word value
 #pragma unroll
     for (int i = 0; i < LM; i++)
-        if (i < L) y[i] = crt_y(Q, i, f[i]);
+        if (i < L) y[i] = f[i];
     u64 X[MW];
     crt_compose<MW>(Q, y, X);
     const u64 dmask = (1ull << base_log2) - 1;
@@ -231,8 +239,7 @@ __global__ void __launch_bounds__(128) k_decrypt_exact(const u64 *__restrict__ x
     for (int i = 0; i < LM; i++)
         if (i < L) {
             const u64 qi = mods[i].q;
-            const u64 tx = red1(shoup(xs[(k * L + i) * N + x], E->t_q[i], E->t_qs[i], qi), qi);
-            y[i] = crt_y(Q, i, addm(tx, E->Qhalf_q[i], qi));
+            y[i] = addm(red1(shoup(xs[(k * L + i) * N + x], E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
         }
     const u64 t = E->t;
     u64 rt;

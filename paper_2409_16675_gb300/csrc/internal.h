@@ -35,11 +35,14 @@ struct ModDev {
     const ulonglong2 *fw, *iw, *z;
     float qf;          // 2^qsh / q in single precision, rounded down
     int qsh;           // max(0, bitlen(q) + 6 - 32): x >> qsh fits 32 bits for x < 64 q
+    u64 qinv;          // q^-1 mod 2^64 (Montgomery reduction of the accumulated products)
+    int fold;          // products summed between exact folds: min(15, floor((2^64-1)/q) + 1)
 };
 
 // A CRT basis {m_i}: M = prod m_i, hat_i = M / m_i, inv_i = hat_i^-1 mod m_i.
 struct CrtDev {
     int n, W;                 // primes, words used by sums
+    int Wh;                   // words of the largest hat_i = M / m_i (<= W)
     u64 m[MAXP];
     u64 inv[MAXP], invs[MAXP];
     u64 hat[MAXP][MAXW];
@@ -73,6 +76,17 @@ struct ExactDev {
     u64 B_q[MAXP], Qhalf_q[MAXP], t_q[MAXP], t_qs[MAXP], delta_q[MAXP], delta_qs[MAXP];
     // decryption: floor(Q/2) mod t, Q^-1 mod t (+Shoup w.r.t. t), 2^64 mod t (+Shoup), floor(2^64/t)
     u64 t, Qhalf_t, Qinv_t, Qinv_ts, r64_t, r64_ts, one_ts;
+    // Folded constants of the rescaling (each a product of the constants
+    // above, so one modular product replaces two or three).  With
+    // inv_i = (Q/q_i)^-1 mod q_i and c_j = Q^-1 (B/b_j)^-1 mod b_j:
+    //   tq[i] = t inv_i, hq[i] = floor(Q/2) inv_i                 (mod q_i)
+    //   tb[j] = t c_j, hb[j] = floor(Q/2) c_j, cb[j] = c_j,
+    //   QhatBc[j][i] = (Q/q_i) c_j, Q_bc[j] = Q c_j               (mod b_j)
+    //   BhatQi[i][j] = (B/b_j) inv_i, B_qi[i] = B inv_i           (mod q_i)
+    u64 f_tq[MAXP], f_tqs[MAXP], f_hq[MAXP];
+    u64 f_tb[MAXP], f_tbs[MAXP], f_hb[MAXP], f_cb[MAXP], f_cbs[MAXP];
+    u64 QhatBc[MAXP][MAXP], QhatBcs[MAXP][MAXP], Q_bc[MAXP], Q_bcs[MAXP];
+    u64 BhatQi[MAXP][MAXP], BhatQis[MAXP][MAXP], B_qi[MAXP], B_qis[MAXP];
 };
 
 }  // namespace he

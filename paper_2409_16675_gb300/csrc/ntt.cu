@@ -195,7 +195,10 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
-// in groups of CH coefficients (128-bit sums), result fully reduced.  The
+// in groups of CH coefficients (128-bit sums), times 2^-64 (a Montgomery
+// reduction ends each sum; the untwist table carries the 2^64 back), fully
+// reduced.  Every M.fold products the sum is folded exactly to below q, so
+// the final sum stays below q (1 + (M.fold - 1) q) <= q 2^64.  The
 // finished groups wait in shared memory (the exchange buffer is idle until
 // the inverse transform; thread tau owns slots k*T + tau), so the registers go
 // to loads in flight: the term loop is unrolled by two.  The caller's shared
@@ -223,14 +226,14 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
                 lo[kk] += pl;
                 hi[kk] += ph + (lo[kk] < pl);
             }
-            if (++cnt == 15) {  // products < 2^124: fold before the 128-bit sum can overflow
+            if (++cnt == M.fold) {  // also keeps the 128-bit sum of products < 2^124 from overflowing
 #pragma unroll
                 for (int kk = 0; kk < CH; kk++) { lo[kk] = reduce128(lo[kk], hi[kk], M); hi[kk] = 0; }
                 cnt = 0;
             }
         }
 #pragma unroll
-        for (int kk = 0; kk < CH; kk++) sm[(part * CH + kk) * T + tau] = reduce128(lo[kk], hi[kk], M);
+        for (int kk = 0; kk < CH; kk++) sm[(part * CH + kk) * T + tau] = redc(lo[kk], hi[kk], M);
     }
 #pragma unroll
     for (int k = 0; k < R; k++) v[k] = sm[k * T + tau];

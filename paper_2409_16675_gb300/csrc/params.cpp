@@ -129,6 +129,7 @@ static bool fill_crt(CrtDev &C, const std::vector<u64> &m, std::string &err) {
         u64 r;
         Big hat = M.div(m[i], &r);
         for (size_t k = 0; k < hat.w.size() && (int)k < MAXW; k++) C.hat[i][k] = hat.w[k];
+        C.Wh = std::max(C.Wh, std::min((int)hat.w.size(), C.W));
         C.inv[i] = invmod(hat.mod(m[i]), m[i]);
         C.invs[i] = shoup_c(C.inv[i], m[i]);
     }
@@ -159,7 +160,10 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     if (!psi) { err = "no primitive 2N-th root"; return false; }
     u64 psiinv = invmod(psi, q);
     const u64 ninv = invmod((u64)N, q);
-    // interleaved (value, Shoup companion) pairs: fw [N], iw [N], z [N]
+    const u64 r64 = (u64)(((u128)1 << 64) % q);
+    // interleaved (value, Shoup companion) pairs: fw [N], iw [N], z [N]; the
+    // untwist z_k = psi^-k N^-1 2^64 also undoes the 2^-64 of the Montgomery
+    // reduction that ends the multiply-accumulate
     std::vector<u64> tab(6 * (size_t)N, 0);
     u64 *fw = tab.data(), *iw = fw + 2 * N, *zt = iw + 2 * N;
     // powers psi^e and psi^-e for e in [0, 2N)
@@ -169,7 +173,7 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     for (int k = 0; k < N; k++) {
         fw[2 * k] = pw[bitrev(k, logN)];
         fw[2 * k + 1] = shoup_c(fw[2 * k], q);
-        zt[2 * k] = mulmod(ipw[k], ninv, q);
+        zt[2 * k] = mulmod(mulmod(ipw[k], ninv, q), r64, q);
         zt[2 * k + 1] = shoup_c(zt[2 * k], q);
     }
     // inverse stage s: omega^-(k 2^(n-1-s)) = psi^-(k 2^(n-s)) for k < 2^s
@@ -197,6 +201,13 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     M.iw = M.fw + N;
     M.z = M.iw + N;
     M.nq = 0 - q;
+    {
+        u64 x = q;  // q^-1 mod 2^64 by Newton's iteration (3, 6, ..., 96 correct bits)
+        for (int it = 0; it < 5; it++) x *= 2 - q * x;
+        M.qinv = x;
+        const u64 f = ~0ull / q + 1;
+        M.fold = (int)(f < 15 ? f : 15);
+    }
     {
         int bq = 0;
         while (bq < 64 && (q >> bq)) bq++;
@@ -355,6 +366,33 @@ int build_tables(he_ctx *c, std::string &err) {
     E.Qinv_t = invmod(Q.mod(t), t);
     if (!E.Qinv_t && t > 1) { err = "q not invertible mod t"; return HE_ERR_UNSUPPORTED_PARAMS; }
     E.Qinv_ts = shoup_c(E.Qinv_t, t);
+    // folded constants of the rescaling
+    for (int i = 0; i < c->L; i++) {
+        const u64 q = c->q[i], inv = E.Q.inv[i];
+        E.f_tq[i] = mulmod(E.t_q[i], inv, q);
+        E.f_tqs[i] = shoup_c(E.f_tq[i], q);
+        E.f_hq[i] = mulmod(E.Qhalf_q[i], inv, q);
+        for (int j = 0; j < c->K; j++) {
+            E.BhatQi[i][j] = mulmod(E.BhatQ[i][j], inv, q);
+            E.BhatQis[i][j] = shoup_c(E.BhatQi[i][j], q);
+        }
+        E.B_qi[i] = mulmod(E.B_q[i], inv, q);
+        E.B_qis[i] = shoup_c(E.B_qi[i], q);
+    }
+    for (int j = 0; j < c->K; j++) {
+        const u64 b = c->aux[j], cj = mulmod(E.Qinv_b[j], E.B.inv[j], b);
+        E.f_cb[j] = cj;
+        E.f_cbs[j] = shoup_c(cj, b);
+        E.f_tb[j] = mulmod(E.t_b[j], cj, b);
+        E.f_tbs[j] = shoup_c(E.f_tb[j], b);
+        E.f_hb[j] = mulmod(E.Qhalf_b[j], cj, b);
+        for (int i = 0; i < c->L; i++) {
+            E.QhatBc[j][i] = mulmod(E.QhatB[j][i], cj, b);
+            E.QhatBcs[j][i] = shoup_c(E.QhatBc[j][i], b);
+        }
+        E.Q_bc[j] = mulmod(E.Q_b[j], cj, b);
+        E.Q_bcs[j] = shoup_c(E.Q_bc[j], b);
+    }
     E.r64_t = (u64)(((u128)1 << 64) % t);
     E.r64_ts = shoup_c(E.r64_t, t);
     E.one_ts = (u64)(((u128)1 << 64) / t);
