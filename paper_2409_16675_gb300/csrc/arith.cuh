@@ -228,6 +228,31 @@ __device__ __forceinline__ u64 conv_to(const u64 (&y)[NM], int n, const u64 *h, 
     return subm(acc, red1(shoup_small((uint32_t)k, Mp, Mps, p), p), p);
 }
 
+// The same conversion with the constants in Montgomery form (hm_i = h_i 2^64
+// mod p): products summed in 128 bits, eight at a time (every y_i < 2^61 and
+// hm_i < p, so eight products stay below 2^64 p), each sum ended by one
+// Montgomery reduction, which removes the 2^64 again.  P is p's table entry.
+template <int NM>
+__device__ __forceinline__ u64 conv_to_m(const u64 (&y)[NM], int n, const u64 *hm, u64 k, u64 Mp, u64 Mps,
+                                         const ModDev &P) {
+    const u64 p = P.q;
+    u64 acc = 0;
+#pragma unroll
+    for (int c0 = 0; c0 < NM; c0 += 8) {
+        u64 lo = 0, hi = 0;
+#pragma unroll
+        for (int i = c0; i < c0 + 8 && i < NM; i++)
+            if (i < n) {
+                u64 pl, ph;
+                mul128(y[i], hm[i], pl, ph);
+                lo += pl;
+                hi += ph + (lo < pl);
+            }
+        acc = addm(acc, redc(lo, hi, P), p);
+    }
+    return subm(acc, red1(shoup_small((uint32_t)k, Mp, Mps, p), p), p);
+}
+
 // ---------------------------------------------------------------- ChaCha20
 // Block function of RFC 8439 (section 2.3): 20 rounds over the 4x4 state of
 // constants, 256-bit key, 32-bit counter and 96-bit nonce, then the input

@@ -416,16 +416,18 @@ static int encrypt_groups(he_ctx *c, const he_keys *k, int n_groups, const uint6
     u64 *un = cv.take<u64>((size_t)n * LN);
     FwdJob fj[4];
     MacJob mj[8];
-    int nf = 0, nm = 0;
+    SampleJob sj[3 * 4];
+    int nf = 0, nm = 0, ns = 0;
     size_t off = 0;
     for (int g = 0; g < n_groups; g++) {
         const int m = counts[g];
         if (!m) continue;
         int8_t *ug = u8 + off * N, *eg = e8 + off * 2 * N;
         u64 *ung = un + off * LN;
-        TRY(launch_sample(c, SAMPLE_TERNARY, seeds[g], 4, 0, m, 1, ug, st));
-        TRY(launch_sample(c, SAMPLE_CBD, seeds[g], 5, 0, m, 1, eg, st));
-        TRY(launch_sample(c, SAMPLE_CBD, seeds[g], 6, 0, m, 1, eg + (size_t)m * N, st));
+        // u (ternary), e1 and e2 (CBD) of every ciphertext of the group
+        sj[ns++] = SampleJob{SAMPLE_TERNARY, 4, 0, m, 1, seeds[g], ug};
+        sj[ns++] = SampleJob{SAMPLE_CBD, 5, 0, m, 1, seeds[g], eg};
+        sj[ns++] = SampleJob{SAMPLE_CBD, 6, 0, m, 1, seeds[g], eg + (size_t)m * N};
         FwdJob f = fwd_job();
         f.src = ug; f.kind = SRC_I8; f.src_stride = N; f.dst = ung; f.dst_stride = LN; f.n_polys = m; f.n_limbs = L;
         fj[nf++] = f;
@@ -443,6 +445,7 @@ static int encrypt_groups(he_ctx *c, const he_keys *k, int n_groups, const uint6
         }
         off += m;
     }
+    TRY(launch_sample_multi(c, sj, ns, st));
     TRY(launch_fwd_multi(c, fj, nf, st));
     return launch_mac_multi(c, mj, nm, st);
 }

@@ -15,11 +15,10 @@
 namespace he {
 
 // ---------------------------------------------------------------- sampling
-__global__ void k_sample(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_limbs, int N, void *out,
-                         long long total_blocks, const ModDev *__restrict__ mods, const ExactDev *__restrict__ E,
-                         int eta) {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total_blocks) return;
+// one ChaCha block (8 words) of a sample job: thread gid of the job
+__device__ __forceinline__ void sample_block(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_limbs, int N,
+                                             void *out, long long gid, const ModDev *__restrict__ mods,
+                                             const ExactDev *__restrict__ E, int eta) {
     if (kind == SAMPLE_UNIFORM_Q) {
         // 4 coefficients per ChaCha block (two words each)
         const int per = N / 4;
@@ -62,6 +61,34 @@ __global__ void k_sample(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, i
     *(u64 *)o = packed;
 }
 
+__global__ void k_sample(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_limbs, int N, void *out,
+                         long long total_blocks, const ModDev *__restrict__ mods, const ExactDev *__restrict__ E,
+                         int eta) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < total_blocks) sample_block(kind, seed, tag, idx0, n_limbs, N, out, gid, mods, E, eta);
+}
+
+// Sample jobs of one launch: blocks [start[i], start[i+1]) belong to job i,
+// whose threads cover total[i] ChaCha blocks.
+struct SampleJobs {
+    int n;
+    SampleJob j[kMaxSampleJobs];
+    long long total[kMaxSampleJobs];
+    int start[kMaxSampleJobs + 1];
+};
+
+__global__ void k_sample_multi(const __grid_constant__ SampleJobs JS, int N, const ModDev *__restrict__ mods,
+                               const ExactDev *__restrict__ E, int eta) {
+    int i = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxSampleJobs; k++)
+        if (k < JS.n && (int)blockIdx.x >= JS.start[k]) i = k;
+    const long long gid = (long long)((int)blockIdx.x - JS.start[i]) * blockDim.x + threadIdx.x;
+    if (gid >= JS.total[i]) return;
+    const SampleJob &J = JS.j[i];
+    sample_block(J.kind, J.seed, J.tag, J.idx0, J.n_limbs, N, J.out, gid, mods, E, eta);
+}
+
 int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_obj, int n_limbs,
                   void *out, cudaStream_t st) {
     const int N = c->N;
@@ -71,6 +98,35 @@ int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx
     k_sample<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(kind, seed, tag, idx0, n_limbs, N, out, total,
                                                                c->d_mods, c->d_exact, c->P.eta);
     return cuda_check(c, cudaGetLastError(), "k_sample");
+}
+
+int launch_sample_multi(he_ctx *c, const SampleJob *jobs, int n, cudaStream_t st) {
+    if (n < 0 || n > kMaxSampleJobs) return fail(c, HE_ERR_INVALID_ARG, "sample job count");
+    const int N = c->N;
+    SampleJobs JS;
+    memset(&JS, 0, sizeof JS);
+    long long blocks = 0;
+    double bytes = 0;
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const SampleJob &J = jobs[i];
+        const long long total = J.kind == SAMPLE_UNIFORM_Q ? (long long)J.n_obj * J.n_limbs * (N / 4)
+                                                           : (long long)J.n_obj * (N / 8);
+        if (total <= 0) continue;
+        JS.j[m] = J;
+        JS.total[m] = total;
+        JS.start[m] = (int)blocks;
+        blocks += (total + 127) / 128;
+        bytes += J.kind == SAMPLE_UNIFORM_Q ? 32.0 * total : (J.kind == SAMPLE_UNIFORM_T ? 64.0 * total : 8.0 * total);
+        m++;
+    }
+    if (!m) return HE_OK;
+    if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "sample launch too large");
+    JS.n = m;
+    JS.start[m] = (int)blocks;
+    TraceScope ts(c, st, "sample", bytes, 0);
+    k_sample_multi<<<(unsigned)blocks, 128, 0, st>>>(JS, N, c->d_mods, c->d_exact, c->P.eta);
+    return cuda_check(c, cudaGetLastError(), "k_sample_multi");
 }
 
 // ---------------------------------------------------------------- exact CRT kernels
@@ -98,10 +154,7 @@ __global__ void __launch_bounds__(128) k_base_extend(const u64 *__restrict__ src
         const u64 k = (u64)v + (fr >= (1ull << 57));
 #pragma unroll
         for (int j = 0; j < KM; j++)
-            if (j < K) {
-                const u64 b = mods[L + j].q;
-                dst[(p * K + j) * N + x] = conv_to<LM>(y, L, E->QhatB[j], E->QhatBs[j], k, E->Q_b[j], E->Q_bs[j], b);
-            }
+            if (j < K) dst[(p * K + j) * N + x] = conv_to_m<LM>(y, L, E->QhatBm[j], k, E->Q_b[j], E->Q_bs[j], mods[L + j]);
         return;
     }
     u64 X[MW];
@@ -117,8 +170,10 @@ __global__ void __launch_bounds__(128) k_base_extend(const u64 *__restrict__ src
 
 // d: [n_out][3][L+K][N] exact tensor products (coefficient form).
 // dq: [n_out][2][L][N] rescaled d0, d1; digits: [n_out][ell][N] of rescaled d2.
+// The smallest size class is held to 64 registers (eight 128-thread CTAs per
+// SM, a few bytes spilled): measured faster than 66 registers and seven CTAs.
 template <int LM, int KM, int MW>
-__global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K, int N,
+__global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u64 *__restrict__ d, int n_out, int L, int K, int N,
                                                      int ell, int base_log2, u64 *__restrict__ dq,
                                                      uint32_t *__restrict__ digits, const ModDev *__restrict__ mods,
                                                      const ExactDev *__restrict__ E) {
@@ -147,7 +202,7 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
 #pragma unroll
         for (int k = 0; k < KM; k++)
             if (k < K)
-                rc[k] = conv_to<LM>(y, L, E->QhatBc[k], E->QhatBcs[k], (u64)v, E->Q_bc[k], E->Q_bcs[k], mods[L + k].q);
+                rc[k] = conv_to_m<LM>(y, L, E->QhatBcm[k], (u64)v, E->Q_bc[k], E->Q_bcs[k], mods[L + k]);
     } else {
         u64 R[MW];
         crt_compose<MW>(Q, y, R);
@@ -172,8 +227,7 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
     // centred F mod q_i; for the digit component (j = 2) directly its CRT
     // residue F inv_i mod q_i (the constants carry the inv_i factor)
     const bool dig = j == 2;
-    const u64(*H)[MAXP] = dig ? E->BhatQi : E->BhatQ;
-    const u64(*Hs)[MAXP] = dig ? E->BhatQis : E->BhatQs;
+    const u64(*H)[MAXP] = dig ? E->BhatQim : E->BhatQm;
     const u64 *Bq = dig ? E->B_qi : E->B_q;
     const u64 *Bqs = dig ? E->B_qis : E->B_qs;
     u64 f[LM];
@@ -181,7 +235,7 @@ __global__ void __launch_bounds__(128) k_scale_round(const u64 *__restrict__ d, 
         const u64 k = (u64)v + (fr >= (1ull << 57));
 #pragma unroll
         for (int i = 0; i < LM; i++)
-            if (i < L) f[i] = conv_to<KM>(yb, K, H[i], Hs[i], k, Bq[i], Bqs[i], mods[i].q);
+            if (i < L) f[i] = conv_to_m<KM>(yb, K, H[i], k, Bq[i], Bqs[i], mods[i]);
     } else {
         u64 F[MW];
         crt_compose<MW>(B, yb, F);

@@ -64,9 +64,11 @@ struct ExactDev {
     CrtDev B;                 // auxiliary basis for the tensor product
     ConvDev Qc, Bc;           // overflow estimates over Q and over B
     // base-conversion tables with Shoup companions:
-    // QhatB[j][i] = (Q / q_i) mod b_j, BhatQ[i][j] = (B / b_j) mod q_i, Qhat_t[i] = (Q / q_i) mod t
-    u64 QhatB[MAXP][MAXP], QhatBs[MAXP][MAXP];
-    u64 BhatQ[MAXP][MAXP], BhatQs[MAXP][MAXP];
+    // QhatB[j][i] = (Q / q_i) mod b_j, BhatQ[i][j] = (B / b_j) mod q_i, Qhat_t[i] = (Q / q_i) mod t;
+    // the ...m tables hold the same values times 2^64 (Montgomery form, for
+    // sums of products ended by one Montgomery reduction)
+    u64 QhatB[MAXP][MAXP], QhatBm[MAXP][MAXP];
+    u64 BhatQ[MAXP][MAXP], BhatQm[MAXP][MAXP];
     u64 Qhat_t[MAXP], Qhat_ts[MAXP];
     u64 Q_bs[MAXP], B_qs[MAXP];  // Shoup companions of Q mod b_j and B mod q_i
     u64 Q_t, Q_ts;               // Q mod t
@@ -85,8 +87,8 @@ struct ExactDev {
     //   BhatQi[i][j] = (B/b_j) inv_i, B_qi[i] = B inv_i           (mod q_i)
     u64 f_tq[MAXP], f_tqs[MAXP], f_hq[MAXP];
     u64 f_tb[MAXP], f_tbs[MAXP], f_hb[MAXP], f_cb[MAXP], f_cbs[MAXP];
-    u64 QhatBc[MAXP][MAXP], QhatBcs[MAXP][MAXP], Q_bc[MAXP], Q_bcs[MAXP];
-    u64 BhatQi[MAXP][MAXP], BhatQis[MAXP][MAXP], B_qi[MAXP], B_qis[MAXP];
+    u64 QhatBc[MAXP][MAXP], QhatBcm[MAXP][MAXP], Q_bc[MAXP], Q_bcs[MAXP];
+    u64 BhatQi[MAXP][MAXP], BhatQim[MAXP][MAXP], B_qi[MAXP], B_qis[MAXP];
 };
 
 }  // namespace he
@@ -301,6 +303,16 @@ int launch_import_sk(he_ctx *c, const int64_t *sk, int8_t *s8, int *bad, cudaStr
 int launch_check_residues(he_ctx *c, const u64 *a, long long n_polys, int *bad, cudaStream_t st);
 int launch_sample(he_ctx *c, int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_obj, int n_limbs,
                   void *out, cudaStream_t st);
+// several sample jobs (each as for launch_sample) in one launch
+struct SampleJob {
+    int kind;
+    uint32_t tag, idx0;
+    int n_obj, n_limbs;
+    uint64_t seed;
+    void *out;
+};
+constexpr int kMaxSampleJobs = 12;
+int launch_sample_multi(he_ctx *c, const SampleJob *jobs, int n, cudaStream_t st);
 
 int launch_base_extend(he_ctx *c, const u64 *src, long long n_polys, u64 *dst_aux, cudaStream_t st);
 int launch_scale_round(he_ctx *c, const u64 *d, int n_out, u64 *dq, uint32_t *digits, cudaStream_t st);

@@ -343,7 +343,7 @@ int build_tables(he_ctx *c, std::string &err) {
         for (int i = 0; i < c->L; i++) {
             u64 r;
             E.QhatB[j][i] = Q.div(c->q[i], &r).mod(b);
-            E.QhatBs[j][i] = shoup_c(E.QhatB[j][i], b);
+            E.QhatBm[j][i] = mulmod(E.QhatB[j][i], (u64)(((u128)1 << 64) % b), b);
         }
         E.Q_bs[j] = shoup_c(E.Q_b[j], b);
     }
@@ -352,7 +352,7 @@ int build_tables(he_ctx *c, std::string &err) {
         for (int j = 0; j < c->K; j++) {
             u64 r;
             E.BhatQ[i][j] = Bp.div(c->aux[j], &r).mod(q);
-            E.BhatQs[i][j] = shoup_c(E.BhatQ[i][j], q);
+            E.BhatQm[i][j] = mulmod(E.BhatQ[i][j], (u64)(((u128)1 << 64) % q), q);
         }
         E.B_qs[i] = shoup_c(E.B_q[i], q);
         u64 r;
@@ -374,7 +374,7 @@ int build_tables(he_ctx *c, std::string &err) {
         E.f_hq[i] = mulmod(E.Qhalf_q[i], inv, q);
         for (int j = 0; j < c->K; j++) {
             E.BhatQi[i][j] = mulmod(E.BhatQ[i][j], inv, q);
-            E.BhatQis[i][j] = shoup_c(E.BhatQi[i][j], q);
+            E.BhatQim[i][j] = mulmod(E.BhatQi[i][j], (u64)(((u128)1 << 64) % q), q);
         }
         E.B_qi[i] = mulmod(E.B_q[i], inv, q);
         E.B_qis[i] = shoup_c(E.B_qi[i], q);
@@ -388,7 +388,7 @@ int build_tables(he_ctx *c, std::string &err) {
         E.f_hb[j] = mulmod(E.Qhalf_b[j], cj, b);
         for (int i = 0; i < c->L; i++) {
             E.QhatBc[j][i] = mulmod(E.QhatB[j][i], cj, b);
-            E.QhatBcs[j][i] = shoup_c(E.QhatBc[j][i], b);
+            E.QhatBcm[j][i] = mulmod(E.QhatBc[j][i], (u64)(((u128)1 << 64) % b), b);
         }
         E.Q_bc[j] = mulmod(E.Q_b[j], cj, b);
         E.Q_bcs[j] = shoup_c(E.Q_bc[j], b);
