@@ -61,6 +61,39 @@ __device__ __forceinline__ u64 shoup_small(uint32_t k, u64 w, u64 ws, u64 q) {
     const u64 qh = ((u64)k * (uint32_t)(ws >> 32) + __umulhi(k, (uint32_t)ws)) >> 32;
     return (u64)k * w - (u64)(uint32_t)qh * q;  // [0, 2q)
 }
+// The same product with a coarser quotient: h = a1 s1 + floor(a0 s1 / 2^32)
+// + floor(a1 s0 / 2^32), two high-half multiplies instead of two wide ones.
+// The three dropped fractions sum to below 3, so h is at most 2 below
+// floor(a w' / 2^64) and the result lies in [0, 4q) for every 64-bit a.
+__device__ __forceinline__ u64 shoup4(u64 a, u64 w, u64 ws, u64 nq) {
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, s0, s1, w0, w1, n0, n1, t1, c, z, h0, h1, l0, l1;\n\t"
+        ".reg .u64 x, h, l;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.hi.u32 t1, a0, s1;\n\t"
+        "mad.hi.cc.u32 c, a1, s0, t1;\n\t"
+        "addc.u32 z, 0, 0;\n\t"
+        "mov.b64 x, {c, z};\n\t"
+        "mad.wide.u32 h, a1, s1, x;\n\t"
+        "mov.b64 {h0, h1}, h;\n\t"
+        "mul.wide.u32 l, a0, w0;\n\t"
+        "mad.wide.u32 l, h0, n0, l;\n\t"
+        "mul.lo.u32 c, a0, w1;\n\t"
+        "mad.lo.u32 c, a1, w0, c;\n\t"
+        "mad.lo.u32 c, h0, n1, c;\n\t"
+        "mad.lo.u32 c, h1, n0, c;\n\t"
+        "mov.b64 {l0, l1}, l;\n\t"
+        "add.u32 l1, l1, c;\n\t"
+        "mov.b64 %0, {l0, l1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(a), "l"(w), "l"(ws), "l"(nq));
+    return r;
+}
 __device__ __forceinline__ u64 red1(u64 a, u64 q) { return a >= q ? a - q : a; }
 __device__ __forceinline__ u64 addm(u64 a, u64 b, u64 q) { return red1(a + b, q); }   // a,b < q
 __device__ __forceinline__ u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
