@@ -106,6 +106,10 @@ typedef struct he_params {
     int32_t device;
     double max_ccmul_scratch_bytes;  /* per-call CCMul scratch; larger calls run in chunks of
                                         outputs (0: 4 GiB) */
+    double max_table_cache_bytes;    /* device copies of term tables kept between calls (they
+                                        are reused by calls of the same shape); once above this,
+                                        the next call synchronises the device and frees them
+                                        (0: 256 MiB) */
 } he_params;
 
 /* Read-only description of a context (filled by he_ctx_query). */

@@ -69,6 +69,7 @@ static const void *cached_table(he_ctx *c, const void *data, size_t bytes, int *
     e = cudaMemcpy(d, data, bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); *rc = cuda_check(c, e, "table upload"); return nullptr; }
     c->table_cache.emplace(std::move(key), d);
+    c->table_cache_bytes += bytes;
     *rc = HE_OK;
     return d;
 }
@@ -142,7 +143,23 @@ static FwdJob fwd_job() {
         if (_rc != HE_OK) return _rc; \
     } while (0)
 
-static int set_device(he_ctx *c) { return cuda_check(c, cudaSetDevice(c->P.device), "cudaSetDevice"); }
+// Start of a call: select the context's device, and drop the cached term
+// tables once they exceed their budget.  No call holds a cached pointer from
+// an earlier call, and the synchronisation waits for the kernels that read
+// them.
+static int set_device(he_ctx *c) {
+    int rc = cuda_check(c, cudaSetDevice(c->P.device), "cudaSetDevice");
+    if (rc) return rc;
+    const size_t cap = c->P.max_table_cache_bytes > 0 ? (size_t)c->P.max_table_cache_bytes : (size_t)256 << 20;
+    if (c->table_cache_bytes > cap) {
+        rc = cuda_check(c, cudaDeviceSynchronize(), "sync before dropping cached tables");
+        if (rc) return rc;
+        for (auto &kv : c->table_cache) cudaFree(kv.second);
+        c->table_cache.clear();
+        c->table_cache_bytes = 0;
+    }
+    return HE_OK;
+}
 
 }  // namespace he
 

@@ -112,6 +112,7 @@ struct he_ctx {
     size_t ws_size = 0;
     // small host->device tables cached by content
     std::unordered_map<std::string, void *> table_cache;
+    size_t table_cache_bytes = 0;
     std::string err;
     // launch tracing
     bool trace = false;

@@ -245,6 +245,7 @@ int build_tables(he_ctx *c, std::string &err) {
     if (P.eta < 1 || P.eta > 32) { err = "eta out of range"; return HE_ERR_INVALID_ARG; }
     if (P.max_ccmul_group < 1) { err = "max_ccmul_group out of range"; return HE_ERR_INVALID_ARG; }
     if (!(P.max_ccmul_scratch_bytes >= 0)) { err = "max_ccmul_scratch_bytes out of range"; return HE_ERR_INVALID_ARG; }
+    if (!(P.max_table_cache_bytes >= 0)) { err = "max_table_cache_bytes out of range"; return HE_ERR_INVALID_ARG; }
     c->N = N;
     c->logN = 0;
     while ((1 << c->logN) < N) c->logN++;

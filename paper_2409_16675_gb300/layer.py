@@ -26,11 +26,13 @@ ENC = {"conv": nv.HE_ENC_CONVENTIONAL, "corr": nv.HE_ENC_CORRELATED}
 class Context:
     """A he_ctx for one ring."""
 
-    def __init__(self, spec: RingSpec, device: int = 0, max_ccmul_group: int = 64, max_ccmul_scratch_bytes: float = 0):
+    def __init__(self, spec: RingSpec, device: int = 0, max_ccmul_group: int = 64, max_ccmul_scratch_bytes: float = 0,
+                 max_table_cache_bytes: float = 0):
         self.spec = spec
         self.params = nv.make_params(spec.N, prime_bits=spec.prime_bits, t=spec.t, base_log2=spec.base_log2,
                                      eta=spec.eta, max_ccmul_group=max_ccmul_group, device=device,
-                                     max_ccmul_scratch_bytes=max_ccmul_scratch_bytes)
+                                     max_ccmul_scratch_bytes=max_ccmul_scratch_bytes,
+                                     max_table_cache_bytes=max_table_cache_bytes)
         self.h = nv.he_setup(self.params)
         self.info = nv.he_ctx_query(self.h)
         self.N, self.L, self.t = spec.N, spec.L, spec.t

@@ -38,7 +38,7 @@ class he_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int32), ("prime_bits", ctypes.c_int32 * HE_MAX_LIMBS),
                 ("q", ctypes.c_uint64 * HE_MAX_LIMBS), ("t", ctypes.c_uint64), ("base_log2", ctypes.c_int32),
                 ("eta", ctypes.c_int32), ("max_ccmul_group", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("max_ccmul_scratch_bytes", ctypes.c_double)]
+                ("max_ccmul_scratch_bytes", ctypes.c_double), ("max_table_cache_bytes", ctypes.c_double)]
 
 
 class he_ctx_info(ctypes.Structure):
@@ -176,7 +176,7 @@ def _check(rc, ctx=None):
 
 
 def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=21, max_ccmul_group=64, device=0,
-                max_ccmul_scratch_bytes=0.0):
+                max_ccmul_scratch_bytes=0.0, max_table_cache_bytes=0.0):
     p = he_params()
     p.N = N
     if q:
@@ -189,6 +189,7 @@ def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=2
             p.prime_bits[i] = b
     p.t, p.base_log2, p.eta, p.max_ccmul_group, p.device = t, base_log2, eta, max_ccmul_group, device
     p.max_ccmul_scratch_bytes = float(max_ccmul_scratch_bytes)
+    p.max_table_cache_bytes = float(max_table_cache_bytes)
     return p
 
 

@@ -46,3 +46,37 @@ def test_setup_rejects_bad_params_without_touching_a_gpu():
     h = ctypes.c_void_p()
     rc = native.lib.he_setup(None, ctypes.byref(h))
     assert rc == -1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """sizeof and every field offset of the header's public structs, printed
+    by a C program compiled against include/cryptotrain.h, equal those of the
+    ctypes mirrors in the binding."""
+    import shutil
+    import subprocess
+    from paper_2409_16675_gb300 import native
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cc or not os.path.isdir(cuda_inc):
+        import pytest
+        pytest.skip("needs gcc and the CUDA headers")
+    structs = [native.he_params, native.he_ctx_info, native.he_conv_shape, native.he_plan_info,
+               native.he_batch_tuning, native.he_server_config, native.he_server_report, native.he_trace_entry]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cryptotrain.h"', "int main(void) {"]
+    for S in structs:
+        n = S.__name__
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (n, n))
+        for f in S._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (n, f[0], n, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, str(src), "-o", str(exe), "-I", os.path.join(ROOT, "include"), "-I", cuda_inc], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for S in structs:
+        n = S.__name__
+        assert int(got[n + " sizeof"]) == ctypes.sizeof(S), n
+        for f in S._fields_:
+            assert int(got["%s %s" % (n, f[0])]) == getattr(S, f[0]).offset, (n, f[0])

@@ -284,6 +284,31 @@ def test_ccmul_in_chunks_gives_the_same_bits():
     small.close()
 
 
+def test_table_cache_budget_gives_the_same_bits():
+    """A context whose term-table cache budget is one byte drops its cached
+    tables (after a device synchronisation) at the start of every call; two
+    layer steps on it give the bits of the same steps on a default context."""
+    c = ctx_for("n4096")
+    tiny = layer.Context(c.spec, max_table_cache_bytes=1.0)
+    shape = wl.ConvShape(3, 16, 16, 6, 3, 1)
+    outs = []
+    for ctx in (c, tiny):
+        keys = layer.Keys(ctx, 16, True)
+        plan = layer.Plan(ctx, shape, "conv")
+        pl = layer.PLayer(ctx, keys, plan, 2)
+        x = torch.from_numpy(wl.activations(17, (2, 3, 16, 16))).cuda()
+        w = torch.from_numpy(wl.weights(18, (6, 3, 3, 3))).cuda()
+        for step in range(2):
+            y = pl.step(x, w, wl.protocol_seeds(19 + step))
+            outs.append((to_np(pl.buf.rr), to_np(pl.buf.out), to_np(y)))
+        keys.close()
+        plan.close()
+    for a, b in zip(outs[:2], outs[2:]):
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)
+    tiny.close()
+
+
 @pytest.mark.parametrize("name", ["n1024", "n8192", "n2048_t40"])
 def test_ppmul_bits(name):
     c = ctx_for(name)
