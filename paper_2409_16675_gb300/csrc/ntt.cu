@@ -13,8 +13,8 @@
 // butterflies with the approximate-quotient Shoup product built from 32-bit
 // multiply-accumulates (twiddle product in [0, 3q) in the forward transform;
 // in [0, 4q) in the inverse, whose coarser quotient takes two high-half
-// multiplies instead of two wide ones: measured 2.6% faster there, while the
-// forward transform spilled and lost 1.8%); the butterfly adds 4q to
+// multiplies instead of two wide ones: measured 2.6% faster there, while in
+// the forward transform it raised the spills and lost 1.8%); the butterfly adds 4q to
 // the difference, so values grow by at most 4q per stage: with every modulus
 // of a launch below 2^57 they stay below 57q < 2^63 through 14 stages and the
 // LAZY variants make no correction inside the transform; otherwise X is
