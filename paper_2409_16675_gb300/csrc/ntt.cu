@@ -11,10 +11,11 @@
 // followed by the untwist psi^-e N^-1 (times 2^64, which undoes the Montgomery
 // reduction ending the multiply-accumulate).  Both use Harvey-style lazy
 // butterflies with the approximate-quotient Shoup product built from 32-bit
-// multiply-accumulates (twiddle product in [0, 3q) in the forward transform;
-// in [0, 4q) in the inverse, whose coarser quotient takes two high-half
-// multiplies instead of two wide ones: measured 2.6% faster there, while in
-// the forward transform it raised the spills and lost 1.8%); the butterfly adds 4q to
+// multiply-accumulates (twiddle product in [0, 4q) in the inverse and, for
+// N <= 4096, in the forward transform: a coarser quotient from two high-half
+// multiplies instead of two wide ones, measured 2.6% faster in the inverse;
+// in [0, 3q) in the forward transform at N >= 8192, where the coarser one
+// raised the spills under 64 registers and lost 1.8%); the butterfly adds 4q to
 // the difference, so values grow by at most 4q per stage: with every modulus
 // of a launch below 2^57 they stay below 57q < 2^63 through 14 stages and the
 // LAZY variants make no correction inside the transform; otherwise X is
@@ -56,6 +57,9 @@ struct Cfg {
     // resident CTAs per SM the register budget targets (64 registers per
     // thread at N = 8192; N = 16384 runs one 1024-thread CTA per SM)
     static constexpr int MINB = LOGN >= 14 ? 1 : 2;
+    // the forward transform takes the coarser Shoup quotient only where the
+    // register budget leaves room for it (128 registers per thread)
+    static constexpr bool COARSE_FWD = LOGN <= 12;
 };
 
 // one pad word per R elements: exchanges are conflict-free for every window
@@ -71,7 +75,7 @@ __device__ __forceinline__ int jidx(int tau, int k, int lo) {
 // Forward pass: S stages on register bits S-1 .. 0 of the window starting at
 // element bit lo (stage s0 + st acts on bit lo + S - 1 - st); the twiddle of
 // the pair whose lower element is j is fw[2^s + (j >> (bit + 1))].
-template <int RB, int S, bool LAZY>
+template <int RB, int S, bool LAZY, bool COARSE>
 __device__ __forceinline__ void fwd_pass(u64 (&v)[1 << RB], int tau, int lo, int s0, const ModDev &M) {
     constexpr int R = 1 << RB;
     const u64 q4 = 2 * M.twoq, nq = M.nq;
@@ -88,7 +92,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&v)[1 << RB], int tau, int lo, int
             u64 X = v[k];
             const u64 Y = v[k | (1 << kb)];
             if (!LAZY) X = X >= q4 ? X - q4 : X;
-            const u64 Tt = shoup3(Y, Wp.x, Wp.y, nq);
+            const u64 Tt = COARSE ? shoup4(Y, Wp.x, Wp.y, nq) : shoup3(Y, Wp.x, Wp.y, nq);
             v[k] = X + Tt;
             v[k | (1 << kb)] = X - Tt + q4;
         }
@@ -188,12 +192,12 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 
     int lo = LOGN - RB;
 #pragma unroll
     for (int pass = 0; pass < NP - 1; pass++) {
-        fwd_pass<RB, RB, LAZY>(v, tau, lo, RB * pass, M);
+        fwd_pass<RB, RB, LAZY, Cfg<LOGN>::COARSE_FWD>(v, tau, lo, RB * pass, M);
         const int lo_next = pass == NP - 2 ? 0 : lo - RB;
         exchange<RB>(sm, v, tau, lo, lo_next);
         lo = lo_next;
     }
-    fwd_pass<RB, RL, LAZY>(v, tau, 0, RB * (NP - 1), M);
+    fwd_pass<RB, RL, LAZY, Cfg<LOGN>::COARSE_FWD>(v, tau, 0, RB * (NP - 1), M);
 #pragma unroll
     for (int k = 0; k < R; k++) d[k * T + tau] = reduce_small(v[k], M);  // from [0, 57q) or [0, 8q)
 }
