@@ -42,6 +42,7 @@ RINGS = {
     "n4096_3x36": wl.RING_SMALL,
     "n2048_6x60": wl.RingSpec(2048, (60,) * 6, 65537),
     "n2048_t40": wl.RingSpec(2048, (50, 50, 50), 1099511480321),
+    "n1024_12x40": wl.RingSpec(1024, (40,) * 12, 65537),  # the largest kernel size class (L > 8)
 }
 WINDOW = Fraction(1, 2 ** 50)
 
