@@ -27,6 +27,10 @@
  *      secret key  int64  [N] in {-1, 0, 1}
  *      public key  uint64 [2][L][N] = (b, a), b = -(a s + e)
  *      relin key   uint64 [ell][2][L][N], rlk_j = (-(a_j s + e_j) + 2^(base*j) s^2, a_j)
+ *  - Keys are bound to the parameters (he_ctx_fingerprint) of the context
+ *    that made them, and a plan to its ring degree N: a call given keys of
+ *    a context with other parameters, or a plan of another N, fails with
+ *    HE_ERR_INVALID_ARG before any device work.
  *  - All arithmetic is exact integer arithmetic; results are bit-identical
  *    to the CPU oracle for the same seeds.
  */

@@ -147,6 +147,31 @@ static FwdJob fwd_job() {
 // tables once they exceed their budget.  No call holds a cached pointer from
 // an earlier call, and the synchronisation waits for the kernels that read
 // them.
+// 64-bit FNV-1a over every parameter that fixes the arithmetic of a context
+static uint64_t params_fingerprint(const he_ctx *c) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; i++) { h ^= (v >> (8 * i)) & 0xff; h *= 1099511628211ull; }
+    };
+    mix((uint64_t)c->N); mix((uint64_t)c->L); mix(c->P.t); mix((uint64_t)c->P.base_log2); mix((uint64_t)c->P.eta);
+    mix((uint64_t)c->ell); mix((uint64_t)c->K);
+    for (u64 q : c->q) mix(q);
+    for (u64 b : c->aux) mix(b);
+    return h;
+}
+
+// Keys and plans carry the parameters they were made for; a call refuses
+// those of another ring (their buffers have other sizes) or other primes.
+static int check_keys(he_ctx *c, const he_keys *k) {
+    if (k->fp != c->fp || k->N != c->N || k->L != c->L)
+        return fail(c, HE_ERR_INVALID_ARG, "keys were made for a context with other parameters");
+    return HE_OK;
+}
+static int check_plan(he_ctx *c, const he_plan *p) {
+    if (p->N != c->N) return fail(c, HE_ERR_INVALID_ARG, "plan of another ring degree");
+    return HE_OK;
+}
+
 static int set_device(he_ctx *c) {
     int rc = cuda_check(c, cudaSetDevice(c->P.device), "cudaSetDevice");
     if (rc) return rc;
@@ -178,6 +203,7 @@ int he_setup(const he_params *params, he_ctx **ctx) {
         rc = build_tables(c, err);
         if (rc != HE_OK && c->err.empty()) c->err = err;
     }
+    if (rc == HE_OK) c->fp = params_fingerprint(c);
     if (rc != HE_OK) {
         std::lock_guard<std::mutex> g(g_setup_mu);
         g_setup_err = c->err;
@@ -235,7 +261,7 @@ int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStrea
     const int N = c->N, L = c->L, ell = with_relin ? c->ell : 0;
     const size_t LN = (size_t)L * N;
     he_keys *k = new he_keys();
-    k->L = L; k->N = N; k->ell = ell;
+    k->L = L; k->N = N; k->ell = ell; k->device = c->P.device; k->fp = c->fp;
     auto alloc = [&](u64 **p, size_t n) { return cudaMalloc((void **)p, n * 8) == cudaSuccess; };
     if (!alloc(&k->sk, N) || !alloc(&k->s_ntt, LN) || !alloc(&k->pk, 2 * LN) || !alloc(&k->pk_ntt, 2 * LN) ||
         (ell && (!alloc(&k->rlk, (size_t)ell * 2 * LN) || !alloc(&k->rlk_ntt, (size_t)ell * 2 * LN)))) {
@@ -321,7 +347,7 @@ int he_keys_import(he_ctx *c, const int64_t *sk, const uint64_t *pk, const uint6
     const int N = c->N, L = c->L, ell = rlk ? c->ell : 0;
     const size_t LN = (size_t)L * N;
     he_keys *k = new he_keys();
-    k->L = L; k->N = N; k->ell = ell;
+    k->L = L; k->N = N; k->ell = ell; k->device = c->P.device; k->fp = c->fp;
     auto alloc = [&](u64 **p, size_t n) { return cudaMalloc((void **)p, n * 8) == cudaSuccess; };
     if (!alloc(&k->sk, N) || !alloc(&k->s_ntt, LN) || !alloc(&k->pk, 2 * LN) || !alloc(&k->pk_ntt, 2 * LN) ||
         (ell && (!alloc(&k->rlk, (size_t)ell * 2 * LN) || !alloc(&k->rlk_ntt, (size_t)ell * 2 * LN)))) {
@@ -369,23 +395,15 @@ int he_keys_import(he_ctx *c, const int64_t *sk, const uint64_t *pk, const uint6
     return HE_OK;
 }
 
-// 64-bit FNV-1a over every parameter that fixes the arithmetic of a context
 int he_ctx_fingerprint(const he_ctx *c, uint64_t *fp) {
     if (!c || !fp) return HE_ERR_INVALID_ARG;
-    uint64_t h = 1469598103934665603ull;
-    auto mix = [&](uint64_t v) {
-        for (int i = 0; i < 8; i++) { h ^= (v >> (8 * i)) & 0xff; h *= 1099511628211ull; }
-    };
-    mix((uint64_t)c->N); mix((uint64_t)c->L); mix(c->P.t); mix((uint64_t)c->P.base_log2); mix((uint64_t)c->P.eta);
-    mix((uint64_t)c->ell); mix((uint64_t)c->K);
-    for (u64 q : c->q) mix(q);
-    for (u64 b : c->aux) mix(b);
-    *fp = h;
+    *fp = c->fp;
     return HE_OK;
 }
 
 int he_keys_destroy(he_keys *k) {
     if (!k) return HE_OK;
+    cudaSetDevice(k->device);
     cudaDeviceSynchronize();
     u64 *ps[] = {k->sk, k->s_ntt, k->pk, k->pk_ntt, k->rlk, k->rlk_ntt};
     for (u64 *p : ps)
@@ -396,6 +414,7 @@ int he_keys_destroy(he_keys *k) {
 
 int he_keys_export(he_ctx *c, const he_keys *k, int which, void *dst, cudaStream_t st) {
     if (!c || !k || !dst) return HE_ERR_INVALID_ARG;
+    TRY(check_keys(c, k));
     TRY(set_device(c));
     const size_t LN = (size_t)c->L * c->N;
     const void *src;
@@ -416,6 +435,7 @@ int he_keys_export(he_ctx *c, const he_keys *k, int which, void *dst, cudaStream
 static int encrypt_groups(he_ctx *c, const he_keys *k, int n_groups, const uint64_t *const *pts, const int *counts,
                           const uint64_t *seeds, uint64_t *const *cts, cudaStream_t st) {
     if (!c || !k || n_groups < 1 || n_groups > 4 || !pts || !counts || !seeds || !cts) return HE_ERR_INVALID_ARG;
+    TRY(check_keys(c, k));
     int n = 0;
     for (int g = 0; g < n_groups; g++) {
         if (counts[g] < 0 || (counts[g] && (!pts[g] || !cts[g]))) return HE_ERR_INVALID_ARG;
@@ -487,6 +507,7 @@ int he_encrypt_many(he_ctx *c, const he_keys *k, int n_groups, const uint64_t *c
 int he_encrypt_symmetric(he_ctx *c, const he_keys *k, const uint64_t *pt, int n, uint64_t seed, uint64_t *c0,
                          cudaStream_t st) {
     if (!c || !k || n < 0 || (n && (!pt || !c0))) return HE_ERR_INVALID_ARG;
+    TRY(check_keys(c, k));
     if (!n) return HE_OK;
     TRY(set_device(c));
     const int N = c->N, L = c->L;
@@ -531,6 +552,7 @@ int he_expand_symmetric(he_ctx *c, uint64_t seed, int n, const uint64_t *c0, uin
 
 int he_decrypt(he_ctx *c, const he_keys *k, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t st) {
     if (!c || !k || n < 0 || (n && (!pt || !ct))) return HE_ERR_INVALID_ARG;
+    TRY(check_keys(c, k));
     if (!n) return HE_OK;
     TRY(set_device(c));
     const int N = c->N, L = c->L;
@@ -594,6 +616,7 @@ int he_plan_query(const he_plan *p, he_plan_info *info) {
 static int encode_common(he_ctx *c, const he_plan *p, int enc, int role, const void *tensor, int dtype, int batch,
                          uint64_t *polys, cudaStream_t st) {
     if (!c || !p || !tensor || !polys) return HE_ERR_INVALID_ARG;
+    TRY(check_plan(c, p));
     if (p->info.encoding != enc) return fail(c, HE_ERR_INVALID_ARG, "plan encoding does not match the encoder");
     if (dtype != HE_DTYPE_U8 && dtype != HE_DTYPE_I8 && dtype != HE_DTYPE_I64) return fail(c, HE_ERR_INVALID_ARG, "bad dtype");
     TRY(set_device(c));
@@ -622,6 +645,7 @@ int he_cpmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x, 
                   const uint64_t *ct_w, const uint64_t *pt_x, const uint64_t *ct_add, uint64_t *ct_out,
                   cudaStream_t st) {
     if (!c || !p || batch < 0 || !ct_out || (!ct_x && !ct_w)) return HE_ERR_INVALID_ARG;
+    TRY(check_plan(c, p));
     if ((ct_x && !pt_w) || (ct_w && !pt_x)) return fail(c, HE_ERR_INVALID_ARG, "missing plaintext operand");
     if (!batch) return HE_OK;
     TRY(set_device(c));
@@ -681,6 +705,7 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     if (!c || !k || !ct_a || !ct_b || !pair_a || !pair_b || !ct_out || n_a < 1 || n_b < 1 || n_pairs < 0 ||
         group < 1 || n_pairs % group)
         return HE_ERR_INVALID_ARG;
+    TRY(check_keys(c, k));
     if (!k->rlk_ntt) return fail(c, HE_ERR_INVALID_ARG, "keys have no relinearisation key");
     if (group > c->P.max_ccmul_group) return fail(c, HE_ERR_INVALID_ARG, "group exceeds max_ccmul_group");
     for (int i = 0; i < n_pairs; i++)
@@ -765,7 +790,9 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
 
 int he_ccmul_conv_precompute(he_ctx *c, const he_keys *k, const he_plan *p, int batch, const uint64_t *ct_rx,
                              const uint64_t *ct_rw, uint64_t *ct_out, cudaStream_t st) {
-    if (!c || !p || batch < 0) return HE_ERR_INVALID_ARG;
+    if (!c || !p || !k || batch < 0) return HE_ERR_INVALID_ARG;
+    TRY(check_plan(c, p));
+    TRY(check_keys(c, k));
     if (!batch) return HE_OK;
     const int T = p->info.T, G = p->info.G, M = p->info.MG;
     std::vector<int32_t> pa, pb;
@@ -783,6 +810,7 @@ int he_ccmul_conv_precompute(he_ctx *c, const he_keys *k, const he_plan *p, int 
 int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, const uint64_t *pt_w, uint64_t *out,
                   cudaStream_t st) {
     if (!c || !p || batch < 0 || (batch && (!pt_x || !pt_w || !out))) return HE_ERR_INVALID_ARG;
+    TRY(check_plan(c, p));
     if (c->t_mod < 0) return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "t is not an NTT prime for this N");
     if (!batch) return HE_OK;
     TRY(set_device(c));
@@ -817,6 +845,7 @@ int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, 
 int he_decode(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt, const uint64_t *sub, int64_t *out,
               cudaStream_t st) {
     if (!c || !p || batch < 0 || (batch && (!pt || !out))) return HE_ERR_INVALID_ARG;
+    TRY(check_plan(c, p));
     TRY(set_device(c));
     return launch_decode(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.MG * p->info.T, batch, pt, sub, out,
                          st);
@@ -825,7 +854,7 @@ int he_decode(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt, const 
 int he_encode_output(he_ctx *c, const he_plan *p, int batch, const int64_t *values, uint64_t *polys,
                      cudaStream_t st) {
     if (!c || !p || batch < 0 || (batch && (!values || !polys))) return HE_ERR_INVALID_ARG;
-    if (p->N != c->N) return fail(c, HE_ERR_INVALID_ARG, "plan of another ring");
+    TRY(check_plan(c, p));
     TRY(set_device(c));
     return launch_encode_output(c, p->out_map, p->info.Ho * p->info.Wo, p->s.M, p->info.MG * p->info.T, batch, values,
                                 polys, st);

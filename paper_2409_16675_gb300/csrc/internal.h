@@ -95,6 +95,7 @@ struct ExactDev {
 
 struct he_ctx {
     he_params P;
+    uint64_t fp = 0;                      // parameter fingerprint (he_ctx_fingerprint)
     int N = 0, logN = 0, L = 0, K = 0;   // K auxiliary primes
     int n_mods = 0;                       // L + K (+1 if the t modulus is available)
     int t_mod = -1;                       // index of the t modulus in the table, -1 if PPMul unsupported
@@ -122,6 +123,8 @@ struct he_ctx {
 
 struct he_keys {
     int L = 0, ell = 0, N = 0;
+    int device = 0;
+    uint64_t fp = 0;         // fingerprint of the parameters the keys were made for
     u64 *sk = nullptr;       // int64 [N] (stored in u64 words)
     u64 *s_ntt = nullptr;    // [L][N] NTT form
     u64 *pk = nullptr;       // [2][L][N] coefficient form

@@ -35,6 +35,7 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
                                      const uint64_t *pt_w, const uint64_t *ct_w, const uint64_t *pt_x,
                                      const uint64_t *ct_add, uint64_t *ct_out, cudaStream_t st) {
     if (!c || !p || batch < 0 || !ct_out || (!ct_x && !ct_w)) return HE_ERR_INVALID_ARG;
+    if (p->N != c->N) return fail(c, HE_ERR_INVALID_ARG, "plan of another ring degree");
     if ((ct_x && !pt_w) || (ct_w && !pt_x)) return fail(c, HE_ERR_INVALID_ARG, "missing plaintext operand");
     if (!batch) return HE_OK;
     const int dev = c->P.device;

@@ -119,3 +119,48 @@ def test_largest_served_ring():
     keys.close()
     plan.close()
     c.close()
+
+
+def test_keys_and_plans_of_another_context_are_refused():
+    """Keys carry the parameter fingerprint of their context and plans their
+    ring degree: every call given foreign ones fails before any device work,
+    and the output buffers stay untouched."""
+    a = layer.Context(wl.RingSpec(1024, (40, 40), 65537))
+    b = layer.Context(wl.RingSpec(1024, (40, 45), 65537))   # same N and L, other primes
+    c = layer.Context(wl.RingSpec(2048, (40, 40), 65537))   # another ring degree
+    assert nv.he_ctx_fingerprint(a.h) != nv.he_ctx_fingerprint(b.h)
+    ka = layer.Keys(a, 3, True)
+    pa = layer.Plan(a, wl.ConvShape(2, 6, 6, 3, 3, 1), "corr")
+    for ctx in (b, c):
+        pt = ctx.u64(1, ctx.N)
+        pt.zero_()
+        out_ct = sentinel(ctx.ct(1))
+        out_pt = sentinel(ctx.u64(1, ctx.N))
+        calls = [
+            lambda: nv.he_encrypt(ctx.h, ka.h, pt, 1, 1, out_ct),
+            lambda: nv.he_encrypt_symmetric(ctx.h, ka.h, pt, 1, 1, out_ct),
+            lambda: nv.he_decrypt(ctx.h, ka.h, out_ct, 1, out_pt),
+            lambda: nv.he_ccmul_precompute(ctx.h, ka.h, out_ct, 1, out_ct, 1, [(0, 0)], 1, out_ct),
+        ]
+        if ctx is c:
+            calls += [
+                lambda: nv.he_cpmul_conv(ctx.h, pa.h, 1, out_ct, pt, None, None, None, out_ct),
+                lambda: nv.he_ppmul_conv(ctx.h, pa.h, 1, pt, pt, out_pt),
+                lambda: nv.he_encode_correlated(ctx.h, pa.h, nv.HE_ROLE_INPUT,
+                                                torch.zeros((1, 2, 6, 6), dtype=torch.uint8, device="cuda"), 1, out_pt),
+            ]
+        for call in calls:
+            with pytest.raises(nv.HEError):
+                call()
+        assert untouched(out_ct) and untouched(out_pt)
+    # the same objects still work on their own context
+    ct = a.ct(1)
+    m = torch.zeros((1, a.N), dtype=torch.uint64, device="cuda")
+    nv.he_encrypt(a.h, ka.h, m, 1, 1, ct)
+    back = a.u64(1, a.N)
+    nv.he_decrypt(a.h, ka.h, ct, 1, back)
+    assert not to_np(back.view(torch.int64)).any()
+    ka.close()
+    pa.close()
+    for ctx in (a, b, c):
+        ctx.close()
