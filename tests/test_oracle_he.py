@@ -141,6 +141,36 @@ def test_ccmul_bits_equal_bruteforce(bits, t):
     assert np.array_equal(got1[0], ccmul_bruteforce(P, K, ct, ct, [(ct[1], ct[3])]))
 
 
+@pytest.mark.parametrize("bits,t", [((36, 36, 36), 65537), ((50,) * 4, 1032193), ((60, 60), 17)])
+def test_ccmul_bits_equal_bruteforce_at_rounding_boundaries(bits, t):
+    """CCMul of a = (1, 1) with b = (b0, b1) gives d0 = b0, d1 = b0 + b1,
+    d2 = b1 exactly.  The coefficients of b are chosen where the rounding is
+    delicate: within a few units of Q/2 (the centred lift), with
+    [t d + floor(Q/2)]_Q within a few units of Q, and with the rounded
+    quotient equal to -1 and 0.  The result equals the big-integer brute force."""
+    P = he.Params(8, he.gen_primes(8, list(bits)), t)
+    K = he.keygen(P, 23, True)
+    Q = P.Q
+    h = Q // 2
+    tinv = pow(t, -1, Q)
+    near_q = [((Q - 1 - j - h) * tinv) % Q for j in range(2)]
+    neg_f = [(-((h + t - 1) // t) - j) % Q for j in (1, 2)]
+    b0 = [h - 1, h, h + 1, h + 2] + near_q + neg_f[:2]
+    b1 = neg_f[::-1] + [h + 1, h] + near_q[::-1] + [Q - 1, 0]
+    for v in neg_f:
+        vc = v if v <= h else v - Q
+        assert (t * vc + h) // Q == -1
+    one = np.zeros((P.L, 8), dtype=np.uint64)
+    one[:, 0] = 1
+    a = np.stack([one, one])[None]
+    b = np.zeros((1, 2, P.L, 8), dtype=np.uint64)
+    for i, qi in enumerate(P.q):
+        b[0, 0, i] = [v % qi for v in b0[:8]]
+        b[0, 1, i] = [v % qi for v in b1[:8]]
+    got = he.ccmul(P, K, a, b, [(0, 0)], group=1)
+    assert np.array_equal(got[0], ccmul_bruteforce(P, K, a, b, [(a[0], b[0])]))
+
+
 @pytest.mark.parametrize("N,bits,t", [(64, (50,) * 4, 1032193), (1024, (36,) * 3, 65537)])
 def test_ccmul_decrypts_to_product(N, bits, t):
     P = he.Params(N, he.gen_primes(N, list(bits)), t)
