@@ -3,9 +3,13 @@
 // floor((t d + floor(q/2)) / q) with digit decomposition, exact decryption,
 // and the encoding / decoding gathers.
 //
-// Exactness: every value is rebuilt as a multi-word integer by CRT (sum of
-// y_i * (M/m_i), then the overflow multiples of M subtracted), so no step is
-// an approximation.  The rescaling uses the identity
+// Exactness: a base conversion needs the CRT overflow count v = floor(sum_i
+// y_i / m_i) of its value; it is taken from a fixed-point estimate of that
+// sum, and wherever the estimate could be off (the sum within 64 ulps of an
+// integer, or of one half for a centred lift) the value is instead rebuilt as
+// a multi-word integer (sum of y_i * (M/m_i), overflow multiples of M
+// subtracted) and reduced directly, so no step is an approximation.  The
+// rescaling uses the identity
 //   floor((t d + h) / q) = (t d + h - r) / q,  r = [t d + h]_q, h = floor(q/2),
 // whose right side is an exact division, evaluated modulo each auxiliary
 // prime and brought back to Q by a second exact CRT (the quotient is smaller
