@@ -135,6 +135,14 @@ __device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[1 << RB], int tau, in
     __syncthreads();
 }
 
+// Work-list items: a launch whose moduli are not all below 2^57 is compiled
+// without the lazy bound (LAZY = false), yet each item whose own modulus is
+// below 2^57 still takes the lazy transform (the choice is uniform over a
+// block).  Measured on 256 uneven jobs with 36-60-bit limbs: 24.18 -> 23.51 ms.
+// The one-call grid kernels keep the launch-wide choice: there the second
+// inlined transform raised the spills and the plain per-job launches lost 1%.
+__device__ __forceinline__ bool lazy_mod(const ModDev &M) { return M.q < (1ull << 57); }
+
 // ---------------------------------------------------------------- per-polynomial building blocks
 // Load one limb polynomial into the first register window (bits [LOGN-4,
 // LOGN): element k*T + tau, coalesced), reducing / lifting it into [0, q).
@@ -375,7 +383,8 @@ __device__ __forceinline__ void mac_item(const MacItem *__restrict__ ip, u64 *sm
     u64 v[Cfg<LOGN>::R];
     mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, MINB)>(ip->A, ip->B, ip->ta, ip->tb, ip->t0, ip->t1, ip->limb, M, tau,
                                                         v, sm);
-    inv_transform<LOGN, LAZY>(v, sm, tau, M);
+    if (LAZY || lazy_mod(M)) inv_transform<LOGN, true>(v, sm, tau, M);
+    else inv_transform<LOGN, false>(v, sm, tau, M);
     u64 *out = ip->out;
     const u64 *add = ip->add;
     const u64 q = M.q;
@@ -395,7 +404,8 @@ __device__ __forceinline__ void fwd_item(const FwdItem *__restrict__ ip, u64 *sm
     const ModDev M = *mp;
     u64 v[Cfg<LOGN>::R];
     fwd_load<LOGN>(ip->kind, ip->src, ip->t, M, tau, v);
-    fwd_transform_store<LOGN, LAZY>(v, sm, tau, M, ip->dst);
+    if (LAZY || lazy_mod(M)) fwd_transform_store<LOGN, true>(v, sm, tau, M, ip->dst);
+    else fwd_transform_store<LOGN, false>(v, sm, tau, M, ip->dst);
 }
 
 template <typename ITEM>
