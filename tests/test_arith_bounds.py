@@ -123,3 +123,22 @@ def test_montgomery_conversion_chunk():
     the precondition of the conversion's Montgomery reduction."""
     for p in (1 << 20, (1 << 50) - 27, (1 << 61) - 1):
         assert 8 * ((1 << 61) - 1) * (p - 1) < (1 << 64) * p
+
+
+@pytest.mark.parametrize("bits", [20, 36, 50, 60, 61])
+def test_crt_overflow_estimate(bits):
+    """The overflow-count estimate: with m' = m << sh in [2^63, 2^64) and
+    c = floor(2^127 / m'), each term floor(floor((y << sh) c / 2^64) / 2^5)
+    is below y / m * 2^58 by less than 1.07 (so n terms by < 1.07 n < 64
+    ulps: the fallback window)."""
+    from fractions import Fraction
+    rng = random.Random(300 + bits)
+    m = primes_near([bits], 1, rng)[0]
+    sh = 64 - m.bit_length()
+    mp = m << sh
+    assert (1 << 63) <= mp < (1 << 64)
+    c = (1 << 127) // mp
+    for y in [0, 1, m - 1, m // 2, m // 2 + 1] + [rng.randrange(m) for _ in range(500)]:
+        term = (((y << sh) * c) >> 64) >> 5
+        err = Fraction(y, m) * (1 << 58) - term
+        assert 0 <= err < Fraction(107, 100)
