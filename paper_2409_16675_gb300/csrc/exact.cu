@@ -268,6 +268,14 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
     crt_compose<MW>(Q, y, X);
     const u64 dmask = (1ull << base_log2) - 1;
     uint32_t *dg = digits + (o * ell) * N + x;
+    if (base_log2 == 16) {  // the paper's base: four whole digits per word, no straddling
+#pragma unroll
+        for (int k = 0; k < MW; k++)
+#pragma unroll
+            for (int s4 = 0; s4 < 4; s4++)
+                if (4 * k + s4 < ell) dg[(long long)(4 * k + s4) * N] = (uint32_t)((X[k] >> (16 * s4)) & 0xffff);
+        return;
+    }
     for (int dd = 0; dd < ell; dd++) {
         const int bit = dd * base_log2;
         const int w = bit >> 6, sh = bit & 63;
