@@ -9,6 +9,10 @@ import sys
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "he_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A prebuilt oracle library to load instead of liboracle.so: the mutation
+# test (tests/test_oracle_mutants.py) points it at deliberately broken builds
+# of he_oracle.c to show that the pins fail on them.
+_OVERRIDE = os.environ.get("ORACLE_LIB_OVERRIDE")
 _lib = None
 
 
@@ -31,8 +35,11 @@ class OrcParams(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        build()
-        _lib = ctypes.CDLL(_LIB)
+        if _OVERRIDE:
+            _lib = ctypes.CDLL(_OVERRIDE)
+        else:
+            build()
+            _lib = ctypes.CDLL(_LIB)
         u64p = ctypes.POINTER(ctypes.c_uint64)
         i64p = ctypes.POINTER(ctypes.c_int64)
         i32p = ctypes.POINTER(ctypes.c_int32)

@@ -34,6 +34,63 @@ def test_keygen_relations():
         assert max(abs(v) for v in ej) <= 21
 
 
+def test_keys_equal_their_definition_from_the_streams():
+    """Every key polynomial equals its definition (Section 2, HE; Fig. 3(b)
+    for rlk), evaluated with schoolbook products on the samples the stream
+    convention names: s = ternary(seed, sk, 0); a_i = uniform(seed, pk_a, 0,
+    limb i); e = CBD(seed, pk_e, 0); b = -(a s + e).  rlk_j: a_j from
+    (seed, rlk_a, j, limb), e_j from (seed, rlk_e, j), r0 = -(a_j s + e_j) +
+    2^(16 j) s^2."""
+    P = small_params(16, (40, 41, 42), 65537)
+    seed = 31
+    K = he.keygen(P, seed, True)
+    N = P.N
+    s = he.sample_ternary(seed, he.TAG_SK, 0, N)
+    assert [int(v) for v in K.sk] == [int(v) for v in s]
+    e = he.sample_cbd(seed, he.TAG_PK_E, 0, P.eta, N)
+    for i, qi in enumerate(P.q):
+        a = he.sample_uniform(seed, he.TAG_PK_A, 0, i, qi, N)
+        assert [int(v) for v in K.pk[1, i]] == [int(v) for v in a]
+        as_ = negacyclic_int([int(v) for v in a], [int(v) for v in s])
+        assert [int(v) for v in K.pk[0, i]] == [(-(x + int(y))) % qi for x, y in zip(as_, e)]
+    s2 = negacyclic_int([int(v) for v in s], [int(v) for v in s])
+    for j in range(P.ell):
+        ej = he.sample_cbd(seed, he.TAG_RLK_E, j, P.eta, N)
+        for i, qi in enumerate(P.q):
+            aj = he.sample_uniform(seed, he.TAG_RLK_A, j, i, qi, N)
+            assert [int(v) for v in K.rlk[j, 1, i]] == [int(v) for v in aj]
+            ajs = negacyclic_int([int(v) for v in aj], [int(v) for v in s])
+            want = [(-(x + int(y)) + (1 << (P.base_log2 * j)) * z) % qi for x, y, z in zip(ajs, ej, s2)]
+            assert [int(v) for v in K.rlk[j, 0, i]] == want
+
+
+def test_encryption_equals_its_definition_from_the_streams():
+    """ct = (b u + e1 + Delta m, a u + e2) bit for bit, with Delta =
+    floor(Q/t), u = ternary(seed, enc_u, k), e1 = CBD(seed, enc_e1, k), e2 =
+    CBD(seed, enc_e2, k) for ciphertext k (first + position), by schoolbook
+    products: a dropped or swapped term, a wrong sign or a wrong Delta fails."""
+    P = small_params(16, (36, 37, 38), 65537)
+    K = he.keygen(P, 8, False)
+    N, t = P.N, P.t
+    delta = P.Q // t
+    rng = np.random.default_rng(4)
+    m = rng.integers(0, t, (2, N), dtype=np.uint64)
+    seed, first = 55, 3
+    ct = he.encrypt(P, K, m, seed, first)
+    for k in range(2):
+        idx = first + k
+        u = [int(v) for v in he.sample_ternary(seed, he.TAG_ENC_U, idx, N)]
+        e1 = he.sample_cbd(seed, he.TAG_ENC_E1, idx, P.eta, N)
+        e2 = he.sample_cbd(seed, he.TAG_ENC_E2, idx, P.eta, N)
+        for i, qi in enumerate(P.q):
+            bu = negacyclic_int([int(v) for v in K.pk[0, i]], u)
+            au = negacyclic_int([int(v) for v in K.pk[1, i]], u)
+            want0 = [(x + int(y) + delta * int(mm)) % qi for x, y, mm in zip(bu, e1, m[k])]
+            want1 = [(x + int(y)) % qi for x, y in zip(au, e2)]
+            assert [int(v) for v in ct[k, 0, i]] == want0
+            assert [int(v) for v in ct[k, 1, i]] == want1
+
+
 @pytest.mark.parametrize("N,bits,t", [(16, (36, 36, 36), 65537), (64, (50,) * 4, 1032193), (4096, (36,) * 3, 65537)])
 def test_encrypt_decrypt_roundtrip(N, bits, t):
     P = he.Params(N, he.gen_primes(N, list(bits)), t)
@@ -206,6 +263,10 @@ def test_ppmul_equals_schoolbook_mod_t():
         got = he.ppmul_terms(P, a, b, [[(0, 0), (1, 1)]])[0]
         want = [(x + y) % t for x, y in zip(negacyclic_mod(a[0], b[0], t), negacyclic_mod(a[1], b[1], t))]
         assert [int(v) for v in got] == want
+        # crossed indices: a transposed operand index fails
+        got = he.ppmul_terms(P, a, b, [[(0, 1)], [(1, 0)]])
+        assert [int(v) for v in got[0]] == negacyclic_mod(a[0], b[1], t)
+        assert [int(v) for v in got[1]] == negacyclic_mod(a[1], b[0], t)
 
 
 @pytest.mark.parametrize("N,bits,t", [(64, (40, 41), 257), (1024, (50, 50, 50), 65537)])

@@ -115,3 +115,25 @@ def test_samplers_distribution():
     w = he.stream_words(11, 2, 0, 1, 0, 4)
     assert int(u[0]) == ((int(w[1]) << 64) | int(w[0])) % q
     assert int(u[1]) == ((int(w[3]) << 64) | int(w[2])) % q
+
+
+def test_samplers_follow_the_stream_convention():
+    """Each sample is the written function of its stream word (limb field 0
+    for the small samplers): ternary floor(3 w / 2^64) - 1; CBD(eta)
+    popcount of the low eta bits minus popcount of the next eta bits;
+    uniform mod t: w mod t; uniform mod q: (w_{2k+1} 2^64 + w_{2k}) mod q."""
+    N = 64
+    w = [int(v) for v in he.stream_words(5, 4, 9, 0, 0, N)]
+    assert [int(v) for v in he.sample_ternary(5, 4, 9, N)] == [(3 * x >> 64) - 1 for x in w]
+    for eta in (3, 21):
+        m = (1 << eta) - 1
+        want = [bin(x & m).count("1") - bin((x >> eta) & m).count("1") for x in w]
+        assert [int(v) for v in he.sample_cbd(5, 4, 9, eta, N)] == want
+    t = 1032193
+    got = np.zeros(N, dtype=np.uint64)
+    he._clib.lib().orc_sample_uniform_t(5, 4, 9, t, N, he._u64(got))
+    assert [int(v) for v in got] == [x % t for x in w]
+    q = 1125899906826241
+    w2 = [int(v) for v in he.stream_words(5, 4, 9, 3, 0, 2 * N)]
+    assert [int(v) for v in he.sample_uniform(5, 4, 9, 3, q, N)] == [
+        ((w2[2 * k + 1] << 64) | w2[2 * k]) % q for k in range(N)]
