@@ -18,7 +18,10 @@ before CPMul.
 Parity unpinned for the random objects (keys, encryption randomness, masks,
 the symmetric-encryption a and e): the paper fixes no generator, so their
 exact bits follow this project's stream convention (ChaCha20, pinned to RFC
-8439; words to samples as stated at each sampler).
+8439; words to samples as stated at each sampler).  Given that convention,
+the tests pin every sampler to its written function of the stream words, and
+the keys and ciphertexts to their definitions evaluated by schoolbook
+products on those samples.
 """
 from __future__ import annotations
 
