@@ -285,6 +285,20 @@ def test_symmetric_encryption_round_trip_and_compression(N, bits, t):
     assert max(he.noise_bits(P, keys, ct[k], m[k]) for k in range(3)) <= 5   # |e| <= eta = 21
     for i, q in enumerate(P.q):
         assert np.array_equal(ct[1, 1, i], he.sample_uniform(99, he.TAG_SYM_A, 1, i, q, N))
+    # exactly: c0 + c1 s - Delta m = -e, e the CBD samples of (seed, SYM_E, k)
+    if N <= 64:
+        Q, delta = P.Q, P.Q // t
+        sk = [int(v) for v in keys.sk]
+        for k in range(3):
+            e = he.sample_cbd(99, he.TAG_SYM_E, k, P.eta, N)
+            c0i = rns_to_int(P, ct[k, 0])
+            c1s = negacyclic_int(rns_to_int(P, ct[k, 1]), sk)
+            x = [centred((a + b - delta * int(mm)) % Q, Q) for a, b, mm in zip(c0i, c1s, m[k])]
+            assert x == [-int(v) for v in e]
+    # a sub-batch starting at `first` equals the same positions of the whole batch
+    c0_sub = he.encrypt_symmetric(P, keys, m[1:], seed=99, first=1)
+    assert np.array_equal(c0_sub, c0[1:])
+    assert np.array_equal(he.expand_symmetric(P, 99, c0_sub, first=1), ct[1:])
     # a different seed gives a different ciphertext of the same message
     ct2 = he.expand_symmetric(P, 98, he.encrypt_symmetric(P, keys, m, seed=98))
     assert not np.array_equal(ct2, ct) and np.array_equal(he.decrypt(P, keys, ct2), m)

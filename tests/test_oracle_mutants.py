@@ -6,7 +6,8 @@ term, a dropped or swapped product term, an off-by-one digit, a wrong sign,
 a missing centred lift, a transposed operand, a wrong rotation and skipped
 prime candidates. In the Python packing and protocol modules they include a
 kernel not reversed, a wrong channel order, a missing output offset, a wrong
-index sign, ignored padding and a wrong mask sign.
+index sign, ignored padding, a wrong mask sign, and a dropped error or
+wrong stream index in the seed-compressed encryption.
 
 The broken copy is built apart and the oracle's pin modules run against it
 in a subprocess: the C library is loaded through the oracle loader's
@@ -70,7 +71,12 @@ PY_MUTANTS = {
     "conv_input_ignores_padding": ("packing.py", [
         ("r, s = r0 + i - p.pad, s0 + j - p.pad", "r, s = r0 + i, s0 + j")]),
     "protocol_mask_sign": ("protocol.py", [("wm = (wp + (tt - r_w)) % tt", "wm = (wp + r_w) % tt")]),
+    "symmetric_drops_e": ("he.py", [("(-(int(x) + int(ee)) + d * mm) % q", "(-int(x) + d * mm) % q")]),
+    "symmetric_wrong_stream": ("he.py", [("a = sample_uniform(seed, TAG_SYM_A, first + k, i, q, P.N)",
+                                          "a = sample_uniform(seed, TAG_SYM_A, k, i, q, P.N)")]),
 }
+PY_PINS = {"packing.py": "tests/test_oracle_packing.py", "protocol.py": "tests/test_oracle_packing.py",
+           "he.py": "tests/test_oracle_he.py"}
 
 
 def build_py_variant(tmp_path, name, fname, edits):
@@ -92,9 +98,9 @@ def build_py_variant(tmp_path, name, fname, edits):
     return str(d)
 
 
-def run_py_pins(tree):
+def run_py_pins(tree, pins="tests/test_oracle_packing.py"):
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu",
-                        "--basetemp", os.path.join(tree, "pt"), "tests/test_oracle_packing.py"],
+                        "--basetemp", os.path.join(tree, "pt"), pins],
                        cwd=tree, capture_output=True, text=True, timeout=300)
     return r.returncode, r.stdout[-2000:]
 
@@ -146,5 +152,5 @@ def test_python_control_tree_passes_the_packing_pins(tmp_path, gcc):
 @pytest.mark.parametrize("name", sorted(PY_MUTANTS))
 def test_planted_packing_or_protocol_mistake_fails_a_pin(tmp_path, gcc, name):
     fname, edits = PY_MUTANTS[name]
-    rc, out = run_py_pins(build_py_variant(tmp_path, name, fname, edits))
+    rc, out = run_py_pins(build_py_variant(tmp_path, name, fname, edits), PY_PINS[fname])
     assert rc == 1, "no pin caught mutant %s:\n%s" % (name, out)
