@@ -6,8 +6,9 @@ term, a dropped or swapped product term, an off-by-one digit, a wrong sign,
 a missing centred lift, a transposed operand, a wrong rotation and skipped
 prime candidates. In the Python packing and protocol modules they include a
 kernel not reversed, a wrong channel order, a missing output offset, a wrong
-index sign, ignored padding, a wrong mask sign, and a dropped error or
-wrong stream index in the seed-compressed encryption.
+index sign, ignored padding, a dropped wrap check, an uncentred or
+misplaced decode, wrong mask signs, and a dropped error or wrong stream
+index in the seed-compressed encryption.
 
 The broken copy is built apart and the oracle's pin modules run against it
 in a subprocess: the C library is loaded through the oracle loader's
@@ -70,7 +71,13 @@ PY_MUTANTS = {
         ("p.Ooff - cl * p.Hn * p.Wn - k * p.Wn - l, c, k, l)", "p.Ooff - cl * p.Hn * p.Wn - k * p.Wn + l, c, k, l)")]),
     "conv_input_ignores_padding": ("packing.py", [
         ("r, s = r0 + i - p.pad, s0 + j - p.pad", "r, s = r0 + i, s0 + j")]),
+    "corr_no_wrap_check": ("packing.py", [("if not (D < N or D - N < (c - 1) * S + rlo):", "if False:")]),
+    "decode_no_centring": ("packing.py", [
+        ("out[m, a, b] = v - t_mod if v > (t_mod - 1) // 2 else v", "out[m, a, b] = v")]),
+    "decode_output_packing_offset": ("packing.py", [
+        ("v = int(polys[m // p.Mn, t, k + (m % p.Mn) * p.Sout])", "v = int(polys[m // p.Mn, t, k + (m // p.Mn) * p.Sout])")]),
     "protocol_mask_sign": ("protocol.py", [("wm = (wp + (tt - r_w)) % tt", "wm = (wp + r_w) % tt")]),
+    "protocol_input_mask_sign": ("protocol.py", [("xm = (xp + (tt - r_x)) % tt", "xm = (xp + r_x) % tt")]),
     "symmetric_drops_e": ("he.py", [("(-(int(x) + int(ee)) + d * mm) % q", "(-int(x) + d * mm) % q")]),
     "symmetric_wrong_stream": ("he.py", [("a = sample_uniform(seed, TAG_SYM_A, first + k, i, q, P.N)",
                                           "a = sample_uniform(seed, TAG_SYM_A, k, i, q, P.N)")]),
