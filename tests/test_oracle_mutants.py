@@ -3,8 +3,9 @@
 Each case below plants one mistake in a copy of the oracle. In the C core
 (he_oracle.c) the mistakes include a wrong root of unity, a dropped rounding
 term, a dropped or swapped product term, an off-by-one digit, a wrong sign,
-a missing centred lift, a transposed operand, a wrong rotation and skipped
-prime candidates. In the Python packing and protocol modules they include a
+a missing centred lift, a transposed operand, a wrong rotation, skipped
+prime candidates, truncating instead of floor division, an uncentred lift
+before the tensor product and a too small auxiliary basis. In the Python packing and protocol modules they include a
 kernel not reversed, a wrong channel order, a missing output offset, a wrong
 index sign, ignored padding, a dropped wrap check, an uncentred or
 misplaced decode, wrong mask signs, and a dropped error or wrong stream
@@ -56,6 +57,10 @@ MUTANTS = {
     "relin_components_swapped": [("rlk + ((size_t)j * 2 + comp) * LN", "rlk + ((size_t)j * 2 + (1 - comp)) * LN")],
     "ppmul_transposed_index": [("tb[x] = b[(size_t)term_b[k] * N + x] % P->t;",
                                 "tb[x] = b[(size_t)term_a[k] * N + x] % P->t;")],
+    "floordiv_truncates": [("if (!rz) { big one; big_from_u64(&one, 1); big_sub(&q, &q, &one); }", "(void)rz;")],
+    "ccmul_lift_not_centred": [("crt_reconstruct_centred(&c->Q, r, &X);\n        for (int j = 0; j < nA; j++) res",
+                                "crt_reconstruct(&c->Q, r, &X);\n        for (int j = 0; j < nA; j++) res")],
+    "ccmul_aux_basis_too_small": [("int k = need_bits / 60 + 2;", "int k = need_bits / 60 - 2;")],
 }
 
 
