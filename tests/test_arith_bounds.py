@@ -142,3 +142,86 @@ def test_crt_overflow_estimate(bits):
         term = (((y << sh) * c) >> 64) >> 5
         err = Fraction(y, m) * (1 << 58) - term
         assert 0 <= err < Fraction(107, 100)
+
+
+# ---------------------------------------------------------------- single-precision quotient
+def f32_round_down_constant(qsh, q):
+    """qf as the context builds it: 2^qsh / q in double precision, converted
+    to single precision (round to nearest), then stepped down while it is not
+    below that double by a relative margin of 1e-12."""
+    import math
+
+    import numpy as np
+    d = math.ldexp(1.0, qsh) / float(q)
+    f = np.float32(d)
+    while float(f) > d * (1.0 - 1e-12):
+        f = np.nextafter(f, np.float32(0.0))
+    return f
+
+
+def rz24(v):
+    """A non-negative rational rounded toward zero to 24 significant bits
+    (single precision, no overflow or subnormals in this range)."""
+    from fractions import Fraction
+    if v == 0:
+        return Fraction(0)
+    e = v.numerator.bit_length() - v.denominator.bit_length()
+    # 2^e <= v < 2^(e+2): find e with 2^23 <= v / 2^(e-23) < 2^24
+    while Fraction(2) ** e > v:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= v:
+        e += 1
+    scale = Fraction(2) ** (e - 23)
+    return Fraction(int(v / scale)) * scale
+
+
+def reduce_small_model(x, q, qsh, qf):
+    """The device routine step by step: xh = x >> qsh (32 bits), k =
+    float2uint_rz(fmul_rz(uint2float_rz(xh), qf)); returns x - k q before
+    its one conditional subtraction."""
+    from fractions import Fraction
+    xh = x >> qsh
+    assert xh < (1 << 32)
+    a = rz24(Fraction(xh))                         # __uint2float_rz
+    p = rz24(a * Fraction(float(qf)))              # __fmul_rz (qf is exact in a double)
+    k = int(p)                                     # __float2uint_rz
+    return x - k * q
+
+
+def reduce_small_moduli(rng):
+    """Every modulus size the forward transform reduces against: plaintext
+    moduli from 17 bits (t = 65537) and RNS / auxiliary primes up to 61 bits,
+    at both ends of each bit length, plus the primes the library generates."""
+    from oracle import he
+    qs = {65537, 1032193}
+    for b in range(17, 63):
+        qs.add((1 << (b - 1)) + 1)
+        qs.add((1 << b) - 1)
+        qs.add(rng.randrange(1 << (b - 1), 1 << b) | 1)
+    for N in (1024, 8192, 16384):
+        for b in (36, 40, 50, 60, 61):
+            qs.update(he.gen_primes(N, [b]))
+    return sorted(qs)
+
+
+def test_single_precision_quotient_of_the_final_reduction():
+    """The forward transform's final reduction of x < 64 q takes its quotient
+    from a round-toward-zero single-precision estimate: it never exceeds
+    floor(x / q) and is at most one below, so x - k q lies in [0, 2q) and one
+    conditional subtraction finishes.  Checked on the boundaries k q - 1,
+    k q and k q + q - 1 for every k < 64, the largest x, and random x, for
+    moduli of every bit length from 17 to 62."""
+    rng = random.Random(4242)
+    for q in reduce_small_moduli(rng):
+        bq = q.bit_length()
+        qsh = bq + 6 - 32 if bq + 6 > 32 else 0
+        qf = f32_round_down_constant(qsh, q)
+        xs = {64 * q - 1}
+        for k in range(64):
+            xs.update({k * q, k * q + q - 1})
+            if k:
+                xs.add(k * q - 1)
+        xs.update(rng.randrange(64 * q) for _ in range(40))
+        for x in xs:
+            r = reduce_small_model(x, q, qsh, qf)
+            assert 0 <= r < 2 * q, (q, x, r)
