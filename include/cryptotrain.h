@@ -264,18 +264,21 @@ int he_cpmul_conv(he_ctx *ctx, const he_plan *plan, int batch, const uint64_t *c
 /* he_cpmul_conv_noalloc: the same computation and argument layout as
  * he_cpmul_conv, bit-identical results, but the call allocates no device
  * memory at all: no cudaMalloc, cudaFree or allocating library routine.  It
- * is meant for callers that cannot allocate at call time: code running while
- * a stream is being captured into a CUDA graph (cudaMalloc is not allowed
- * there), serving loops whose device memory is fully reserved up front by
- * another allocator, and latency-critical paths that must not hit the
- * synchronisation that cudaMalloc/cudaFree imply.  The paper has no
- * counterpart; this is a deployment variant of the CPMul convolution.
+ * is meant for callers that cannot allocate at call time: serving processes
+ * whose device memory is fully reserved up front by another allocator (a
+ * framework's caching pool, an inference engine's arena), so that a
+ * cudaMalloc inside the library would fail or evict their cache, and
+ * latency-critical loops that must not hit the device-wide synchronisation
+ * that cudaMalloc/cudaFree imply.  The paper has no counterpart; this is a
+ * deployment variant of the CPMul convolution.
  *  - Scratch: a fixed 32 MiB static device array inside the library (held on
  *    every GPU that loads the library until the process exits).  A call whose
  *    NTT-form operands and term table need more returns
  *    HE_ERR_BUDGET_EXCEEDED and does nothing; the online 3x32x32 -> 16 layer
  *    of one image (N = 8192, L = 4, 9 input ciphertexts, 8 output
  *    polynomials after output packing) needs about 7 MiB.
+ *  - The term table is written on the device by a kernel from scalar
+ *    arguments; the call leaves no host buffer for the stream to read.
  *  - The first call on a device looks up the array's device address once
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Every call on a device shares the one array and overwrites it (each byte
