@@ -12,8 +12,16 @@ value: layers (images) per second over all ranks; e2e: the same through the
 public API with the input tensors copied from pinned host memory and the
 decoded output copied back inside the timed region.
 
---impl reference times the CPU oracle (single thread) on a bounded sample of
-the same workload.  Under torchrun every rank runs its own batch (weak scaling,
+The default line also carries the metric's other parts, each measured for a
+few seconds: the batched form against the plain per-job launch (vs_plain),
+the served form with p50/p99 latency (serve), this layer under both
+encodings (conv_vs_corr) and the plain N = 4096 conventional layer (config1);
+and the CPU oracle on every host core (cpu_baseline, with the single-core
+rate beside it).
+
+--impl reference times the CPU oracle on the host cores: each step is one
+whole image of the layer per core, one single-threaded oracle process per
+core.  Under torchrun every rank runs its own batch (weak scaling,
 no data-path collective); only the timing uses collectives.
 """
 from __future__ import annotations
@@ -58,6 +66,8 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=1.0, help="serve: warm-up seconds per rate")
     ap.add_argument("--hbm-budget-gb", type=float, default=150.0, help="serve: admission budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="layer: skip the batched, served, both-encodings and config-1 sub-objects")
     return ap.parse_args()
 
 
@@ -71,7 +81,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 50 ms while running."""
+    """nvidia-smi clock / throttle samples every 10 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -85,7 +95,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -117,37 +127,79 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def cpu_oracle_layers(seconds_budget: float, steps: int = 1):
-    """Time the CPU oracle on one image of the layer, restricted to the first
-    m output channels so that `steps` samples fit the budget; returns
-    (layers/s equivalent, description, threads)."""
-    import numpy as np  # noqa: F401
-    from oracle import he, packing, protocol
-    from paper_2409_16675_gb300 import workloads as wl
+# ---------------------------------------------------------------- CPU oracle on the host cores
+# One image of the layer per task: the whole CryptoTrain-P layer through the
+# oracle (encode, masks, 4 encryptions, CCMul-Precompute, CPMul, PPMul,
+# decrypt, decode), keys generated once per worker outside the timing.  A
+# process pool (spawn start method: the parent may hold a CUDA context) runs
+# one task per host core at a time; each worker is single-threaded.
+_ORC = {}
 
+
+def _oracle_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import he, packing
+    from paper_2409_16675_gb300 import workloads as wl
     w = wl.CONV_MID
     s = w.shape
     P = he.Params.from_spec(w.ring)
-    keys = he.keygen(P, 1, True)
-    # one output channel first, to size the sample
-    m_sel = 1
-    x, k = wl.layer_inputs(w, 1)
-    plan = packing.make_plan(w.encoding, P.N, s.C, s.H, s.W, m_sel, s.h, s.pad)
+    _ORC.update(P=P, keys=he.keygen(P, 1, True), w=w,
+                plan=packing.make_plan(w.encoding, P.N, s.C, s.H, s.W, s.M, s.h, s.pad),
+                inputs=wl.layer_inputs(w, 8))
+
+
+def _oracle_image(i):
+    from oracle import protocol
+    from paper_2409_16675_gb300 import workloads as wl
+    x, k = _ORC["inputs"]
     t0 = time.perf_counter()
-    protocol.run_layer(P, plan, x[0], k[:m_sel], wl.protocol_seeds(w.seed), keys=keys)
-    per_channel = time.perf_counter() - t0
-    m_sel = int(max(1, min(s.M, seconds_budget / max(steps, 1) / per_channel)))
-    plan = packing.make_plan(w.encoding, P.N, s.C, s.H, s.W, m_sel, s.h, s.pad)
-    times = []
-    for i in range(steps):
+    protocol.run_layer(_ORC["P"], _ORC["plan"], x[i % len(x)], k, wl.protocol_seeds(_ORC["w"].seed + i),
+                       keys=_ORC["keys"])
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """nproc single-threaded oracle workers; step() runs one image per worker
+    and returns (wall seconds, per-image seconds)."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init)
+        self.next = 0
+
+    def step(self):
+        idx = list(range(self.next, self.next + self.cores))
+        self.next += self.cores
         t0 = time.perf_counter()
-        protocol.run_layer(P, plan, x[0], k[:m_sel], wl.protocol_seeds(w.seed + i), keys=keys)
-        times.append(time.perf_counter() - t0)
-    per_layer = (sum(times) / len(times)) * s.M / m_sel
-    desc = ("one 3x32x32 image, %d of the %d output channels per sample (whole CryptoTrain-P layer: "
-            "encode, masks, 4 encryptions, CCMul-Precompute, CPMul, PPMul, decrypt, decode), "
-            "scaled to a full layer; keygen excluded" % (m_sel, s.M))
-    return 1.0 / per_layer, desc, times
+        per = self.pool.map(_oracle_image, idx, chunksize=1)
+        return time.perf_counter() - t0, per
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+ORACLE_SAMPLE = ("one 3x32x32 image per host core per step, all 16 output channels (the whole CryptoTrain-P "
+                 "layer: encode, masks, 4 encryptions, CCMul-Precompute, CPMul, PPMul, decrypt, decode), "
+                 "one single-threaded oracle process per core; keygen once per process, outside the timing")
+
+
+def cpu_oracle_baseline():
+    """One pool step (one image per core, about 10 s): all-core layers/s, and
+    the single-core rate from the same run's per-image times."""
+    pool = OraclePool()
+    try:
+        pool.step()                      # warm-up (imports, tables, first-touch)
+        wall, per = pool.step()
+    finally:
+        pool.close()
+    single = len(per) / sum(per)
+    return {"value": pool.cores / wall, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": ORACLE_SAMPLE + "; one warm-up step, then one timed step",
+            "nproc": os.cpu_count(), "single_core": {"value": single, "unit": UNIT, "cores": 1,
+                                                     "ms_per_layer": 1000.0 / single}}
 
 
 def run_reference(args):
@@ -156,18 +208,130 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2409_16675_gb300 import workloads as wl
-    budget = 150.0
-    val, desc, times = cpu_oracle_layers(budget, max(1, args.steps))
+    pool = OraclePool()
+    t_start = time.perf_counter()
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        walls, per = [], []
+        for _ in range(args.steps):
+            wt, pt = pool.step()
+            walls.append(wt)
+            per += pt
+    finally:
+        pool.close()
+    total = sum(walls)
+    val = pool.cores * args.steps / total
     w = wl.CONV_MID
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": w.name, "batch": 1, "N": w.ring.N, "L": w.ring.L, "t": w.ring.t,
-                       "encoding": w.encoding},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": w.name, "batch": pool.cores, "N": w.ring.N, "L": w.ring.L, "t": w.ring.t,
+                       "encoding": w.encoding, "images_per_step": pool.cores},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                             "sample": ORACLE_SAMPLE, "nproc": os.cpu_count(),
+                             "single_core": {"value": len(per) / sum(per), "unit": UNIT, "cores": 1}},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "consistency": {"timed_s": total, "wall_s_incl_warmup_and_pool": time.perf_counter() - t_start,
+                            "extrapolated": False}}
     print(json.dumps(line), flush=True)
+
+
+def _timed(fn, steps, warmup, stream):
+    """ms per call of fn: warm-up calls, then steps calls between CUDA events
+    on the launching stream."""
+    import torch
+    for _ in range(max(1, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def config1_measure(steps, warmup, batch=64):
+    """Config 1: the plain single encrypted conv layer, conventional encoding,
+    CPMul only.  N = 4096, 3 x 36-bit limbs, t = 65537; one 1x28x28 uint8
+    image, 4 int8 3x3 kernels, valid.  A step: encode x and w, encrypt x,
+    he_cpmul_conv ([x] times the encoded kernels), decrypt, decode.  Timed at
+    batch 1 (the latency of one layer) and at `batch` images per call; the
+    decoded outputs are checked against a float64 convolution (exact here:
+    |values| <= 255 * 8 * 9)."""
+    import torch
+
+    from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
+
+    w_ = wl.CONV_SMALL
+    s = w_.shape
+    ctx = layer.Context(w_.ring)
+    keys = layer.Keys(ctx, w_.seed * 7 + 1, False)
+    plan = layer.Plan(ctx, s, w_.encoding)
+    st = torch.cuda.current_stream()
+    x_h, k_h = wl.layer_inputs(w_, batch)
+    x_all, k = torch.from_numpy(x_h).cuda(), torch.from_numpy(k_h).cuda()
+    out = {}
+    exact = True
+    for B in (1, batch):
+        x = x_all[:B].contiguous()
+        nx, nw, no = B * plan.T * plan.G, plan.MG * plan.G, B * plan.MG * plan.T
+        xp, wp, ct_x, ct_o, dec = ctx.u64(nx, ctx.N), ctx.u64(nw, ctx.N), ctx.ct(nx), ctx.ct(no), ctx.u64(no, ctx.N)
+        y = torch.empty((B, s.M, plan.info.Ho, plan.info.Wo), dtype=torch.int64, device="cuda")
+
+        def step():
+            plan.encode_input(x, B, xp)
+            plan.encode_kernel(k, wp)
+            nv.he_encrypt(ctx.h, keys.h, xp, nx, 1234, ct_x)
+            nv.he_cpmul_conv(ctx.h, plan.h, B, ct_x, wp, None, None, None, ct_o)
+            nv.he_decrypt(ctx.h, keys.h, ct_o, no, dec)
+            nv.he_decode(ctx.h, plan.h, B, dec, None, y)
+
+        ms = _timed(step, steps, warmup, st)
+        ref = torch.nn.functional.conv2d(x.double(), k.double(), padding=s.pad).round().long()
+        exact = exact and bool(torch.equal(y, ref))
+        out["batch%d" % B] = {"ms_per_step": ms, "layers_per_s": B / (ms / 1000.0)}
+    plan.close()
+    keys.close()
+    ctx.close()
+    return {"workload": w_.name, **out, "products_per_image": plan.products,
+            "decoded_equals_integer_conv": exact, "steps": steps, "warmup": warmup}
+
+
+def conv_vs_corr_measure(steps, warmup, batch=64):
+    """Config 2 under both encodings: the whole CryptoTrain-P layer step
+    (3x32x32 -> 16, 3x3 same, N = 8192, 4 x 50-bit, batch `batch`) with the
+    conventional and with the correlated packing; both decode to the same
+    integer convolution."""
+    import torch
+
+    from paper_2409_16675_gb300 import layer, workloads as wl
+
+    w_ = wl.CONV_MID
+    ctx = layer.Context(w_.ring)
+    keys = layer.Keys(ctx, w_.seed * 7 + 1, True)
+    x_h, k_h = wl.layer_inputs(w_, batch)
+    x, k = torch.from_numpy(x_h).cuda(), torch.from_numpy(k_h).cuda()
+    seeds = wl.protocol_seeds(w_.seed)
+    st = torch.cuda.current_stream()
+    res, ys = {}, {}
+    for enc in ("conv", "corr"):
+        plan = layer.Plan(ctx, w_.shape, enc)
+        pl = layer.PLayer(ctx, keys, plan, batch)
+        ms = _timed(lambda: pl.step(x, k, seeds), steps, warmup, st)
+        ys[enc] = pl.buf.y.clone()
+        res[enc] = {"ms_per_step": ms, "layers_per_s": batch / (ms / 1000.0), "products_per_image": plan.products,
+                    "input_polys_per_image": plan.T * plan.G}
+        del pl
+        plan.close()
+    keys.close()
+    ctx.close()
+    return {"workload": w_.name, "batch": batch, **res,
+            "corr_speedup": res["conv"]["ms_per_step"] / res["corr"]["ms_per_step"],
+            "same_decoded_outputs": bool(torch.equal(ys["conv"], ys["corr"])), "steps": steps, "warmup": warmup}
 
 
 def run_gpu(args):
@@ -306,9 +470,17 @@ def run_gpu(args):
             "gpu_launches": int(launches_total),
             "roofline": roof,
             "kernels": kernels}
+    if ws == 1 and not args.no_extras:
+        # the metric's other parts, each bounded to seconds: the batched form
+        # against the plain per-job launch (config 4), the served form with
+        # p50/p99 (config 5), both encodings of this layer (config 2) and the
+        # plain N = 4096 conventional layer (config 1)
+        line["vs_plain"] = batched_measure(5, 2)
+        line["serve"] = serve_measure([300.0, 1000.0, 2000.0], 2.0, 0.5, args.hbm_budget_gb)
+        line["conv_vs_corr"] = conv_vs_corr_measure(10, 2)
+        line["config1"] = config1_measure(20, 3)
     if not args.no_cpu_baseline and ws == 1:
-        val, desc, _ = cpu_oracle_layers(20.0, 1)
-        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_oracle_baseline()
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
@@ -355,16 +527,18 @@ def run_train(args):
     tr.close()
 
 
-def run_batched(args):
-    """256 ct x pt convolution jobs of uneven shapes (channels {3,16,32,64,128},
-    spatial {8,16,32}, kernel {1,3,5}), N in {4096, 8192}, 2-5 limbs of 36-60
-    bits, both encodings: jobs per second as one call per job (plain), as
-    persistent queue kernels, and replayed from a CUDA graph, after the
-    autotuner has picked the launch configuration."""
+def batched_measure(steps, warmup, sample_every=16):
+    """Config 4: 256 ct x pt convolution jobs of uneven shapes (channels
+    {3,16,32,64,128}, spatial {8,16,32}, kernel {1,3,5}), N in {4096, 8192},
+    2-5 limbs of 36-60 bits, both encodings.  ms per batch as one call per job
+    (plain), as persistent queue kernels, and replayed from a CUDA graph,
+    after the autotuner has picked the launch configuration; every
+    sample_every-th job's output compared across the three modes."""
     import torch
 
     from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
 
+    t_setup = time.perf_counter()
     jobs = wl.batched_jobs()
     ctxs, items = {}, []
     for j in jobs:
@@ -384,36 +558,52 @@ def run_batched(args):
     for (c, p, ct, pt, out) in items:
         nv.he_batch_add_cpmul(b, c.h, p.h, 1, ct, pt, None, out)
     nv.he_batch_prepare(b)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
     s = torch.cuda.Stream()
     res, outs = {}, {}
     with torch.cuda.stream(s):
+        t0 = time.perf_counter()
         tuning = nv.he_batch_autotune(b)
+        tune_s = time.perf_counter() - t0
         for name, mode in (("plain", nv.HE_BATCH_PLAIN), ("persistent", nv.HE_BATCH_PERSISTENT),
                            ("graph", nv.HE_BATCH_GRAPH)):
-            for _ in range(max(1, args.warmup)):
+            for it in items:
+                it[4].zero_()
+            for _ in range(max(1, warmup)):
                 nv.he_batch_run(b, mode)
             s.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 nv.he_batch_run(b, mode)
             e1.record(s)
             s.synchronize()
-            res[name] = e0.elapsed_time(e1) / args.steps
-            outs[name] = [it[4][:1].clone() for it in items[::16]]
+            res[name] = e0.elapsed_time(e1) / steps
+            outs[name] = [it[4].clone() for it in items[::sample_every]]
     same = all(torch.equal(a, r) for m in outs for a, r in zip(outs[m], outs["plain"]))
-    print(json.dumps({"metric": "batched ct x pt conv jobs/s (256 uneven jobs)", "unit": "jobs/s",
-                      "value": len(jobs) / (res["graph"] / 1000.0), "higher_is_better": True,
-                      "steps": args.steps, "warmup": args.warmup, "dtype": "u64", "data": "synthetic",
-                      "ms_per_batch": res, "jobs_per_s": {k: len(jobs) / (v / 1000.0) for k, v in res.items()},
-                      "speedup_vs_plain": {k: res["plain"] / v for k, v in res.items()},
-                      "identical_results": bool(same), "autotune": tuning, "contexts": len(ctxs),
-                      "config": {"workload": "256 uneven conv jobs, N 4096/8192, 2-5 limbs of 36-60 bits"}}),
-          flush=True)
     nv.he_batch_destroy(b)
+    for (c, p, ct, pt, out) in items:
+        p.close()
+    for c in ctxs.values():
+        c.close()
+    return {"jobs": len(jobs), "ms_per_batch": res,
+            "jobs_per_s": {k: len(jobs) / (v / 1000.0) for k, v in res.items()},
+            "speedup_vs_plain": {k: res["plain"] / v for k, v in res.items()},
+            "identical_results": bool(same), "compared_jobs": len(outs["plain"]), "autotune": tuning,
+            "contexts": len(ctxs), "steps": steps, "warmup": warmup, "setup_s": setup_s, "autotune_s": tune_s}
 
 
-def run_serve(args):
+def run_batched(args):
+    r = batched_measure(args.steps, args.warmup)
+    print(json.dumps({"metric": "batched ct x pt conv jobs/s (256 uneven jobs)", "unit": "jobs/s",
+                      "value": r["jobs_per_s"]["graph"], "higher_is_better": True,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "u64", "data": "synthetic",
+                      **r, "config": {"workload": "256 uneven conv jobs, N 4096/8192, 2-5 limbs of 36-60 bits"}}),
+          flush=True)
+
+
+def serve_measure(rates, seconds, warmup_s, budget_gb):
     """Served form: 64 clients, each with its own ring (N in {4096, 8192,
     16384}, 2-8 limbs of 36-60 bits), keys, plan and layer (shapes as in the
     batched form), whose encrypted inputs, masked plaintexts and precomputed
@@ -475,7 +665,7 @@ def run_serve(args):
         st.synchronize()
     plain_lps = reps * len(clients) / (e0.elapsed_time(e1) / 1000.0)
 
-    srv = nv.he_server_create(0, hbm_budget_bytes=args.hbm_budget_gb * 1e9, max_group=64, max_inflight=4,
+    srv = nv.he_server_create(0, hbm_budget_bytes=budget_gb * 1e9, max_group=64, max_inflight=4,
                               n_streams=4, poll_us=20)
     # saturation: every client submits DEPTH requests at once
     for rep in range(2):
@@ -491,14 +681,13 @@ def run_serve(args):
     sweep = []
     gpu = int(os.environ.get("LOCAL_RANK", "0"))
     with ClockSampler(gpu) as clk:
-        for ri, rate in enumerate(float(r) for r in args.rates.split(",")):
-            times, who = wl.poisson_arrivals(wl.MASTER_SEED + 50 + ri, rate,
-                                             args.serve_warmup + args.serve_seconds, len(clients))
+        for ri, rate in enumerate(rates):
+            times, who = wl.poisson_arrivals(wl.MASTER_SEED + 50 + ri, rate, warmup_s + seconds, len(clients))
             inflight = [[] for _ in clients]          # (request id, slot)
             shed, lag, measured = 0, [], False
             start = time.perf_counter()
             for tt, ci in zip(times, who):
-                if not measured and tt >= args.serve_warmup:
+                if not measured and tt >= warmup_s:
                     nv.he_server_reset_stats(srv)
                     measured = True
                 while True:
@@ -527,22 +716,30 @@ def run_serve(args):
                           "groups": r["groups"], "arena_peak_gb": r["arena_peak_bytes"] / 1e9,
                           "submit_lag_p99_ms": float(np.percentile(lag, 99)) * 1e3 if lag else None})
     nv.he_server_destroy(srv)
-    print(json.dumps({
-        "metric": "served CryptoTrain-P layers/s with p50/p99 latency (64 clients, Poisson arrivals)",
-        "unit": "layers/s", "value": sat_lps, "higher_is_better": True, "n_gpus": 1, "dtype": "u64",
-        "data": "synthetic", "plain_launch_layers_per_s": plain_lps, "speedup_vs_plain": sat_lps / plain_lps,
-        "saturation": {"requests": sat["completed"], "p50_ms": sat["p50_us"] / 1e3, "p99_ms": sat["p99_us"] / 1e3,
-                       "groups": sat["groups"]},
-        "sweep": sweep, "identical_results": bool(same), "clocks": clk.summary(),
-        "setup_s": setup_s, "resident_gb": resident / 1e9,
-        "config": {"workload": "64 clients, N 4096/8192/16384, 2-8 limbs of 36-60 bits, batched-form shapes, "
-                               "one image per request",
-                   "hbm_budget_gb": args.hbm_budget_gb, "seconds_per_rate": args.serve_seconds,
-                   "warmup_s_per_rate": args.serve_warmup, "max_requests_per_client": DEPTH}}), flush=True)
     for (ctx, keys, plan, pl, outs) in clients:
         keys.close()
         plan.close()
         ctx.close()
+    return {"saturated_layers_per_s": sat_lps, "plain_launch_layers_per_s": plain_lps,
+            "speedup_vs_plain": sat_lps / plain_lps,
+            "saturation": {"requests": sat["completed"], "p50_ms": sat["p50_us"] / 1e3,
+                           "p99_ms": sat["p99_us"] / 1e3, "groups": sat["groups"]},
+            "sweep": sweep, "identical_results": bool(same), "clocks": clk.summary(),
+            "setup_s": setup_s, "resident_gb": resident / 1e9,
+            "config": {"workload": "64 clients, N 4096/8192/16384, 2-8 limbs of 36-60 bits, batched-form shapes, "
+                                   "one image per request",
+                       "hbm_budget_gb": budget_gb, "seconds_per_rate": seconds, "warmup_s_per_rate": warmup_s,
+                       "max_requests_per_client": DEPTH}}
+
+
+def run_serve(args):
+    """Served form (config 5), see serve_measure."""
+    r = serve_measure([float(x) for x in args.rates.split(",")], args.serve_seconds, args.serve_warmup,
+                      args.hbm_budget_gb)
+    print(json.dumps({
+        "metric": "served CryptoTrain-P layers/s with p50/p99 latency (64 clients, Poisson arrivals)",
+        "unit": "layers/s", "value": r["saturated_layers_per_s"], "higher_is_better": True, "n_gpus": 1,
+        "dtype": "u64", "data": "synthetic", **r}), flush=True)
 
 
 def run_plancount(args):

@@ -120,3 +120,40 @@ def test_every_launch_configuration_gives_the_same_bits():
     nv.he_batch_destroy(b)
     for c in ctxs.values():
         c.close()
+
+
+def test_full_config4_batch_sampled_against_the_oracle():
+    """The real 256-job batch of the batched form (C, M in {3..128}, spatial
+    {8, 16, 32}, kernels {1, 3, 5}, N in {4096, 8192}, 2-5 limbs of 36-60
+    bits, both encodings), one image per job, replayed from its CUDA graph in
+    the launch configuration the autotuner picks: for every 16th job, the
+    first and the last output ciphertext (all limbs, both components) equal
+    the oracle's sum of ciphertext x plaintext products."""
+    jobs = wl.batched_jobs()
+    ctxs, items = build(jobs, B=1)
+    b = nv.he_batch_create(0)
+    for (c, p, ct, pt, out) in items:
+        nv.he_batch_add_cpmul(b, c.h, p.h, 1, ct, pt, None, out)
+    nv.he_batch_prepare(b)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nv.he_batch_autotune(b)
+        for it in items:
+            it[4].zero_()
+        nv.he_batch_run(b, nv.HE_BATCH_GRAPH)
+        s.synchronize()
+    nv.he_batch_destroy(b)
+    checked = set()
+    for (c, p, ct, pt, out) in items[::16]:
+        T, G, MG = p.T, p.G, p.MG
+        terms = [[(t * G + g, m * G + g) for g in range(G)] for m in range(MG) for t in range(T)]
+        sel = sorted({0, len(terms) - 1})
+        want = he.cpmul_terms(he.Params(c.N, c.q, c.t), ct.cpu().numpy(), pt.cpu().numpy(), [terms[o] for o in sel])
+        got = out.cpu().numpy()[sel]
+        assert np.array_equal(got, want), (c.N, c.L, p.shape, p.encoding)
+        checked.add((c.N, c.L, p.encoding))
+    assert {n for (n, _, _) in checked} == {4096, 8192} and {e for (_, _, e) in checked} == {"conv", "corr"}
+    for (c, p, ct, pt, out) in items:
+        p.close()
+    for c in ctxs.values():
+        c.close()

@@ -1,7 +1,8 @@
 """Served form: continuous batching of CryptoTrain-P online layers from several
 clients (each with its own ring, keys and resident precomputed products).
 Every result is bit-identical to the same request run alone, decodes to the
-exact convolution, and admission respects the HBM budget."""
+exact convolution, equals the oracle's ciphertexts on every client ring, and
+admission respects the HBM budget."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from oracle import protocol  # noqa: E402
+from oracle import he, protocol  # noqa: E402
 from paper_2409_16675_gb300 import layer, native as nv, workloads as wl  # noqa: E402
 
 CLIENTS = [
@@ -57,6 +58,20 @@ def test_server_results_equal_alone_and_decode():
         assert done and lat > 0
     for pl, o in outs:
         assert torch.equal(o, pl.buf.out)           # same bits as the request alone
+    # one served result per client ring against the oracle's CPMul + CCAdd at
+    # the ciphertext level: out[b][m][t] = sum_g [x][b][t][g] (w - r^w)[m][g]
+    # + [w][m][g] (x - r^x)[b][t][g] + [r^x r^w][b][m][t]
+    for (ctx, keys, plan, pl, x, w), (pl2, o) in zip(clients, outs[:len(clients)]):
+        b = pl.buf
+        T, G, MG, B = plan.T, plan.G, plan.MG, pl.B
+        nx, nw = B * T * G, MG * G
+        terms = [[((bb * T + t) * G + g, m * G + g) for g in range(G)] +
+                 [(nx + m * G + g, nw + (bb * T + t) * G + g) for g in range(G)]
+                 for bb in range(B) for m in range(MG) for t in range(T)]
+        ct = torch.cat([b.ct_x, b.ct_w]).cpu().numpy()
+        pt = torch.cat([b.wm, b.xm]).cpu().numpy()
+        want = he.cpmul_terms(he.Params(ctx.N, ctx.q, ctx.t), ct, pt, terms, add=b.rr.cpu().numpy())
+        assert np.array_equal(o.cpu().numpy(), want), ctx.N
     # decode one result per client: the exact convolution
     for (ctx, keys, plan, pl, x, w), (pl2, o) in zip(clients, outs[:len(clients)]):
         pl.buf.out.copy_(o)
