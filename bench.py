@@ -433,8 +433,12 @@ def run_gpu(args):
     # ---- roofline of the dominant kernel family
     peak, peak_kind = peaks()
     clocks = clk.summary()
-    dom = max(trace.items(), key=lambda kv: kv[1][1])
-    name, (launches, tot_ms, byt, mm) = dom
+    # kernel families (the part of a trace name before the call site's role)
+    fam = {}
+    for k, (n, t, b_, m_) in trace.items():
+        f = fam.setdefault(k.split(".")[0], [0, 0.0, 0.0, 0.0])
+        f[0] += n; f[1] += t; f[2] += b_; f[3] += m_
+    name, (launches, tot_ms, byt, mm) = max(fam.items(), key=lambda kv: kv[1][1])
     gbs = byt / (tot_ms / 1000.0) / 1e9
     # The NTT / multiply-accumulate kernels are bound by the integer multiply
     # pipe, not by HBM: peak = SMs x 64 IMAD lanes per cycle x SM clock / 10
@@ -455,8 +459,12 @@ def run_gpu(args):
                             % (ms_traced / args.steps),
             "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                     "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind}}
-    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / sum(u[1] for u in trace.values()),
-                   "GB/s": v[2] / (v[1] / 1000.0) / 1e9 if v[1] else None} for k, v in trace.items()}
+    total_ms = sum(u[1] for u in trace.values())
+    kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms,
+                   "GB/s": v[2] / (v[1] / 1000.0) / 1e9 if v[1] else None,
+                   "Tmodmul/s": v[3] / (v[1] / 1000.0) / 1e12 if v[1] else None}
+               for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+    families = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in fam.items()}
     launches_total = sum(v[0] for v in trace.values())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -469,7 +477,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(yp.numel() * 8)},
             "gpu_launches": int(launches_total),
             "roofline": roof,
-            "kernels": kernels}
+            "kernels": kernels, "families": families}
     if ws == 1 and not args.no_extras:
         # the metric's other parts, each bounded to seconds: the batched form
         # against the plain per-job launch (config 4), the served form with

@@ -460,8 +460,10 @@ int he_server_destroy(he_server *server);
  * on its stream and tagged with the kernel family name and its algorithmic
  * bytes (each distinct input polynomial read once, each output written
  * once) and 64-bit modular products.  he_trace_read synchronises the device,
- * folds the recorded launches into one entry per kernel family, and clears
- * the record.  Tracing adds two event records per launch. */
+ * folds the recorded launches into one entry per kernel family and call
+ * site, named "family.role" (for example mac_intt.relin, ntt_fwd.relin_digits,
+ * mac_intt.cpmul), and clears the record.  Tracing adds two event records per
+ * launch. */
 typedef struct he_trace_entry {
     char name[32];
     int64_t launches;

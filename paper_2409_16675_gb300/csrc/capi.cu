@@ -108,12 +108,14 @@ static int upload_terms(he_ctx *c, const Terms &T, MacJob &m) {
     return upload_terms_raw(c, T, &m.ptr, &m.ta, &m.tb);
 }
 
+thread_local const char *g_trace_role = nullptr;
+
 // Every traced launch is also an NVTX range (host side, around the enqueue),
 // so profilers can select the library's stages by name.
 TraceScope::TraceScope(he_ctx *c_, cudaStream_t st_, const char *name, double bytes, double modmuls) : c(c_), st(st_) {
     nvtxRangePushA(name);
     if (!c || !c->trace) return;
-    he_ctx::TraceRec r{name, nullptr, nullptr, bytes, modmuls};
+    he_ctx::TraceRec r{name, g_trace_role, nullptr, nullptr, bytes, modmuls};
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
     cudaEventRecord(r.a, st);
     c->trace_recs.push_back(r);
@@ -257,6 +259,7 @@ int he_last_error(const he_ctx *c, char *buf, int len) {
 int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStream_t st) {
     if (!c || !out) return HE_ERR_INVALID_ARG;
     *out = nullptr;
+    TraceRole tr_("keygen");
     TRY(set_device(c));
     const int N = c->N, L = c->L, ell = with_relin ? c->ell : 0;
     const size_t LN = (size_t)L * N;
@@ -436,6 +439,7 @@ static int encrypt_groups(he_ctx *c, const he_keys *k, int n_groups, const uint6
                           const uint64_t *seeds, uint64_t *const *cts, cudaStream_t st) {
     if (!c || !k || n_groups < 1 || n_groups > 4 || !pts || !counts || !seeds || !cts) return HE_ERR_INVALID_ARG;
     TRY(check_keys(c, k));
+    TraceRole tr_("enc");
     int n = 0;
     for (int g = 0; g < n_groups; g++) {
         if (counts[g] < 0 || (counts[g] && (!pts[g] || !cts[g]))) return HE_ERR_INVALID_ARG;
@@ -508,6 +512,7 @@ int he_encrypt_symmetric(he_ctx *c, const he_keys *k, const uint64_t *pt, int n,
                          cudaStream_t st) {
     if (!c || !k || n < 0 || (n && (!pt || !c0))) return HE_ERR_INVALID_ARG;
     TRY(check_keys(c, k));
+    TraceRole tr_("enc_sym");
     if (!n) return HE_OK;
     TRY(set_device(c));
     const int N = c->N, L = c->L;
@@ -536,6 +541,7 @@ int he_encrypt_symmetric(he_ctx *c, const he_keys *k, const uint64_t *pt, int n,
 int he_expand_symmetric(he_ctx *c, uint64_t seed, int n, const uint64_t *c0, uint64_t *ct, cudaStream_t st) {
     if (!c || n < 0 || (n && (!c0 || !ct))) return HE_ERR_INVALID_ARG;
     if (!n) return HE_OK;
+    TraceRole tr_("expand_sym");
     TRY(set_device(c));
     const int N = c->N, L = c->L;
     const size_t LN = (size_t)L * N;
@@ -553,6 +559,7 @@ int he_expand_symmetric(he_ctx *c, uint64_t seed, int n, const uint64_t *c0, uin
 int he_decrypt(he_ctx *c, const he_keys *k, const uint64_t *ct, int n, uint64_t *pt, cudaStream_t st) {
     if (!c || !k || n < 0 || (n && (!pt || !ct))) return HE_ERR_INVALID_ARG;
     TRY(check_keys(c, k));
+    TraceRole tr_("dec");
     if (!n) return HE_OK;
     TRY(set_device(c));
     const int N = c->N, L = c->L;
@@ -646,6 +653,7 @@ int he_cpmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *ct_x, 
                   cudaStream_t st) {
     if (!c || !p || batch < 0 || !ct_out || (!ct_x && !ct_w)) return HE_ERR_INVALID_ARG;
     TRY(check_plan(c, p));
+    TraceRole tr_("cpmul");
     if ((ct_x && !pt_w) || (ct_w && !pt_x)) return fail(c, HE_ERR_INVALID_ARG, "missing plaintext operand");
     if (!batch) return HE_OK;
     TRY(set_device(c));
@@ -735,6 +743,7 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     u64 *dq = cv.take<u64>((size_t)chunk * 2 * LN);
     uint32_t *dig = cv.take<uint32_t>((size_t)chunk * ell * N);
     u64 *dign = cv.take<u64>((size_t)chunk * ell * LN);
+    TraceRole tr_("ccmul_in");
     // 1. exact base extension Q -> B of both operands
     TRY(launch_base_extend(c, ct_a, (long long)n_a * 2, aux_a, st));
     TRY(launch_base_extend(c, ct_b, (long long)n_b * 2, aux_b, st));
@@ -749,6 +758,7 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     TRY(launch_fwd_multi(c, fab, 2, st));
     for (int o0 = 0; o0 < n_out; o0 += chunk) {
         const int nc = std::min(chunk, n_out - o0);
+        g_trace_role = "tensor";
         // 3. tensor product (summed over the group) + inverse NTT, output o*3 + j
         Terms Tt;
         for (int o = o0; o < o0 + nc; o++)
@@ -765,13 +775,16 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
         TRY(upload_terms(c, Tt, mt));
         mt.A = An; mt.B = Bn; mt.out = d; mt.out_stride = LKN; mt.n_out = nc * 3; mt.n_limbs = LK;
         TRY(launch_mac_intt(c, mt, st));
+        g_trace_role = "rescale";
         // 4. exact rescaling by t/q and digits of d2
         TRY(launch_scale_round(c, d, nc, dq, dig, st));
+        g_trace_role = "relin_digits";
         // 5. digits to the NTT domain over Q
         f = fwd_job();
         f.kind = SRC_U32; f.src = dig; f.src_stride = N; f.dst = dign; f.dst_stride = LN; f.n_polys = nc * ell;
         f.n_limbs = L;
         TRY(launch_fwd(c, f, st));
+        g_trace_role = "relin";
         // 6. key switch: (c0, c1) = (d0, d1) + sum_j D_j rlk_j
         Terms Tk;
         for (int o = 0; o < nc; o++)
@@ -814,6 +827,7 @@ int he_ppmul_conv(he_ctx *c, const he_plan *p, int batch, const uint64_t *pt_x, 
     if (c->t_mod < 0) return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "t is not an NTT prime for this N");
     if (!batch) return HE_OK;
     TRY(set_device(c));
+    TraceRole tr_("ppmul");
     const int N = c->N, T = p->info.T, G = p->info.G, M = p->info.MG;
     const long long nX = (long long)batch * T * G, nW = (long long)M * G;
     TRY(ws_reserve(c, Carver::round((nX + nW) * N * 8) + 4096));
@@ -880,8 +894,9 @@ int he_trace_read(he_ctx *c, he_trace_entry *out, int max_entries, int *n_entrie
     for (auto &r : c->trace_recs) {
         float ms = 0;
         cudaEventElapsedTime(&ms, r.a, r.b);
-        he_trace_entry &e = acc[r.name];
-        snprintf(e.name, sizeof e.name, "%s", r.name);
+        const std::string key = r.role ? std::string(r.name) + "." + r.role : std::string(r.name);
+        he_trace_entry &e = acc[key];
+        snprintf(e.name, sizeof e.name, "%s", key.c_str());
         e.launches++;
         e.total_ms += ms;
         e.bytes += r.bytes;

@@ -18,9 +18,18 @@ constexpr int MAX_MODS = 48;   // Q limbs + aux limbs + t
 constexpr int MAXP = 24;       // primes of one CRT basis
 constexpr int MAXW = 18;       // 64-bit words of a CRT sum (< n * M)
 
+// Register tile of the NTT kernels: every thread holds 2^kNttTileBits
+// coefficients, and passes of up to kNttTileBits stages run in registers.
+// The forward factor table's order (below) follows the same pass structure.
+constexpr int kNttTileBits = 4;
+
 // One NTT-friendly modulus: constants for Shoup products and its tables.
 //   fw[2^s + i]  forward factor of group i at stage s of the merged-twist
-//                negacyclic transform: psi^bitrev(2^s + i)
+//                negacyclic transform, psi^bitrev(2^s + i), stored within its
+//                stage at the position the forward pass reads it from:
+//                group i = h 2^gb + g (g < 2^gb, gb = the register bits of the
+//                stage above the butterfly bit) sits at 2^s + g 2^(s-gb) + h,
+//                so that a warp's loads of one g are contiguous
 //   iw[2^s + k]  inverse (decimation-in-time, bit-reversed input) factor for
 //                offset k at stage s: omega^-(k 2^(n-1-s)), omega = psi^2
 //   z[e]         untwist and scale: psi^-e N^-1
@@ -117,7 +126,7 @@ struct he_ctx {
     std::string err;
     // launch tracing
     bool trace = false;
-    struct TraceRec { const char *name; cudaEvent_t a, b; double bytes, modmuls; };
+    struct TraceRec { const char *name, *role; cudaEvent_t a, b; double bytes, modmuls; };
     std::vector<TraceRec> trace_recs;
 };
 
@@ -155,6 +164,15 @@ inline bool plan_pair(const he_plan *p, int mg, int g) {
 
 
 namespace he {
+
+// The role of the launches a call site issues (a string literal, or null);
+// the trace reports each launch as "family.role".
+extern thread_local const char *g_trace_role;
+struct TraceRole {
+    const char *prev;
+    explicit TraceRole(const char *r) : prev(g_trace_role) { g_trace_role = r; }
+    ~TraceRole() { g_trace_role = prev; }
+};
 
 // launch tracing: bracket a launch with events when the context traces
 struct TraceScope {

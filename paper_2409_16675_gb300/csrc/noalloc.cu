@@ -82,6 +82,7 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
     if (dev < 0 || dev >= kMaxDevices) return fail(c, HE_ERR_INVALID_ARG, "device ordinal out of range");
     int rc = cuda_check(c, cudaSetDevice(dev), "cudaSetDevice");
     if (rc) return rc;
+    TraceRole tr_("cpmul_noalloc");
     const int N = c->N, L = c->L, T = p->info.T, G = p->info.G, M = p->info.MG;
     const size_t LN = (size_t)L * N;
     const long long nX = ct_x ? (long long)batch * T * G * 2 : 0;

@@ -171,10 +171,29 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
     pw[0] = ipw[0] = 1;
     for (int e = 1; e < 2 * N; e++) { pw[e] = mulmod(pw[e - 1], psi, q); ipw[e] = mulmod(ipw[e - 1], psiinv, q); }
     for (int k = 0; k < N; k++) {
-        fw[2 * k] = pw[bitrev(k, logN)];
-        fw[2 * k + 1] = shoup_c(fw[2 * k], q);
         zt[2 * k] = mulmod(mulmod(ipw[k], ninv, q), r64, q);
         zt[2 * k + 1] = shoup_c(zt[2 * k], q);
+    }
+    // forward factors psi^bitrev(2^s + i), each stage's groups permuted to the
+    // order its register pass reads them: passes of RB stages from the top
+    // bit down, the last pass holding the remaining RL stages; in a pass, the
+    // stage at position st acts on register bit kb = S - 1 - st and its group
+    // index is i = h 2^gb + g with g the gb = RB - 1 - kb register bits above
+    // kb and h = the thread's bits above the register window
+    {
+        const int RB = kNttTileBits, NP = (logN + RB - 1) / RB, RL = logN - RB * (NP - 1);
+        for (int pass = 0; pass < NP; pass++) {
+            const int S = pass == NP - 1 ? RL : RB;
+            for (int st = 0; st < S; st++) {
+                const int s = RB * pass + st, gb = RB - 1 - (S - 1 - st);
+                for (int i = 0; i < (1 << s); i++) {
+                    const int g = i & ((1 << gb) - 1), h = i >> gb;
+                    const size_t pos = (size_t)(1 << s) + ((size_t)g << (s - gb)) + h;
+                    fw[2 * pos] = pw[bitrev((1 << s) + i, logN)];
+                    fw[2 * pos + 1] = shoup_c(fw[2 * pos], q);
+                }
+            }
+        }
     }
     // inverse stage s: omega^-(k 2^(n-1-s)) = psi^-(k 2^(n-s)) for k < 2^s
     for (int s = 0; s < logN; s++)
