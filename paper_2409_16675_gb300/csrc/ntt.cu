@@ -238,9 +238,12 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 
 // reduced.  Every M.fold products the sum is folded exactly to below q, so
 // the final sum stays below q (1 + (M.fold - 1) q) <= q 2^64.  The
 // finished groups wait in shared memory (the exchange buffer is idle until
-// the inverse transform; thread tau owns slots k*T + tau), so the registers go
-// to loads in flight: the term loop is unrolled by two.  The caller's shared
-// buffer must be free on entry (no thread still reading a previous exchange).
+// the inverse transform), so the registers go to loads in flight: the term
+// loop is unrolled by two.  Thread tau parks coefficient k in the slot its
+// inverse transform's first exchange (from the window at bit 0) writes
+// register k to, so no thread touches another's slots before that exchange
+// and no CTA barrier is needed here.  The caller's shared buffer must be
+// free on entry (no thread still reading a previous exchange).
 template <int LOGN, int CH>
 __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const u64 *__restrict__ B,
                                                const int32_t *__restrict__ ta, const int32_t *__restrict__ tb, int t0,
@@ -271,11 +274,11 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
             }
         }
 #pragma unroll
-        for (int kk = 0; kk < CH; kk++) sm[(part * CH + kk) * T + tau] = redc(lo[kk], hi[kk], M);
+        for (int kk = 0; kk < CH; kk++)
+            sm[padi<Cfg<LOGN>::RB>(jidx<Cfg<LOGN>::RB>(tau, part * CH + kk, 0))] = redc(lo[kk], hi[kk], M);
     }
 #pragma unroll
-    for (int k = 0; k < R; k++) v[k] = sm[k * T + tau];
-    __syncthreads();  // every stash is read before the transform's first exchange reuses the buffer
+    for (int k = 0; k < R; k++) v[k] = sm[padi<Cfg<LOGN>::RB>(jidx<Cfg<LOGN>::RB>(tau, k, 0))];
 }
 
 // Inverse transform: the register-tile bits [0, RB) first, then upward; the
