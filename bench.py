@@ -539,9 +539,11 @@ def batched_measure(steps, warmup, sample_every=16):
     """Config 4: 256 ct x pt convolution jobs of uneven shapes (channels
     {3,16,32,64,128}, spatial {8,16,32}, kernel {1,3,5}), N in {4096, 8192},
     2-5 limbs of 36-60 bits, both encodings.  ms per batch as one call per job
-    (plain), as persistent queue kernels, and replayed from a CUDA graph,
-    after the autotuner has picked the launch configuration; every
-    sample_every-th job's output compared across the three modes."""
+    (plain), as per-degree work-list launches (persistent), as one persistent
+    launch for the whole batch (fused), and replayed from a CUDA graph of the
+    faster of the last two, after the autotuner has picked the launch
+    configuration; every sample_every-th job's output compared across the
+    modes."""
     import torch
 
     from paper_2409_16675_gb300 import layer, native as nv, workloads as wl
@@ -574,8 +576,12 @@ def batched_measure(steps, warmup, sample_every=16):
         t0 = time.perf_counter()
         tuning = nv.he_batch_autotune(b)
         tune_s = time.perf_counter() - t0
-        for name, mode in (("plain", nv.HE_BATCH_PLAIN), ("persistent", nv.HE_BATCH_PERSISTENT),
-                           ("graph", nv.HE_BATCH_GRAPH)):
+        info = nv.he_batch_query(b)
+        modes = [("plain", nv.HE_BATCH_PLAIN), ("persistent", nv.HE_BATCH_PERSISTENT)]
+        if info["fused_supported"]:
+            modes.append(("fused", nv.HE_BATCH_FUSED))
+        modes.append(("graph", nv.HE_BATCH_GRAPH))
+        for name, mode in modes:
             for it in items:
                 it[4].zero_()
             for _ in range(max(1, warmup)):
@@ -588,6 +594,7 @@ def batched_measure(steps, warmup, sample_every=16):
             e1.record(s)
             s.synchronize()
             res[name] = e0.elapsed_time(e1) / steps
+            nv.he_batch_status(b)
             outs[name] = [it[4].clone() for it in items[::sample_every]]
     same = all(torch.equal(a, r) for m in outs for a, r in zip(outs[m], outs["plain"]))
     nv.he_batch_destroy(b)
@@ -599,6 +606,9 @@ def batched_measure(steps, warmup, sample_every=16):
             "jobs_per_s": {k: len(jobs) / (v / 1000.0) for k, v in res.items()},
             "speedup_vs_plain": {k: res["plain"] / v for k, v in res.items()},
             "identical_results": bool(same), "compared_jobs": len(outs["plain"]), "autotune": tuning,
+            "one_launch": {"graph_uses_it": bool(info["graph_fused"]), "regs_ctas_per_sm": info["fused_regs_ctas_per_sm"],
+                           "units": info["n_units"], "autotune_ms": info["fused_ms"],
+                           "per_degree_autotune_ms": info["per_degree_ms"]},
             "contexts": len(ctxs), "steps": steps, "warmup": warmup, "setup_s": setup_s, "autotune_s": tune_s}
 
 

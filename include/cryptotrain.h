@@ -346,8 +346,21 @@ int he_ct_add(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int n, uint64_t
  *               persistent CTAs that pull items from a device counter, or one
  *               CTA per item in list order, as he_batch_autotune measures best
  *               (default: persistent, 2 CTAs per SM);
- *   graph       that launch sequence captured once in a CUDA graph and
- *               replayed (needs a non-default stream).
+ *   fused       one persistent launch for the whole batch: both phases of
+ *               every job and both ring degrees (one degree, or two of which
+ *               one is half the other, up to 2^13).  CTAs of the larger
+ *               degree's tile take work units from one device counter: all
+ *               forward units first (an item of the larger degree, or two of
+ *               the smaller, one per half of the CTA), then the
+ *               multiply-accumulate units, heaviest first; each of those waits
+ *               until its job's forward items are counted done.  Every wait
+ *               is bounded (he_batch_set_wait_limit): a unit that runs out
+ *               writes HE_ERR_TIMEOUT to the batch's status word, skips its
+ *               work, and every CTA stops at its next claim;
+ *   graph       the faster of the persistent and the fused forms (as
+ *               he_batch_autotune measured; he_batch_set_fused overrides)
+ *               captured once in a CUDA graph and replayed (needs a
+ *               non-default stream).
  * Results are bit-identical in every form and to a job run alone.  The batch
  * owns one device allocation (made by he_batch_prepare) holding every job's
  * NTT-form operands, term tables and work lists; input and output pointers
@@ -356,6 +369,7 @@ int he_ct_add(he_ctx *ctx, const uint64_t *a, const uint64_t *b, int n, uint64_t
 #define HE_BATCH_PLAIN 0
 #define HE_BATCH_PERSISTENT 1
 #define HE_BATCH_GRAPH 2
+#define HE_BATCH_FUSED 3
 
 typedef struct he_batch he_batch;
 /* launch configuration chosen by he_batch_autotune for one ring degree */
@@ -399,6 +413,36 @@ int he_batch_autotune(he_batch *batch, cudaStream_t stream, he_batch_tuning *out
  * INVALID_ARG for a value out of range or a degree with no job; invalidates
  * a captured graph. */
 int he_batch_set_tuning(he_batch *batch, const he_batch_tuning *tuning, int n);
+
+/* The one-launch (fused) form: whether the batch's degrees allow it, whether
+ * the graph form uses it, its register budget (resident CTAs per SM: 1 or 2)
+ * and unit count, and the times he_batch_autotune measured for it and for the
+ * per-degree launches (0 before autotuning). */
+typedef struct he_batch_info {
+    int32_t fused_supported, graph_fused, fused_regs_ctas_per_sm, n_units;
+    float fused_ms, per_degree_ms;
+} he_batch_info;
+int he_batch_query(const he_batch *batch, he_batch_info *info);
+/* Make the graph form use the fused launch (graph_fused = 1) or the
+ * per-degree launches (0), and set the fused register budget (1 or 2; 0
+ * keeps it).  UNSUPPORTED_PARAMS if the degrees allow no fused form;
+ * invalidates a captured graph. */
+int he_batch_set_fused(he_batch *batch, int graph_fused, int regs_ctas_per_sm);
+/* Synchronise `stream` and read the status word of the fused form: HE_OK, or
+ * HE_ERR_TIMEOUT (message: the unit that gave up) if a unit of a fused run
+ * on it ran out of its wait limit; clears the word.  While the word holds a
+ * timeout every fused run stops at its first claim and does no work, so
+ * check it after fused or graph runs before trusting their outputs. */
+int he_batch_status(he_batch *batch, cudaStream_t stream);
+/* Polls (each followed by a sleep of at least 256 ns) of a job's counter
+ * before a multiply-accumulate unit of the fused form gives up (default
+ * 2^22, about a second or more); invalidates a captured graph. */
+int he_batch_set_wait_limit(he_batch *batch, long long polls);
+/* Test hook of the bounded wait: with hold = 1 the fused form waits for one
+ * more forward item of `job` than it has, so that job's multiply-accumulate
+ * units run out of their limit (the wait's failure path, made on the host
+ * without any fault); hold = 0 restores the count. */
+int he_batch_test_hold_job(he_batch *batch, int job, int hold);
 
 /* ------------------------------------------------------------------
  * Continuous-batching request server for CPMul convolution layers (the

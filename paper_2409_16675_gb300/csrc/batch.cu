@@ -8,8 +8,9 @@
 // transform and add.  The persistent form runs each list with one launch:
 // persistent CTAs pulling items from an atomic counter (heaviest items
 // first), or one CTA per item in list order, whichever the autotuner
-// measures faster; the graph form replays that launch sequence from a
-// captured CUDA graph.
+// measures faster.  The one-launch form (fused.cu) runs every degree's
+// forward and multiply-accumulate items in a single persistent launch; the
+// graph form replays whichever of the two the autotuner measured faster.
 // The plain form calls he_cpmul_conv once per job, for comparison.
 #include <algorithm>
 #include <cstdio>
@@ -108,6 +109,21 @@ struct he_batch {
     };
     std::vector<Class> classes;
     int *counters = nullptr;  // two per class
+    // the one-launch form (fused.cu): possible when the batch has one ring
+    // degree, or two of which one is half the other, and the larger is 2^12
+    // or 2^13
+    bool fused_ok = false;
+    int fused_big = 0;        // logN of the larger degree
+    int fused_minb = 2;       // register budget: resident CTAs per SM
+    bool graph_fused = false; // the graph and persistent forms use the one-launch form
+    he::FusedUnit *units = nullptr;
+    int n_units = 0;
+    int *fused_counter = nullptr;  // [1 + jobs]: unit counter, then each job's finished forward items
+    int *fwd_need = nullptr;       // per job: its forward items
+    int *status = nullptr;         // [2]
+    std::vector<int> need_host;
+    long long wait_limit = 1ll << 22;  // polls of 256 ns or more: a second or longer
+    float fused_ms = 0, per_degree_ms = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -138,6 +154,37 @@ int run_persistent(he_batch *b, cudaStream_t st) {
         if (rc) return bfail(b, rc, "multiply-accumulate queue launch");
     }
     return HE_OK;
+}
+
+he::FusedArgs fused_args(const he_batch *b) {
+    he::FusedArgs a;
+    memset(&a, 0, sizeof a);
+    for (const auto &k : b->classes) {
+        if (k.logN == b->fused_big) { a.fwd_big = k.fi; a.mac_big = k.mi; }
+        else { a.fwd_small = k.fi; a.mac_small = k.mi; }
+    }
+    a.units = b->units;
+    a.n_units = b->n_units;
+    a.counter = b->fused_counter;
+    a.fwd_done = b->fused_counter + 1;
+    a.fwd_need = b->fwd_need;
+    a.status = b->status;
+    a.wait_limit = b->wait_limit;
+    return a;
+}
+
+int run_fused(he_batch *b, cudaStream_t st, int minb) {
+    if (!b->fused_ok)
+        return bfail(b, HE_ERR_UNSUPPORTED_PARAMS,
+                     "one-launch form needs one ring degree, or two of which one is half the other, up to 2^13");
+    if (cudaMemsetAsync(b->fused_counter, 0, sizeof(int) * (1 + b->jobs.size()), st) != cudaSuccess)
+        return bfail(b, HE_ERR_CUDA, "counter reset");
+    const int rc = he::launch_fused(b->fused_big, minb, fused_args(b), b->n_sms * minb, st);
+    return rc ? bfail(b, rc, "fused launch") : HE_OK;
+}
+
+int run_batch_form(he_batch *b, cudaStream_t st) {
+    return b->graph_fused ? run_fused(b, st, b->fused_minb) : run_persistent(b, st);
 }
 
 void drop_graph(he_batch *b) {
@@ -225,25 +272,95 @@ int he_batch_prepare(he_batch *b) {
     off += al(2 * degrees.size() * sizeof(he::ItemSeg));
     const size_t cnt_off = off;
     off += al(2 * degrees.size() * sizeof(int));
+    // one-launch form: units, [counter][fwd_done per job], fwd_need per job, status
+    b->fused_ok = (degrees.size() == 1 && (degrees[0] == 12 || degrees[0] == 13)) ||
+                  (degrees.size() == 2 && degrees[1] == degrees[0] + 1 && (degrees[1] == 12 || degrees[1] == 13));
+    b->fused_big = degrees.empty() ? 0 : degrees.back();
+    const size_t units_off = off;
+    off += al((nf_total + nm_total) * sizeof(he::FusedUnit));
+    const size_t fcnt_off = off;
+    off += al((1 + b->jobs.size()) * sizeof(int));
+    const size_t need_off = off;
+    off += al(b->jobs.size() * sizeof(int));
+    const size_t status_off = off;
+    off += al(2 * sizeof(int));
     if (cudaMalloc(&b->mem, off) != cudaSuccess) return bfail(b, HE_ERR_OOM, "batch scratch allocation");
     char *base = (char *)b->mem;
     std::vector<std::vector<he::FwdItem>> F(degrees.size());
     std::vector<std::vector<he::MacItem>> Mi(degrees.size());
+    std::vector<std::vector<int>> Fjob(degrees.size()), Mjob(degrees.size());  // the job of each item
     std::vector<int32_t> terms;
+    b->need_host.assign(b->jobs.size(), 0);
     for (size_t j = 0; j < b->jobs.size(); j++) {
         const auto &J = b->jobs[j];
         const int ci = (int)(std::find(degrees.begin(), degrees.end(), J.c->logN) - degrees.begin());
         const he::JobLayout l = he::job_layout(J);
+        const size_t f0 = F[ci].size(), m0 = Mi[ci].size();
         he::job_items(J, base + job_off[j], terms, F[ci], Mi[ci]);
+        Fjob[ci].resize(F[ci].size(), (int)j);
+        Mjob[ci].resize(Mi[ci].size(), (int)j);
+        b->need_host[j] = (int)(F[ci].size() - f0);
+        (void)m0;
         if (cudaMemcpy(base + job_off[j] + l.a_bytes + l.b_bytes, terms.data(), terms.size() * 4,
                        cudaMemcpyHostToDevice) != cudaSuccess)
             return bfail(b, HE_ERR_CUDA, "term upload");
     }
-    // heaviest multiply-accumulate items first
-    for (auto &v : Mi)
-        std::stable_sort(v.begin(), v.end(), [](const he::MacItem &x, const he::MacItem &y) {
-            return (x.t1 - x.t0) > (y.t1 - y.t0);
-        });
+    // heaviest multiply-accumulate items first (the job of each item follows it)
+    for (size_t ci = 0; ci < degrees.size(); ci++) {
+        std::vector<size_t> perm(Mi[ci].size());
+        for (size_t i = 0; i < perm.size(); i++) perm[i] = i;
+        const auto &v = Mi[ci];
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](size_t x, size_t y) { return (v[x].t1 - v[x].t0) > (v[y].t1 - v[y].t0); });
+        std::vector<he::MacItem> sorted(v.size());
+        std::vector<int> sj(v.size());
+        for (size_t i = 0; i < perm.size(); i++) { sorted[i] = v[perm[i]]; sj[i] = Mjob[ci][perm[i]]; }
+        Mi[ci].swap(sorted);
+        Mjob[ci].swap(sj);
+    }
+    // one-launch units: every forward unit (an item of the larger degree, or
+    // two of the smaller), then the multiply-accumulate units, heaviest first
+    if (b->fused_ok) {
+        std::vector<he::FusedUnit> U;
+        const int cb = (int)degrees.size() - 1, cs = degrees.size() == 2 ? 0 : -1;
+        auto pairs = [&](int ci, int mac, std::vector<he::FusedUnit> &out) {
+            const size_t n = mac ? Mi[ci].size() : F[ci].size();
+            const std::vector<int> &jb = mac ? Mjob[ci] : Fjob[ci];
+            for (size_t i = 0; i < n; i += 2) {
+                he::FusedUnit u{mac, 0, {(int32_t)i, -1}, {jb[i], 0}};
+                if (i + 1 < n) { u.item[1] = (int32_t)(i + 1); u.job[1] = jb[i + 1]; }
+                out.push_back(u);
+            }
+        };
+        for (size_t i = 0; i < F[cb].size(); i++) U.push_back({0, 1, {(int32_t)i, -1}, {Fjob[cb][i], 0}});
+        if (cs >= 0) pairs(cs, 0, U);
+        std::vector<he::FusedUnit> small_mac;
+        if (cs >= 0) pairs(cs, 1, small_mac);
+        auto weight = [&](const he::FusedUnit &u) {
+            const auto &v = Mi[u.big ? cb : cs];
+            return v[u.item[0]].t1 - v[u.item[0]].t0;  // the first item of a pair is the heavier
+        };
+        size_t ib = 0, is = 0;
+        while (ib < Mi[cb].size() || is < small_mac.size()) {
+            const he::FusedUnit ub{1, 1, {(int32_t)ib, -1}, {ib < Mi[cb].size() ? Mjob[cb][ib] : 0, 0}};
+            if (is >= small_mac.size() || (ib < Mi[cb].size() && weight(ub) >= weight(small_mac[is]))) {
+                U.push_back(ub);
+                ib++;
+            } else {
+                U.push_back(small_mac[is++]);
+            }
+        }
+        b->n_units = (int)U.size();
+        b->units = (he::FusedUnit *)(base + units_off);
+        b->fused_counter = (int *)(base + fcnt_off);
+        b->fwd_need = (int *)(base + need_off);
+        b->status = (int *)(base + status_off);
+        if (cudaMemcpy(b->units, U.data(), U.size() * sizeof(he::FusedUnit), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(b->fwd_need, b->need_host.data(), b->need_host.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemset(b->status, 0, 2 * sizeof(int)) != cudaSuccess)
+            return bfail(b, HE_ERR_CUDA, "unit upload");
+    }
     size_t fo = items_off, mo = mitems_off;
     std::vector<he::ItemSeg> segs;
     b->classes.clear();
@@ -289,12 +406,15 @@ int he_batch_run(he_batch *b, int mode, cudaStream_t st) {
     }
     if (!b->prepared) return bfail(b, HE_ERR_INVALID_ARG, "he_batch_prepare first");
     if (mode == HE_BATCH_PERSISTENT) return run_persistent(b, st);
+    if (mode == HE_BATCH_FUSED) return run_fused(b, st, b->fused_minb);
     if (mode != HE_BATCH_GRAPH) return bfail(b, HE_ERR_INVALID_ARG, "bad mode");
     if (!b->exec || b->graph_stream != st) {
         drop_graph(b);
+        if (b->graph_fused && he::fused_set_attributes(b->fused_big, b->fused_minb))
+            return bfail(b, HE_ERR_CUDA, "fused kernel attributes");
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return bfail(b, HE_ERR_CUDA, "stream capture (a non-default stream is needed)");
-        int rc = run_persistent(b, st);
+        int rc = run_batch_form(b, st);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(st, &g);
         if (rc || e != cudaSuccess) {
@@ -374,6 +494,40 @@ int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int ma
         k.grid_mult = bg;
         k.best_ms = best;
     }
+    b->per_degree_ms = 0;
+    for (const auto &k : b->classes) b->per_degree_ms += k.best_ms;
+    // the one-launch form at both register budgets, three runs each
+    b->fused_ms = 0;
+    if (b->fused_ok) {
+        float best = 1e30f;
+        int bm = b->fused_minb;
+        for (int mb = 1; mb <= 2; mb++) {
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 3; rep++) {
+                cudaEventRecord(e0, st);
+                int rc = run_fused(b, st, mb);
+                cudaEventRecord(e1, st);
+                if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return bfail(b, rc ? rc : HE_ERR_CUDA, "autotune of the one-launch form");
+                }
+                float ms;
+                cudaEventElapsedTime(&ms, e0, e1);
+                tmin = std::min(tmin, ms);
+            }
+            if (tmin < best) { best = tmin; bm = mb; }
+        }
+        int st_h[2] = {0, 0};
+        if (cudaMemcpy(st_h, b->status, sizeof st_h, cudaMemcpyDeviceToHost) != cudaSuccess || st_h[0]) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bfail(b, st_h[0] ? st_h[0] : HE_ERR_CUDA, "one-launch form gave up waiting during autotuning");
+        }
+        b->fused_minb = bm;
+        b->fused_ms = best;
+        b->graph_fused = best < b->per_degree_ms;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_out) *n_out = (int)b->classes.size();
@@ -385,6 +539,60 @@ int he_batch_autotune(he_batch *b, cudaStream_t st, he_batch_tuning *out, int ma
         out[i].fwd_items = b->classes[i].nf;
         out[i].mac_items = b->classes[i].nm;
     }
+    return HE_OK;
+}
+
+int he_batch_query(const he_batch *b, he_batch_info *info) {
+    if (!b || !info) return HE_ERR_INVALID_ARG;
+    memset(info, 0, sizeof *info);
+    info->fused_supported = b->fused_ok;
+    info->graph_fused = b->graph_fused;
+    info->fused_regs_ctas_per_sm = b->fused_minb;
+    info->n_units = b->n_units;
+    info->fused_ms = b->fused_ms;
+    info->per_degree_ms = b->per_degree_ms;
+    return HE_OK;
+}
+
+int he_batch_set_fused(he_batch *b, int graph_fused, int regs_ctas_per_sm) {
+    if (!b || regs_ctas_per_sm < 0 || regs_ctas_per_sm > 2) return HE_ERR_INVALID_ARG;
+    if (!b->prepared) return bfail(b, HE_ERR_INVALID_ARG, "he_batch_prepare first");
+    if (graph_fused && !b->fused_ok) return bfail(b, HE_ERR_UNSUPPORTED_PARAMS, "no one-launch form for these degrees");
+    b->graph_fused = graph_fused != 0;
+    if (regs_ctas_per_sm) b->fused_minb = regs_ctas_per_sm;
+    drop_graph(b);
+    return HE_OK;
+}
+
+int he_batch_status(he_batch *b, cudaStream_t st) {
+    if (!b) return HE_ERR_INVALID_ARG;
+    if (!b->prepared || !b->status) return HE_OK;
+    if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return bfail(b, HE_ERR_CUDA, "stream synchronisation");
+    int h[2] = {0, 0};
+    if (cudaMemcpy(h, b->status, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(b->status, 0, sizeof h) != cudaSuccess)
+        return bfail(b, HE_ERR_CUDA, "status read");
+    if (h[0])
+        return bfail(b, h[0], "one-launch form: work unit " + std::to_string(h[1]) +
+                                  " gave up waiting for its job's forward transforms");
+    return HE_OK;
+}
+
+int he_batch_set_wait_limit(he_batch *b, long long polls) {
+    if (!b || polls < 1) return HE_ERR_INVALID_ARG;
+    b->wait_limit = polls;
+    drop_graph(b);
+    return HE_OK;
+}
+
+int he_batch_test_hold_job(he_batch *b, int job, int hold) {
+    if (!b || job < 0 || job >= (int)b->jobs.size()) return HE_ERR_INVALID_ARG;
+    if (!b->prepared || !b->fused_ok) return bfail(b, HE_ERR_INVALID_ARG, "prepared one-launch batch needed");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HE_ERR_CUDA, "cudaSetDevice");
+    const int need = b->need_host[job] + (hold ? 1 : 0);
+    if (cudaMemcpy(b->fwd_need + job, &need, sizeof need, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, HE_ERR_CUDA, "hold");
     return HE_OK;
 }
 

@@ -278,6 +278,35 @@ struct MacItem {            // multiply-accumulate + inverse NTT + add of one ou
     const u64 *add;         // this limb's addend or null
     const ModDev *mod;
 };
+// The batched form as one persistent launch (fused.cu): a unit is one work
+// item of the larger ring degree of the batch (the whole CTA) or up to two
+// items of the degree half its size (one per half of the CTA).  Forward
+// units come first; a multiply-accumulate unit starts once every forward item
+// of its job has been counted in fwd_done.
+struct FusedUnit {
+    int32_t mac;      // 0: forward items, 1: multiply-accumulate items
+    int32_t big;      // 1: one item of the larger degree; 0: up to two of the smaller
+    int32_t item[2];  // indices into that degree's forward or MAC item list (-1: none)
+    int32_t job[2];   // job of each item
+};
+struct FusedArgs {
+    const FwdItem *fwd_big, *fwd_small;
+    const MacItem *mac_big, *mac_small;
+    const FusedUnit *units;
+    int n_units;
+    int *counter;          // next unit (zero at launch)
+    int *fwd_done;         // per job: forward items finished (zero at launch)
+    const int *fwd_need;   // per job: forward items to wait for
+    int *status;           // [0]: 0 or HE_ERR_TIMEOUT, [1]: the unit that gave up
+    long long wait_limit;  // polls of a job's counter before a unit gives up
+};
+// Launch the fused kernel whose larger degree is 2^logN_big (12 or 13),
+// compiled for minb (1 or 2) resident CTAs per SM, with `grid` CTAs.
+int launch_fused(int logN_big, int minb, const FusedArgs &a, int grid, cudaStream_t st);
+// Set the fused kernel's per-device attributes (done by its first launch;
+// called before a stream capture so that nothing but the launch is captured).
+int fused_set_attributes(int logN_big, int minb);
+
 // One CPMul convolution job (he_cpmul_conv arguments) for the work-list forms.
 struct JobDesc {
     he_ctx *c;

@@ -25,7 +25,7 @@ HE_ROLE_INPUT, HE_ROLE_KERNEL = 0, 1
 HE_DTYPE_U8, HE_DTYPE_I8, HE_DTYPE_I64 = 0, 1, 2
 HE_PLAN_DEPTHWISE = 16
 HE_KEY_SK, HE_KEY_PK, HE_KEY_RLK = 0, 1, 2
-HE_BATCH_PLAIN, HE_BATCH_PERSISTENT, HE_BATCH_GRAPH = 0, 1, 2
+HE_BATCH_PLAIN, HE_BATCH_PERSISTENT, HE_BATCH_GRAPH, HE_BATCH_FUSED = 0, 1, 2, 3
 
 
 class HEError(RuntimeError):
@@ -54,6 +54,12 @@ class he_conv_shape(ctypes.Structure):
 class he_trace_entry(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("modmuls", ctypes.c_double)]
+
+
+class he_batch_info(ctypes.Structure):
+    _fields_ = [("fused_supported", ctypes.c_int32), ("graph_fused", ctypes.c_int32),
+                ("fused_regs_ctas_per_sm", ctypes.c_int32), ("n_units", ctypes.c_int32),
+                ("fused_ms", ctypes.c_float), ("per_degree_ms", ctypes.c_float)]
 
 
 class he_batch_tuning(ctypes.Structure):
@@ -126,6 +132,11 @@ def _load():
         "he_batch_autotune": [vp, vp, ctypes.POINTER(he_batch_tuning), i32, ctypes.POINTER(i32)],
         "he_batch_add_cpmul2": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp],
         "he_batch_set_tuning": [vp, ctypes.POINTER(he_batch_tuning), i32],
+        "he_batch_query": [vp, ctypes.POINTER(he_batch_info)],
+        "he_batch_set_fused": [vp, i32, i32],
+        "he_batch_status": [vp, vp],
+        "he_batch_set_wait_limit": [vp, ctypes.c_int64],
+        "he_batch_test_hold_job": [vp, i32, i32],
         "he_server_create": [ctypes.POINTER(he_server_config), pp],
         "he_server_submit": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)],
         "he_server_poll": [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
@@ -407,6 +418,30 @@ def he_batch_autotune(b):
     _bcheck(lib.he_batch_autotune(b, _stream(), arr, 8, ctypes.byref(n)), b)
     return [dict(logN=arr[i].logN, regs_ctas_per_sm=arr[i].regs_ctas_per_sm, grid_ctas_per_sm=arr[i].grid_ctas_per_sm,
                  ms=arr[i].ms, fwd_items=arr[i].fwd_items, mac_items=arr[i].mac_items) for i in range(min(n.value, 8))]
+
+
+def he_batch_query(b) -> dict:
+    info = he_batch_info()
+    _bcheck(lib.he_batch_query(b, ctypes.byref(info)), b)
+    return {f: getattr(info, f) for f, _ in he_batch_info._fields_}
+
+
+def he_batch_set_fused(b, graph_fused, regs_ctas_per_sm=0):
+    _bcheck(lib.he_batch_set_fused(b, int(graph_fused), regs_ctas_per_sm), b)
+
+
+def he_batch_status(b):
+    """Synchronise the current stream and raise HEError (HE_ERR_TIMEOUT) if a
+    fused run gave up waiting; clears the status."""
+    _bcheck(lib.he_batch_status(b, _stream()), b)
+
+
+def he_batch_set_wait_limit(b, polls):
+    _bcheck(lib.he_batch_set_wait_limit(b, int(polls)), b)
+
+
+def he_batch_test_hold_job(b, job, hold):
+    _bcheck(lib.he_batch_test_hold_job(b, job, int(hold)), b)
 
 
 def he_batch_last_error(b) -> str:

@@ -157,3 +157,82 @@ def test_full_config4_batch_sampled_against_the_oracle():
         p.close()
     for c in ctxs.values():
         c.close()
+
+
+def _mixed_batch(seed=123, n_jobs=14):
+    jobs = wl.batched_jobs(seed=seed, n_jobs=n_jobs, channels=(3, 5, 16), sizes=(6, 8, 12), kernels=(1, 3, 5),
+                           degrees=(4096, 8192))
+    ctxs, items = build(jobs, B=2)
+    b = nv.he_batch_create(0)
+    for (c, p, ct, pt, out) in items:
+        nv.he_batch_add_cpmul(b, c.h, p.h, 2, ct, pt, None, out)
+    nv.he_batch_prepare(b)
+    return ctxs, items, b
+
+
+def test_fused_one_launch_form_bits():
+    """The whole batch (N = 4096 and 8192 jobs, both phases) in one persistent
+    launch, at both register budgets and replayed from a CUDA graph, gives
+    the plain form's bits on every run, and its status stays clear."""
+    ctxs, items, b = _mixed_batch()
+    info = nv.he_batch_query(b)
+    assert info["fused_supported"] == 1 and info["n_units"] > 0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nv.he_batch_run(b, nv.HE_BATCH_PLAIN)
+        s.synchronize()
+        ref = [it[4].clone() for it in items]
+        for regs in (1, 2):
+            nv.he_batch_set_fused(b, True, regs)
+            for mode in (nv.HE_BATCH_FUSED, nv.HE_BATCH_FUSED, nv.HE_BATCH_GRAPH, nv.HE_BATCH_GRAPH):
+                for it in items:
+                    it[4].zero_()
+                nv.he_batch_run(b, mode)
+                nv.he_batch_status(b)
+                for it, r in zip(items, ref):
+                    assert torch.equal(it[4], r), (regs, mode)
+        tuning = nv.he_batch_autotune(b)
+        info = nv.he_batch_query(b)
+        assert tuning and info["fused_ms"] > 0 and info["per_degree_ms"] > 0
+        for it in items:
+            it[4].zero_()
+        nv.he_batch_run(b, nv.HE_BATCH_GRAPH)
+        nv.he_batch_status(b)
+        for it, r in zip(items, ref):
+            assert torch.equal(it[4], r)
+    nv.he_batch_destroy(b)
+    for c in ctxs.values():
+        c.close()
+
+
+def test_fused_wait_limit_gives_up_and_recovers():
+    """A job whose forward count is held one short (a host-side hold: its
+    multiply-accumulate units can never start) makes those units run out of a
+    short wait limit: the run reports HE_ERR_TIMEOUT, the held job's outputs
+    are never written, and after the hold is released the same batch runs to
+    the plain form's bits."""
+    ctxs, items, b = _mixed_batch(seed=77, n_jobs=6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        nv.he_batch_run(b, nv.HE_BATCH_PLAIN)
+        s.synchronize()
+        ref = [it[4].clone() for it in items]
+        for it in items:
+            it[4].zero_()
+        nv.he_batch_set_wait_limit(b, 2000)
+        nv.he_batch_test_hold_job(b, 0, True)
+        nv.he_batch_run(b, nv.HE_BATCH_FUSED)
+        with pytest.raises(nv.HEError) as e:
+            nv.he_batch_status(b)
+        assert e.value.code == -6 and "gave up" in str(e.value)
+        assert not bool(items[0][4].view(torch.int64).any())
+        nv.he_batch_status(b)                     # the status was cleared by the read
+        nv.he_batch_test_hold_job(b, 0, False)
+        nv.he_batch_set_wait_limit(b, 1 << 22)
+        nv.he_batch_run(b, nv.HE_BATCH_FUSED)
+        nv.he_batch_status(b)
+        for it, r in zip(items, ref):
+            assert torch.equal(it[4], r)
+    nv.he_batch_destroy(b)
+    for c in ctxs.values():
+        c.close()
