@@ -518,6 +518,28 @@ typedef struct he_trace_entry {
 int he_trace_enable(he_ctx *ctx, int on);
 int he_trace_read(he_ctx *ctx, he_trace_entry *out, int max_entries, int *n_entries);
 
+/* ------------------------------------------------------------------
+ * Bounds-checked debug build (a sanitizer stand-in; the paper has no
+ * counterpart).  libcryptotrain_checks.so is the same library compiled with
+ * every kernel's global loads and stores checked against the device ranges
+ * the call may touch: the library's own allocations and the allocations that
+ * hold the call's device pointers.  An access outside them is skipped (a load
+ * yields zero, a store does nothing; nothing traps), and the entry point
+ * returns HE_ERR_INVALID_ARG after synchronising the device.  Kernels run
+ * several times slower; the request server's asynchronous launches are
+ * reported by the next call.
+ *   he_checks_enabled      1 in the checks build, 0 otherwise.
+ *   he_checks_last_error   the first violation of the last failing call:
+ *                          source file and line, address.
+ *   he_checks_test_exclude (test hook) leave [ptr, ptr + bytes) out of the
+ *                          ranges, so that accesses to that valid memory are
+ *                          reported and skipped; ptr = NULL clears it.
+ *                          UNSUPPORTED_PARAMS outside the checks build.
+ * ------------------------------------------------------------------ */
+int he_checks_enabled(void);
+int he_checks_last_error(char *buf, int len);
+int he_checks_test_exclude(const void *ptr, long long bytes);
+
 #ifdef __cplusplus
 }
 #endif

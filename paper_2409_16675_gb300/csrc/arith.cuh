@@ -7,6 +7,7 @@
 // a*w - floor(a w' / 2^64)*q lies in [0, 2q) for every 64-bit a.
 #pragma once
 #include "internal.h"
+#include "checks.cuh"
 
 namespace he {
 

@@ -217,7 +217,7 @@ int he_batch_destroy(he_batch *b) {
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     drop_graph(b);
-    if (b->mem) cudaFree(b->mem);
+    if (b->mem) he::dev_free(b->mem);
     delete b;
     return HE_OK;
 }
@@ -284,7 +284,7 @@ int he_batch_prepare(he_batch *b) {
     off += al(b->jobs.size() * sizeof(int));
     const size_t status_off = off;
     off += al(2 * sizeof(int));
-    if (cudaMalloc(&b->mem, off) != cudaSuccess) return bfail(b, HE_ERR_OOM, "batch scratch allocation");
+    if (he::dev_alloc((void **)&b->mem, off) != cudaSuccess) return bfail(b, HE_ERR_OOM, "batch scratch allocation");
     char *base = (char *)b->mem;
     std::vector<std::vector<he::FwdItem>> F(degrees.size());
     std::vector<std::vector<he::MacItem>> Mi(degrees.size());

@@ -36,10 +36,10 @@ static int ws_reserve(he_ctx *c, size_t bytes) {
     size_t want = bytes + bytes / 4 + (1 << 20);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_check(c, e, "sync before workspace growth");
-    if (c->ws) cudaFree(c->ws);
+    if (c->ws) he::dev_free(c->ws);
     c->ws = nullptr;
     c->ws_size = 0;
-    e = cudaMalloc(&c->ws, want);
+    e = he::dev_alloc((void **)&c->ws, want);
     if (e != cudaSuccess) return cuda_check(c, e, "workspace cudaMalloc");
     c->ws_size = want;
     return HE_OK;
@@ -64,10 +64,10 @@ static const void *cached_table(he_ctx *c, const void *data, size_t bytes, int *
     auto it = c->table_cache.find(key);
     if (it != c->table_cache.end()) { *rc = HE_OK; return it->second; }
     void *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, bytes ? bytes : 8);
+    cudaError_t e = he::dev_alloc((void **)&d, bytes ? bytes : 8);
     if (e != cudaSuccess) { *rc = cuda_check(c, e, "table cudaMalloc"); return nullptr; }
     e = cudaMemcpy(d, data, bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { cudaFree(d); *rc = cuda_check(c, e, "table upload"); return nullptr; }
+    if (e != cudaSuccess) { he::dev_free(d); *rc = cuda_check(c, e, "table upload"); return nullptr; }
     c->table_cache.emplace(std::move(key), d);
     c->table_cache_bytes += bytes;
     *rc = HE_OK;
@@ -181,7 +181,7 @@ static int set_device(he_ctx *c) {
     if (c->table_cache_bytes > cap) {
         rc = cuda_check(c, cudaDeviceSynchronize(), "sync before dropping cached tables");
         if (rc) return rc;
-        for (auto &kv : c->table_cache) cudaFree(kv.second);
+        for (auto &kv : c->table_cache) he::dev_free(kv.second);
         c->table_cache.clear();
         c->table_cache_bytes = 0;
     }
@@ -220,11 +220,11 @@ int he_ctx_destroy(he_ctx *c) {
     if (!c) return HE_OK;
     cudaSetDevice(c->P.device);
     cudaDeviceSynchronize();
-    for (void *p : c->allocs) cudaFree(p);
-    for (auto &kv : c->table_cache) cudaFree(kv.second);
-    if (c->d_mods) cudaFree(c->d_mods);
-    if (c->d_exact) cudaFree(c->d_exact);
-    if (c->ws) cudaFree(c->ws);
+    for (void *p : c->allocs) he::dev_free(p);
+    for (auto &kv : c->table_cache) he::dev_free(kv.second);
+    if (c->d_mods) he::dev_free(c->d_mods);
+    if (c->d_exact) he::dev_free(c->d_exact);
+    if (c->ws) he::dev_free(c->ws);
     delete c;
     return HE_OK;
 }
@@ -265,7 +265,7 @@ int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStrea
     const size_t LN = (size_t)L * N;
     he_keys *k = new he_keys();
     k->L = L; k->N = N; k->ell = ell; k->device = c->P.device; k->fp = c->fp;
-    auto alloc = [&](u64 **p, size_t n) { return cudaMalloc((void **)p, n * 8) == cudaSuccess; };
+    auto alloc = [&](u64 **p, size_t n) { return he::dev_alloc((void **)p, n * 8) == cudaSuccess; };
     if (!alloc(&k->sk, N) || !alloc(&k->s_ntt, LN) || !alloc(&k->pk, 2 * LN) || !alloc(&k->pk_ntt, 2 * LN) ||
         (ell && (!alloc(&k->rlk, (size_t)ell * 2 * LN) || !alloc(&k->rlk_ntt, (size_t)ell * 2 * LN)))) {
         he_keys_destroy(k);
@@ -351,7 +351,7 @@ int he_keys_import(he_ctx *c, const int64_t *sk, const uint64_t *pk, const uint6
     const size_t LN = (size_t)L * N;
     he_keys *k = new he_keys();
     k->L = L; k->N = N; k->ell = ell; k->device = c->P.device; k->fp = c->fp;
-    auto alloc = [&](u64 **p, size_t n) { return cudaMalloc((void **)p, n * 8) == cudaSuccess; };
+    auto alloc = [&](u64 **p, size_t n) { return he::dev_alloc((void **)p, n * 8) == cudaSuccess; };
     if (!alloc(&k->sk, N) || !alloc(&k->s_ntt, LN) || !alloc(&k->pk, 2 * LN) || !alloc(&k->pk_ntt, 2 * LN) ||
         (ell && (!alloc(&k->rlk, (size_t)ell * 2 * LN) || !alloc(&k->rlk_ntt, (size_t)ell * 2 * LN)))) {
         he_keys_destroy(k);
@@ -410,7 +410,7 @@ int he_keys_destroy(he_keys *k) {
     cudaDeviceSynchronize();
     u64 *ps[] = {k->sk, k->s_ntt, k->pk, k->pk_ntt, k->rlk, k->rlk_ntt};
     for (u64 *p : ps)
-        if (p) cudaFree(p);
+        if (p) he::dev_free(p);
     delete k;
     return HE_OK;
 }
@@ -607,9 +607,9 @@ int he_conv_plan(he_ctx *c, const he_conv_shape *s, int encoding, he_plan **out)
 
 int he_plan_destroy(he_plan *p) {
     if (!p) return HE_OK;
-    if (p->in_map) cudaFree(p->in_map);
-    if (p->ker_map) cudaFree(p->ker_map);
-    if (p->out_map) cudaFree(p->out_map);
+    if (p->in_map) he::dev_free(p->in_map);
+    if (p->ker_map) he::dev_free(p->ker_map);
+    if (p->out_map) he::dev_free(p->out_map);
     delete p;
     return HE_OK;
 }
@@ -879,6 +879,17 @@ int he_ct_add(he_ctx *c, const uint64_t *a, const uint64_t *b, int n, uint64_t *
     TRY(set_device(c));
     return launch_ct_add(c, a, b, (long long)n * 2, out, st);
 }
+
+#ifndef HE_CHECKS
+// the bounds-checked build's calls (checks.cpp); this build has no checks
+int he_checks_enabled(void) { return 0; }
+int he_checks_last_error(char *buf, int len) {
+    if (!buf || len <= 0) return HE_ERR_INVALID_ARG;
+    buf[0] = 0;
+    return HE_OK;
+}
+int he_checks_test_exclude(const void *, long long) { return HE_ERR_UNSUPPORTED_PARAMS; }
+#endif
 
 int he_trace_enable(he_ctx *c, int on) {
     if (!c) return HE_ERR_INVALID_ARG;

@@ -32,10 +32,11 @@ __device__ __forceinline__ void sample_block(int kind, uint64_t seed, uint32_t t
         const long long obj = ol / n_limbs;
         u64 w[8];
         chacha_block8(seed, tag, idx0 + (uint32_t)obj, (uint32_t)limb, (uint32_t)b, w);
+        if (!HE_OBJ_OK(mods + limb)) return;
         const ModDev M = mods[limb];
         u64 *o = (u64 *)out + (obj * n_limbs + limb) * N + 4 * b;
 #pragma unroll
-        for (int j = 0; j < 4; j++) o[j] = reduce128(w[2 * j], w[2 * j + 1], M);
+        for (int j = 0; j < 4; j++) HE_ST(o + j, reduce128(w[2 * j], w[2 * j + 1], M));
         return;
     }
     const int per = N / 8;
@@ -44,9 +45,10 @@ __device__ __forceinline__ void sample_block(int kind, uint64_t seed, uint32_t t
     u64 w[8];
     chacha_block8(seed, tag, idx0 + (uint32_t)obj, 0u, (uint32_t)b, w);
     if (kind == SAMPLE_UNIFORM_T) {
+        if (!HE_OBJ_OK(E)) return;
         u64 *o = (u64 *)out + obj * N + 8 * b;
 #pragma unroll
-        for (int j = 0; j < 8; j++) o[j] = reduce64(w[j], E->t, E->one_ts);
+        for (int j = 0; j < 8; j++) HE_ST(o + j, reduce64(w[j], E->t, E->one_ts));
         return;
     }
     int8_t r[8];
@@ -62,7 +64,7 @@ __device__ __forceinline__ void sample_block(int kind, uint64_t seed, uint32_t t
     u64 packed = 0;
 #pragma unroll
     for (int j = 0; j < 8; j++) packed |= (u64)(uint8_t)r[j] << (8 * j);
-    *(u64 *)o = packed;
+    HE_ST((u64 *)o, packed);
 }
 
 __global__ void k_sample(int kind, uint64_t seed, uint32_t tag, uint32_t idx0, int n_limbs, int N, void *out,
@@ -145,20 +147,21 @@ __global__ void __launch_bounds__(128) k_base_extend(const u64 *__restrict__ src
                                                      const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= n_polys * N) return;
+    if (!HE_OBJ_OK(E) || !HE_SPAN_OK(mods, L + K)) return;
     const int x = (int)(gid % N);
     const long long p = gid / N;
     const CrtDev &Q = E->Q;
     u64 y[LM];
 #pragma unroll
     for (int i = 0; i < LM; i++)
-        if (i < L) y[i] = crt_y(Q, i, src[(p * L + i) * N + x]);
+        if (i < L) y[i] = crt_y(Q, i, HE_LD(src + (p * L + i) * N + x));
     int v;
     u64 fr;
     if (crt_overflow<LM>(E->Qc, y, L, v, fr) && half_certain(fr)) {
         const u64 k = (u64)v + (fr >= (1ull << 57));
 #pragma unroll
         for (int j = 0; j < KM; j++)
-            if (j < K) dst[(p * K + j) * N + x] = conv_to_m<LM>(y, L, E->QhatBm[j], k, E->Q_b[j], E->Q_bs[j], mods[L + j]);
+            if (j < K) HE_ST(dst + (p * K + j) * N + x, conv_to_m<LM>(y, L, E->QhatBm[j], k, E->Q_b[j], E->Q_bs[j], mods[L + j]));
         return;
     }
     u64 X[MW];
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(128) k_base_extend(const u64 *__restrict__ src
         const ModDev &M = mods[L + j];
         u64 a = mw_mod<MW>(X, Q.W, M.q, M.r64, M.r64s, M.one_s);
         if (neg) a = subm(a, E->Q_b[j], M.q);
-        dst[(p * K + j) * N + x] = a;
+        HE_ST(dst + (p * K + j) * N + x, a);
     }
 }
 
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
                                                      const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n_out * 3 * N) return;
+    if (!HE_OBJ_OK(E) || !HE_SPAN_OK(mods, L + K)) return;
     const int x = (int)(gid % N);
     const int j = (int)((gid / N) % 3);
     const long long o = gid / (3LL * N);
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
     for (int i = 0; i < LM; i++)
         if (i < L) {
             const u64 qi = mods[i].q;
-            y[i] = addm(red1(shoup(src[(long long)i * N], E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
+            y[i] = addm(red1(shoup(HE_LD(src + (long long)i * N), E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
         }
     // r c_k mod b_k (c_k = q^-1 (B/b_k)^-1 mod b_k folded into the conversion)
     u64 rc[KM];
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
     for (int k = 0; k < KM; k++)
         if (k < K) {
             const u64 b = mods[L + k].q;
-            const u64 td = red1(shoup(src[(long long)(L + k) * N], E->f_tb[k], E->f_tbs[k], b), b);
+            const u64 td = red1(shoup(HE_LD(src + (long long)(L + k) * N), E->f_tb[k], E->f_tbs[k], b), b);
             yb[k] = subm(addm(td, E->f_hb[k], b), rc[k], b);
         }
     // centred F mod q_i; for the digit component (j = 2) directly its CRT
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
         u64 *out = dq + ((o * 2 + j) * L) * N + x;
 #pragma unroll
         for (int i = 0; i < LM; i++)
-            if (i < L) out[(long long)i * N] = f[i];
+            if (i < L) HE_ST(out + (long long)i * N, f[i]);
         return;
     }
     // digits of [F]_q in [0, q): exact multi-word value
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
         for (int k = 0; k < MW; k++)
 #pragma unroll
             for (int s4 = 0; s4 < 4; s4++)
-                if (4 * k + s4 < ell) dg[(long long)(4 * k + s4) * N] = (uint32_t)((X[k] >> (16 * s4)) & 0xffff);
+                if (4 * k + s4 < ell) HE_ST(dg + (long long)(4 * k + s4) * N, (uint32_t)((X[k] >> (16 * s4)) & 0xffff));
         return;
     }
     for (int dd = 0; dd < ell; dd++) {
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(128, (LM <= 4 ? 8 : 1)) k_scale_round(const u6
             if (k == w) val = X[k] >> sh;
             if (k == w + 1 && sh + base_log2 > 64) val |= X[k] << (64 - sh);
         }
-        dg[(long long)dd * N] = (uint32_t)(val & dmask);
+        HE_ST(dg + (long long)dd * N, (uint32_t)(val & dmask));
     }
 }
 
@@ -297,6 +301,7 @@ __global__ void __launch_bounds__(128) k_decrypt_exact(const u64 *__restrict__ x
                                                        const ExactDev *__restrict__ E) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)n * N) return;
+    if (!HE_OBJ_OK(E) || !HE_SPAN_OK(mods, L)) return;
     const int x = (int)(gid % N);
     const long long k = gid / N;
     const CrtDev &Q = E->Q;
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(128) k_decrypt_exact(const u64 *__restrict__ x
     for (int i = 0; i < LM; i++)
         if (i < L) {
             const u64 qi = mods[i].q;
-            y[i] = addm(red1(shoup(xs[(k * L + i) * N + x], E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
+            y[i] = addm(red1(shoup(HE_LD(xs + (k * L + i) * N + x), E->f_tq[i], E->f_tqs[i], qi), qi), E->f_hq[i], qi);
         }
     const u64 t = E->t;
     u64 rt;
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(128) k_decrypt_exact(const u64 *__restrict__ x
         crt_compose<MW>(Q, y, R);
         rt = mw_mod<MW>(R, Q.W, t, E->r64_t, E->r64_ts, E->one_ts);
     }
-    m[k * N + x] = red1(shoup(subm(E->Qhalf_t, rt, t), E->Qinv_t, E->Qinv_ts, t), t);
+    HE_ST(m + k * N + x, red1(shoup(subm(E->Qhalf_t, rt, t), E->Qinv_t, E->Qinv_ts, t), t));
 }
 
 // kernel size class of a context: limb bounds and multi-word capacity
@@ -368,9 +373,9 @@ int launch_decrypt_exact(he_ctx *c, const u64 *x, int n, u64 *m, cudaStream_t st
 // ---------------------------------------------------------------- encode / decode
 __device__ __forceinline__ u64 to_t(const void *tensor, int dtype, long long i, u64 t) {
     long long v;
-    if (dtype == HE_DTYPE_U8) v = ((const uint8_t *)tensor)[i];
-    else if (dtype == HE_DTYPE_I8) v = ((const int8_t *)tensor)[i];
-    else v = ((const long long *)tensor)[i];
+    if (dtype == HE_DTYPE_U8) v = HE_LD((const uint8_t *)tensor + i);
+    else if (dtype == HE_DTYPE_I8) v = HE_LD((const int8_t *)tensor + i);
+    else v = HE_LD((const long long *)tensor + i);
     if (v >= 0) return (u64)v % t;
     const u64 r = (u64)(-(v + 1)) % t;  // -(v+1) >= 0, no overflow
     return t - 1 - r;
@@ -385,8 +390,8 @@ __global__ void k_encode_input(const int32_t *__restrict__ map, int n_polys, int
     if (gid >= per * batch) return;
     const long long b = gid / per;
     const long long r = gid - b * per;
-    const int idx = map[r];
-    out[b * out_batch_polys * N + r] = idx >= 0 ? to_t(tensor, dtype, b * tensor_stride + idx, t) : 0;
+    const int idx = HE_LD(map + r);
+    HE_ST(out + b * out_batch_polys * N + r, idx >= 0 ? to_t(tensor, dtype, b * tensor_stride + idx, t) : 0);
 }
 
 // kernel role: out[(mg*G + g)*N + x] = w[map[(mg*G + g)*N + x]] mod t (absolute index into w)
@@ -395,8 +400,8 @@ __global__ void k_encode_kernel(const int32_t *__restrict__ map, int G, int M, i
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (long long)G * N * M) return;
     (void)per_m;
-    const int idx = map[gid];
-    out[gid] = idx >= 0 ? to_t(tensor, dtype, idx, t) : 0;
+    const int idx = HE_LD(map + gid);
+    HE_ST(out + gid, idx >= 0 ? to_t(tensor, dtype, idx, t) : 0);
 }
 
 // out[(b*M + m)*HW + i] = centred((pt - sub)[b*polys*N + map[m*HW + i]] mod t),
@@ -407,15 +412,15 @@ __global__ void k_decode(const int32_t *__restrict__ map, int HW, int M, int pol
     if (gid >= (long long)batch * M * HW) return;
     const long long mi = gid % ((long long)M * HW);
     const long long b = gid / ((long long)M * HW);
-    const long long src = b * polys * N + map[mi];
-    u64 v = pt[src];
+    const long long src = b * polys * N + HE_LD(map + mi);
+    u64 v = HE_LD(pt + src);
     v = v >= t ? v % t : v;
     if (sub) {
-        u64 s = sub[src];
+        u64 s = HE_LD(sub + src);
         s = s >= t ? s % t : s;
         v = v >= s ? v - s : v + t - s;
     }
-    out[gid] = v > (t - 1) / 2 ? (long long)v - (long long)t : (long long)v;
+    HE_ST(out + gid, v > (t - 1) / 2 ? (long long)v - (long long)t : (long long)v);
 }
 
 // inverse of k_decode: out[b*polys*N + map[m*HW + i]] = values[(b*M + m)*HW + i] mod t
@@ -426,8 +431,8 @@ __global__ void k_encode_output(const int32_t *__restrict__ map, int HW, int M, 
     if (gid >= (long long)batch * M * HW) return;
     const long long mi = gid % ((long long)M * HW);
     const long long b = gid / ((long long)M * HW);
-    const long long v = values[gid];
-    out[b * polys * N + map[mi]] = v >= 0 ? (u64)v % t : t - 1 - (u64)(-(v + 1)) % t;
+    const long long v = HE_LD(values + gid);
+    HE_ST(out + b * polys * N + HE_LD(map + mi), v >= 0 ? (u64)v % t : t - 1 - (u64)(-(v + 1)) % t);
 }
 
 // ciphertext addition (CCAdd): out = a + b mod q_limb over n polynomials of L limbs
@@ -435,23 +440,24 @@ __global__ void k_ct_add(const u64 *__restrict__ a, const u64 *__restrict__ b, l
                          u64 *__restrict__ out, const ModDev *__restrict__ mods) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= total) return;
+    if (!HE_SPAN_OK(mods, L)) return;
     const u64 q = mods[(gid / N) % L].q;
-    out[gid] = addm(a[gid], b[gid], q);
+    HE_ST(out + gid, addm(HE_LD(a + gid), HE_LD(b + gid), q));
 }
 
 __global__ void k_pt_sub(const u64 *__restrict__ a, const u64 *__restrict__ b, long long n, u64 *__restrict__ out,
                          u64 t) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= n) return;
-    u64 x = a[gid], y = b[gid];
+    u64 x = HE_LD(a + gid), y = HE_LD(b + gid);
     x = x >= t ? x % t : x;
     y = y >= t ? y % t : y;
-    out[gid] = x >= y ? x - y : x + t - y;
+    HE_ST(out + gid, x >= y ? x - y : x + t - y);
 }
 
 __global__ void k_copy_sk(const int8_t *__restrict__ s8, long long *__restrict__ sk, int N) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid < N) sk[gid] = s8[gid];
+    if (gid < N) HE_ST(sk + gid, (long long)HE_LD(s8 + gid));
 }
 
 int launch_encode(he_ctx *c, const int32_t *map, int n_polys, int map_polys, const void *tensor, int dtype,
@@ -510,15 +516,16 @@ int launch_pt_sub(he_ctx *c, const u64 *a, const u64 *b, long long n, u64 *out, 
 __global__ void k_import_sk(const long long *__restrict__ sk, int N, int8_t *__restrict__ s8, int *bad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const long long v = sk[i];
-    if (v < -1 || v > 1) atomicOr(bad, 1);
-    s8[i] = (int8_t)(v < -1 ? -1 : (v > 1 ? 1 : v));
+    const long long v = HE_LD(sk + i);
+    if ((v < -1 || v > 1) && HE_OBJ_OK(bad)) atomicOr(bad, 1);
+    HE_ST(s8 + i, (int8_t)(v < -1 ? -1 : (v > 1 ? 1 : v)));
 }
 __global__ void k_check_residues(const u64 *__restrict__ a, long long total, int N, int L,
                                  const ModDev *__restrict__ mods, int *bad) {
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= total) return;
-    if (a[gid] >= mods[(gid / N) % L].q) atomicOr(bad, 2);
+    if (!HE_SPAN_OK(mods, L) || !HE_OBJ_OK(bad)) return;
+    if (HE_LD(a + gid) >= mods[(gid / N) % L].q) atomicOr(bad, 2);
 }
 
 int launch_import_sk(he_ctx *c, const int64_t *sk, int8_t *s8, int *bad, cudaStream_t st) {
@@ -538,3 +545,5 @@ int launch_copy_sk(he_ctx *c, const int8_t *s8, u64 *sk, cudaStream_t st) {
 }
 
 }  // namespace he
+
+HE_CHECKS_UNIT(exact)

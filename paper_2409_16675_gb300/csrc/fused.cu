@@ -33,6 +33,7 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 // Poll job's forward counter until it reaches fwd_need; false if the limit
 // ran out (status set) or another unit has already given up.
 __device__ bool fused_wait(const FusedArgs &a, int job, int unit) {
+    if (!HE_OBJ_OK(a.fwd_need + job) || !HE_OBJ_OK(a.fwd_done + job) || !HE_OBJ_OK(a.status + 1)) return false;
     const int need = a.fwd_need[job];
     long long polls = 0;
     while (ld_acquire(a.fwd_done + job) < need) {
@@ -49,6 +50,7 @@ __device__ bool fused_wait(const FusedArgs &a, int job, int unit) {
 // the next unit index, or n_units (stop) once a unit has given up waiting;
 // called by thread 0 only, so the whole CTA takes the same decision
 __device__ __forceinline__ int fused_claim(const FusedArgs &a) {
+    if (!HE_OBJ_OK(a.status) || !HE_OBJ_OK(a.counter)) return a.n_units;
     return *(volatile int *)a.status != 0 ? a.n_units : atomicAdd(a.counter, 1);
 }
 
@@ -56,7 +58,7 @@ __device__ __forceinline__ int fused_claim(const FusedArgs &a) {
 // caller's barrier): make them visible device-wide, then count the item
 __device__ __forceinline__ void fused_count(const FusedArgs &a, int job) {
     __threadfence();
-    atomicAdd(a.fwd_done + job, 1);
+    if (HE_OBJ_OK(a.fwd_done + job)) atomicAdd(a.fwd_done + job, 1);
 }
 
 // The four unit bodies are separate (not inlined) functions, so that each is
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(Cfg<LB>::T, MINB) k_batch_fused(const __grid_c
         const int it = s_unit[iter & 1];
         if (it >= a.n_units) return;
         if (threadIdx.x == 0) s_unit[(iter + 1) & 1] = fused_claim(a);
+        if (!HE_OBJ_OK(a.units + it)) continue;  // (checks build; uniform over the CTA)
         const FusedUnit u = a.units[it];
         if (u.big) {
             if (u.mac) {
@@ -166,10 +169,17 @@ static int fused_l(const FusedArgs &a, int grid, cudaStream_t st) {
 }
 
 int fused_set_attributes(int logN_big, int minb) {
+#ifdef HE_CHECKS
+    minb = 2;
+#endif
     switch (logN_big * 2 + minb - 1) {
+#ifndef HE_CHECKS
     case 24: return fused_attr<12, 1>();
+#endif
     case 25: return fused_attr<12, 2>();
+#ifndef HE_CHECKS
     case 26: return fused_attr<13, 1>();
+#endif
     case 27: return fused_attr<13, 2>();
     }
     return HE_ERR_UNSUPPORTED_PARAMS;
@@ -178,13 +188,24 @@ int fused_set_attributes(int logN_big, int minb) {
 int launch_fused(int logN_big, int minb, const FusedArgs &a, int grid, cudaStream_t st) {
     if (a.n_units <= 0) return HE_OK;
     if (grid <= 0 || minb < 1 || minb > 2) return HE_ERR_INVALID_ARG;
+#ifdef HE_CHECKS
+    // the bounds-checked build compiles one register budget (same bits)
+    if (minb == 1) grid *= 2;
+    minb = 2;
+#endif
     switch (logN_big * 2 + minb - 1) {
+#ifndef HE_CHECKS
     case 24: return fused_l<12, 1>(a, grid, st);
+#endif
     case 25: return fused_l<12, 2>(a, grid, st);
+#ifndef HE_CHECKS
     case 26: return fused_l<13, 1>(a, grid, st);
+#endif
     case 27: return fused_l<13, 2>(a, grid, st);
     }
     return HE_ERR_UNSUPPORTED_PARAMS;
 }
 
 }  // namespace he
+
+HE_CHECKS_UNIT(fused)

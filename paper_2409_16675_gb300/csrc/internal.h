@@ -165,6 +165,19 @@ inline bool plan_pair(const he_plan *p, int mg, int g) {
 
 namespace he {
 
+// Device allocations of the library.  In the bounds-checked build (HE_CHECKS)
+// each allocation's range is registered for the kernels' address checks and
+// unregistered when freed; otherwise these are cudaMalloc / cudaFree.
+#ifdef HE_CHECKS
+cudaError_t dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+void checks_register(const void *p, size_t bytes);  // a range that is not a cudaMalloc (a __device__ array)
+#else
+inline cudaError_t dev_alloc(void **p, size_t bytes) { return cudaMalloc(p, bytes); }
+inline void dev_free(void *p) { cudaFree(p); }
+inline void checks_register(const void *, size_t) {}
+#endif
+
 // The role of the launches a call site issues (a string literal, or null);
 // the trace reports each launch as "family.role".
 extern thread_local const char *g_trace_role;

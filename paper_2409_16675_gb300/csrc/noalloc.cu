@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "checks.cuh"
 
 namespace {
 
@@ -43,7 +44,7 @@ struct NoAllocTermArgs {
 __global__ void k_noalloc_terms(const NoAllocTermArgs a) {
     const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (o > a.n_out) return;
-    a.ptr[o] = (int32_t)(o * a.per_out);
+    HE_ST(a.ptr + o, (int32_t)(o * a.per_out));
     if (o == a.n_out) return;
     const int comp = (int)(o & 1);
     long long r = o >> 1;
@@ -55,13 +56,13 @@ __global__ void k_noalloc_terms(const NoAllocTermArgs a) {
     for (int g = 0; g < a.G; g++) {
         if (a.depthwise && g != (m * a.Mn) / a.Cn) continue;
         if (a.has_x) {
-            a.ta[k] = (int32_t)((((b * a.T + t) * a.G + g) * 2 + comp) * a.L);
-            a.tb[k] = (int32_t)(((long long)m * a.G + g) * a.L);
+            HE_ST(a.ta + k, (int32_t)((((b * a.T + t) * a.G + g) * 2 + comp) * a.L));
+            HE_ST(a.tb + k, (int32_t)(((long long)m * a.G + g) * a.L));
             k++;
         }
         if (a.has_w) {
-            a.ta[k] = (int32_t)((a.nX + ((long long)m * a.G + g) * 2 + comp) * a.L);
-            a.tb[k] = (int32_t)((a.nWp + (b * a.T + t) * a.G + g) * a.L);
+            HE_ST(a.ta + k, (int32_t)((a.nX + ((long long)m * a.G + g) * 2 + comp) * a.L));
+            HE_ST(a.tb + k, (int32_t)((a.nWp + (b * a.T + t) * a.G + g) * a.L));
             k++;
         }
     }
@@ -126,6 +127,7 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
             void *a = nullptr;
             rc = cuda_check(c, cudaGetSymbolAddress(&a, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)");
             if (rc) return rc;
+            checks_register(a, kNoAllocScratchBytes);  // (bounds-checked build only)
             g_noalloc_addr[dev] = a;
         }
         base = g_noalloc_addr[dev];
@@ -187,3 +189,5 @@ extern "C" int he_cpmul_conv_noalloc(he_ctx *c, const he_plan *p, int batch, con
     mj.n_terms = (int)n_terms;
     return launch_mac_intt(c, mj, st);
 }
+
+HE_CHECKS_UNIT(noalloc)

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB) k_fwd(FwdJobs J
     const int local = (int)blockIdx.x - base;
     const int limb = local / J.n_polys;
     const int p = local - limb * J.n_polys;
+    if (!HE_OBJ_OK(mods + J.mod_base + limb)) return;  // uniform over the CTA
     const ModDev M = mods[J.mod_base + limb];
     const void *src;
     if (J.kind == SRC_RNS)
@@ -60,10 +61,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const int local = (int)blockIdx.x - JS.start[jj];
     const int limb = local / J.n_out;
     const int o = local - limb * J.n_out;
+    if (!HE_OBJ_OK(mods + J.mod_base + limb)) return;  // uniform over the CTA
     const ModDev M = mods[J.mod_base + limb];
     u64 v[Cfg<LOGN>::R];
-    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, J.ptr[o], J.ptr[o + 1], limb, M, tau,
-                                                                   v, sm);
+    mac_accumulate<LOGN, mac_group(Cfg<LOGN>::T, Cfg<LOGN>::MINB)>(J.A, J.B, J.ta, J.tb, HE_LD(J.ptr + o),
+                                                                   HE_LD(J.ptr + o + 1), limb, M, tau, v, sm);
     inv_transform<LOGN, LAZY>(v, sm, tau, M);
     // natural order: element j = k*T + tau
     const u64 q = M.q;
@@ -73,27 +75,30 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const u64 *msg = (J.msg && (o % J.msg_div) == 0) ? J.msg + (long long)(o / J.msg_div) * J.msg_stride : nullptr;
     const u64 *s2 = J.s2 ? J.s2 + (long long)limb * N : nullptr;
     u64 g = 0, gs = 0, dl = 0, dls = 0;
-    if (s2) { g = J.gmul[2 * ((long long)o * J.n_limbs + limb)]; gs = J.gmul[2 * ((long long)o * J.n_limbs + limb) + 1]; }
-    if (msg) { dl = J.E->delta_q[J.mod_base + limb]; dls = J.E->delta_qs[J.mod_base + limb]; }
-    const u64 t = msg ? J.E->t : 0;
+    if (s2) {
+        g = HE_LD(J.gmul + 2 * ((long long)o * J.n_limbs + limb));
+        gs = HE_LD(J.gmul + 2 * ((long long)o * J.n_limbs + limb) + 1);
+    }
+    if (msg) { dl = HE_LD(J.E->delta_q + J.mod_base + limb); dls = HE_LD(J.E->delta_qs + J.mod_base + limb); }
+    const u64 t = msg ? HE_LD(&J.E->t) : 0;
 #pragma unroll
     for (int k = 0; k < Cfg<LOGN>::R; k++) {
         const int x = k * T + tau;
-        const ulonglong2 zp = __ldg(M.z + x);
+        const ulonglong2 zp = HE_LDG(M.z + x);
         u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
         if (err) {
-            const int e = err[x];
+            const int e = HE_LD(err + x);
             r = e >= 0 ? addm(r, (u64)e, q) : subm(r, (u64)(-e), q);
         }
         if (J.negate) r = r ? q - r : 0;
-        if (s2) r = addm(r, red1(shoup(s2[x], g, gs, q), q), q);
+        if (s2) r = addm(r, red1(shoup(HE_LD(s2 + x), g, gs, q), q), q);
         if (msg) {
-            u64 m = msg[x];
+            u64 m = HE_LD(msg + x);
             m = m >= t ? m % t : m;
             r = addm(r, red1(shoup(m, dl, dls, q), q), q);
         }
-        if (add) r = addm(r, add[x], q);
-        out[x] = r;
+        if (add) r = addm(r, HE_LD(add + x), q);
+        HE_ST(out + x, r);
     }
 }
 
@@ -108,13 +113,13 @@ template <typename ITEM>
 __device__ __forceinline__ const ITEM *next_item(const ItemSeg *segs, int nseg, int total, int *counter,
                                                  int *s_meta) {
     if (threadIdx.x == 0) {
-        const int it = atomicAdd(counter, 1);
+        const int it = HE_OBJ_OK(counter) ? atomicAdd(counter, 1) : total;
         int sidx = 0;
         if (it < total) {
             int lo = 0, hi = nseg - 1;  // last segment whose begin <= it
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (segs[mid].begin <= it) lo = mid;
+                if (HE_LD(&segs[mid].begin) <= it) lo = mid;
                 else hi = mid - 1;
             }
             sidx = lo;
@@ -126,7 +131,7 @@ __device__ __forceinline__ const ITEM *next_item(const ItemSeg *segs, int nseg, 
     const int it = s_meta[0], sidx = s_meta[1];
     __syncthreads();
     if (it >= total) return nullptr;
-    return (const ITEM *)segs[sidx].items + (it - segs[sidx].begin);
+    return (const ITEM *)HE_LD(&segs[sidx].items) + (it - HE_LD(&segs[sidx].begin));
 }
 
 // LAZY: every item's modulus is below 2^57 (checked by the host per launch)
@@ -156,10 +161,10 @@ __device__ __forceinline__ const ITEM *item_at(const ItemSeg *segs, int nseg, in
     int lo = 0, hi = nseg - 1;  // last segment whose begin <= it
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].begin <= it) lo = mid;
+        if (HE_LD(&segs[mid].begin) <= it) lo = mid;
         else hi = mid - 1;
     }
-    return (const ITEM *)segs[lo].items + (it - segs[lo].begin);
+    return (const ITEM *)HE_LD(&segs[lo].items) + (it - HE_LD(&segs[lo].begin));
 }
 
 template <int LOGN, int MINB, bool LAZY>
@@ -201,7 +206,7 @@ static int fwd_t(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static std::atomic<unsigned long long> attr_mask{0};
     if (first_on_device(attr_mask)) {
-        cudaFuncSetAttribute(k_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if constexpr (kAllVariants) cudaFuncSetAttribute(k_fwd<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_fwd<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     FwdJobs JS;
@@ -225,8 +230,13 @@ static int fwd_t(he_ctx *c, const FwdJob *jobs, int n, cudaStream_t st) {
     if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "forward launch too large");
     const bool lazy = lazy_ok(c, jobs[0].mod_base, jobs[0].n_limbs);
     TraceScope ts(c, st, "ntt_fwd", bytes, (double)blocks * (N / 2) * LOGN);
-    if (lazy) k_fwd<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
-    else k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    if constexpr (kAllVariants) {
+        if (lazy) k_fwd<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+        else k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    } else {
+        (void)lazy;
+        k_fwd<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    }
     return cuda_check(c, cudaGetLastError(), "k_fwd");
 }
 
@@ -235,7 +245,8 @@ static int mac_t(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
     const int smem = Cfg<LOGN>::SMEM;
     static std::atomic<unsigned long long> attr_mask{0};
     if (first_on_device(attr_mask)) {
-        cudaFuncSetAttribute(k_mac_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if constexpr (kAllVariants)
+            cudaFuncSetAttribute(k_mac_intt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(k_mac_intt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     MacJobs JS;
@@ -260,8 +271,13 @@ static int mac_t(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
     if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "multiply-accumulate launch too large");
     const bool lazy = lazy_ok(c, jobs[0].mod_base, jobs[0].n_limbs);
     TraceScope ts(c, st, "mac_intt", bytes, mm);
-    if (lazy) k_mac_intt<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
-    else k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    if constexpr (kAllVariants) {
+        if (lazy) k_mac_intt<LOGN, true><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+        else k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    } else {
+        (void)lazy;
+        k_mac_intt<LOGN, false><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(JS, c->d_mods);
+    }
     return cuda_check(c, cudaGetLastError(), "k_mac_intt");
 }
 
@@ -302,21 +318,25 @@ static int queue_l(bool fwd, const ItemSeg *segs, int nseg, int total, int *coun
 template <int LOGN, int MINB>
 static int queue_t(bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter, int grid,
                    cudaStream_t st) {
-    return lazy ? queue_l<LOGN, MINB, true>(fwd, segs, nseg, total, counter, grid, st)
-                : queue_l<LOGN, MINB, false>(fwd, segs, nseg, total, counter, grid, st);
+    if constexpr (kAllVariants)
+        return lazy ? queue_l<LOGN, MINB, true>(fwd, segs, nseg, total, counter, grid, st)
+                    : queue_l<LOGN, MINB, false>(fwd, segs, nseg, total, counter, grid, st);
+    (void)lazy;
+    return queue_l<LOGN, MINB, false>(fwd, segs, nseg, total, counter, grid, st);
 }
 
 int launch_queue(int logN, int minb, bool fwd, bool lazy, const ItemSeg *segs, int nseg, int total, int *counter,
                  int grid, cudaStream_t st) {
     if (total <= 0 || nseg <= 0) return HE_OK;
+    if (!kAllVariants) minb = logN >= 14 ? 1 : 2;
     switch (logN * 2 + (minb >= 2 ? 1 : 0)) {
-    case 20: return queue_t<10, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 20: if constexpr (kAllVariants) return queue_t<10, 1>(fwd, lazy, segs, nseg, total, counter, grid, st); break;
     case 21: return queue_t<10, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
-    case 22: return queue_t<11, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 22: if constexpr (kAllVariants) return queue_t<11, 1>(fwd, lazy, segs, nseg, total, counter, grid, st); break;
     case 23: return queue_t<11, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
-    case 24: return queue_t<12, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 24: if constexpr (kAllVariants) return queue_t<12, 1>(fwd, lazy, segs, nseg, total, counter, grid, st); break;
     case 25: return queue_t<12, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
-    case 26: return queue_t<13, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
+    case 26: if constexpr (kAllVariants) return queue_t<13, 1>(fwd, lazy, segs, nseg, total, counter, grid, st); break;
     case 27: return queue_t<13, 2>(fwd, lazy, segs, nseg, total, counter, grid, st);
     case 28: return queue_t<14, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
     case 29: return queue_t<14, 1>(fwd, lazy, segs, nseg, total, counter, grid, st);
@@ -339,3 +359,5 @@ int launch_mac_multi(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
 int launch_mac_intt(he_ctx *c, const MacJob &j, cudaStream_t st) { return launch_mac_multi(c, &j, 1, st); }
 
 }  // namespace he
+
+HE_CHECKS_UNIT(ntt)

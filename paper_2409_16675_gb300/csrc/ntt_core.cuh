@@ -94,7 +94,7 @@ __device__ __forceinline__ void fwd_pass(u64 (&v)[1 << RB], int tau, int lo, int
         for (int k = 0; k < R; k++) {
             if (k & (1 << kb)) continue;
             const int widx = base + ((k >> (kb + 1)) << (s - gb));
-            const ulonglong2 Wp = __ldg(M.fw + widx);
+            const ulonglong2 Wp = HE_LDG(M.fw + widx);
             u64 X = v[k];
             const u64 Y = v[k | (1 << kb)];
             if (!LAZY) X = X >= q4 ? X - q4 : X;
@@ -121,7 +121,7 @@ __device__ __forceinline__ void inv_pass(u64 (&v)[1 << RB], int tau, int lo, int
         for (int k = 0; k < R; k++) {
             if (k & (1 << kb)) continue;
             const int widx = base + ((k & ((1 << kb) - 1)) << lo);
-            const ulonglong2 Wp = __ldg(M.iw + widx);
+            const ulonglong2 Wp = HE_LDG(M.iw + widx);
             u64 X = v[k];
             if (!LAZY) X = X >= q4 ? X - q4 : X;
             const u64 Tt = shoup4(v[k | (1 << kb)], Wp.x, Wp.y, nq);
@@ -175,7 +175,16 @@ __device__ __forceinline__ void exchange(u64 *sm, u64 (&v)[1 << RB], int tau, in
 // block).  Measured on 256 uneven jobs with 36-60-bit limbs: 24.18 -> 23.51 ms.
 // The one-call grid kernels keep the launch-wide choice: there the second
 // inlined transform raised the spills and the plain per-job launches lost 1%.
-__device__ __forceinline__ bool lazy_mod(const ModDev &M) { return M.q < (1ull << 57); }
+// The bounds-checked build compiles one variant of each kernel (the
+// non-lazy transform, valid for every modulus below 2^61, and one register
+// budget per ring degree); the variants give the same bits, so only speed
+// differs, and its compile time stays a few minutes.
+#ifdef HE_CHECKS
+constexpr bool kAllVariants = false;
+#else
+constexpr bool kAllVariants = true;
+#endif
+__device__ __forceinline__ bool lazy_mod(const ModDev &M) { return kAllVariants && M.q < (1ull << 57); }
 
 // ---------------------------------------------------------------- per-polynomial building blocks
 // Load one limb polynomial into the first register window (bits [LOGN-4,
@@ -187,7 +196,7 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
     case SRC_RNS: {
         const u64 *s = (const u64 *)src;
 #pragma unroll
-        for (int k = 0; k < R; k++) v[k] = s[k * T + tau];
+        for (int k = 0; k < R; k++) v[k] = HE_LD(s + k * T + tau);
         break;
     }
     case SRC_T_LIFT: {
@@ -195,7 +204,7 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
         const u64 half = (t - 1) / 2;
 #pragma unroll
         for (int k = 0; k < R; k++) {
-            u64 x = s[k * T + tau];
+            u64 x = HE_LD(s + k * T + tau);
             x = x >= t ? x % t : x;
             v[k] = x <= half ? x : M.q - (t - x);
         }
@@ -205,7 +214,7 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
         const int8_t *s = (const int8_t *)src;
 #pragma unroll
         for (int k = 0; k < R; k++) {
-            const int x = s[k * T + tau];
+            const int x = HE_LD(s + k * T + tau);
             v[k] = x >= 0 ? (u64)x : M.q - (u64)(-x);
         }
         break;
@@ -213,13 +222,13 @@ __device__ __forceinline__ void fwd_load(int kind, const void *src, u64 t, const
     case SRC_U32: {
         const uint32_t *s = (const uint32_t *)src;
 #pragma unroll
-        for (int k = 0; k < R; k++) v[k] = s[k * T + tau];
+        for (int k = 0; k < R; k++) v[k] = HE_LD(s + k * T + tau);
         break;
     }
     default: {  // SRC_T_RAW
         const u64 *s = (const u64 *)src;
 #pragma unroll
-        for (int k = 0; k < R; k++) v[k] = reduce64(s[k * T + tau], M.q, M.one_s);
+        for (int k = 0; k < R; k++) v[k] = reduce64(HE_LD(s + k * T + tau), M.q, M.one_s);
         break;
     }
     }
@@ -243,7 +252,7 @@ __device__ __forceinline__ void fwd_transform_store(u64 (&v)[Cfg<LOGN>::R], u64 
     }
     fwd_pass<RB, RL, LAZY, COARSE>(v, tau, 0, RB * (NP - 1), M);
 #pragma unroll
-    for (int k = 0; k < R; k++) d[k * T + tau] = reduce_small(v[k], M);  // from [0, 57q) or [0, 8q)
+    for (int k = 0; k < R; k++) HE_ST(d + k * T + tau, reduce_small(v[k], M));  // from [0, 57q) or [0, 8q)
 }
 
 // sum over terms [t0, t1) of A[ta + limb] * B[tb + limb] in the NTT domain,
@@ -275,13 +284,13 @@ __device__ __forceinline__ void mac_accumulate(const u64 *__restrict__ A, const 
         int cnt = 0;
 #pragma unroll 2
         for (int tk = t0; tk < t1; tk++) {
-            const u64 *a = A + ((long long)ta[tk] + limb) * N + part * CH * T + tau;
-            const u64 *b = B + ((long long)tb[tk] + limb) * N + part * CH * T + tau;
+            const u64 *a = A + ((long long)HE_LD(ta + tk) + limb) * N + part * CH * T + tau;
+            const u64 *b = B + ((long long)HE_LD(tb + tk) + limb) * N + part * CH * T + tau;
 #pragma unroll
             for (int kk = 0; kk < CH; kk++) {
                 u64 pl, ph;
-                if (CG) mul128(__ldca(a + kk * T), __ldca(b + kk * T), pl, ph);
-                else mul128(a[kk * T], b[kk * T], pl, ph);
+                if (CG) mul128(HE_LDCA(a + kk * T), HE_LDCA(b + kk * T), pl, ph);
+                else mul128(HE_LD(a + kk * T), HE_LD(b + kk * T), pl, ph);
                 lo[kk] += pl;
                 hi[kk] += ph + (lo[kk] < pl);
             }
@@ -343,7 +352,9 @@ template <int LOGN, int MINB, bool LAZY, class SYNC = CtaSync, bool CG = false,
           int CH = mac_group(Cfg<LOGN>::T, MINB)>
 __device__ __forceinline__ void mac_item(const MacItem *__restrict__ ip, u64 *sm, int tau, const SYNC &sy = SYNC()) {
     constexpr int T = Cfg<LOGN>::T;
+    if (!HE_OBJ_OK(ip)) return;               // (checks build: the item lies in a registered allocation)
     const ModDev *__restrict__ mp = ip->mod;  // read-only: fields may be re-read rather than kept live
+    if (!HE_OBJ_OK(mp)) return;
     const ModDev M = *mp;
     u64 v[Cfg<LOGN>::R];
     mac_accumulate<LOGN, CH, CG>(ip->A, ip->B, ip->ta, ip->tb, ip->t0, ip->t1, ip->limb, M, tau, v, sm);
@@ -355,16 +366,18 @@ __device__ __forceinline__ void mac_item(const MacItem *__restrict__ ip, u64 *sm
 #pragma unroll
     for (int k = 0; k < Cfg<LOGN>::R; k++) {
         const int x = k * T + tau;
-        const ulonglong2 zp = __ldg(M.z + x);
+        const ulonglong2 zp = HE_LDG(M.z + x);
         u64 r = red1(shoup(v[k], zp.x, zp.y, q), q);
-        if (add) r = addm(r, add[x], q);
-        out[x] = r;
+        if (add) r = addm(r, HE_LD(add + x), q);
+        HE_ST(out + x, r);
     }
 }
 
 template <int LOGN, bool LAZY, class SYNC = CtaSync, bool COARSE = Cfg<LOGN>::COARSE_FWD>
 __device__ __forceinline__ void fwd_item(const FwdItem *__restrict__ ip, u64 *sm, int tau, const SYNC &sy = SYNC()) {
+    if (!HE_OBJ_OK(ip)) return;
     const ModDev *__restrict__ mp = ip->mod;
+    if (!HE_OBJ_OK(mp)) return;
     const ModDev M = *mp;
     u64 v[Cfg<LOGN>::R];
     fwd_load<LOGN>(ip->kind, ip->src, ip->t, M, tau, v);

@@ -204,7 +204,7 @@ static bool add_modulus(he_ctx *c, u64 q, std::string &err) {
             iw[2 * i + 1] = shoup_c(iw[2 * i], q);
         }
     void *d = nullptr;
-    if (cudaMalloc(&d, tab.size() * 8) != cudaSuccess) { err = "cudaMalloc twiddles"; return false; }
+    if (he::dev_alloc((void **)&d, tab.size() * 8) != cudaSuccess) { err = "cudaMalloc twiddles"; return false; }
     c->allocs.push_back(d);
     if (cudaMemcpy(d, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) { err = "upload twiddles"; return false; }
     ModDev M;
@@ -417,8 +417,8 @@ int build_tables(he_ctx *c, std::string &err) {
     E.r64_ts = shoup_c(E.r64_t, t);
     E.one_ts = (u64)(((u128)1 << 64) / t);
     // upload
-    if (cudaMalloc((void **)&c->d_mods, sizeof(ModDev) * c->n_mods) != cudaSuccess ||
-        cudaMalloc((void **)&c->d_exact, sizeof(ExactDev)) != cudaSuccess) {
+    if (he::dev_alloc((void **)&c->d_mods, sizeof(ModDev) * c->n_mods) != cudaSuccess ||
+        he::dev_alloc((void **)&c->d_exact, sizeof(ExactDev)) != cudaSuccess) {
         err = "cudaMalloc tables";
         return HE_ERR_OOM;
     }

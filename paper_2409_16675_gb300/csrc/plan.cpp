@@ -291,7 +291,7 @@ int build_plan(he_ctx *c, const he_conv_shape &s, int encoding, he_plan *p, std:
         }
     // upload
     auto up = [&](const std::vector<int32_t> &h, int32_t **d) -> bool {
-        if (cudaMalloc((void **)d, h.size() * 4) != cudaSuccess) return false;
+        if (he::dev_alloc((void **)d, h.size() * 4) != cudaSuccess) return false;
         return cudaMemcpy(*d, h.data(), h.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
     };
     if (!up(p->h_in_map, &p->in_map) || !up(p->h_ker_map, &p->ker_map) || !up(p->h_out_map, &p->out_map)) {

@@ -324,14 +324,14 @@ int he_server_create(const he_server_config *cfg, he_server **out) {
         return HE_ERR_CUDA;
     }
     s->arena_size = al((size_t)cfg->hbm_budget_bytes);
-    if (cudaMalloc((void **)&s->arena_base, s->arena_size) != cudaSuccess) {
+    if (he::dev_alloc((void **)&s->arena_base, s->arena_size) != cudaSuccess) {
         delete s;
         return HE_ERR_OOM;
     }
     s->arena.init(s->arena_size);
     s->slot_bytes = slot_bytes(cfg->max_group);
     if (!s->arena.alloc(s->slot_bytes * cfg->max_inflight, s->slots_off)) {
-        cudaFree(s->arena_base);
+        he::dev_free(s->arena_base);
         delete s;
         return HE_ERR_BUDGET_EXCEEDED;
     }
@@ -468,7 +468,7 @@ int he_server_destroy(he_server *s) {
     cudaSetDevice(s->cfg.device);
     for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
     for (auto &p : s->pinned_free) cudaFreeHost(p.first);
-    if (s->arena_base) cudaFree(s->arena_base);
+    if (s->arena_base) he::dev_free(s->arena_base);
     delete s;
     return HE_OK;
 }

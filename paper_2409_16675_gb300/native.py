@@ -14,7 +14,10 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcryptotrain.so")
+# CRYPTOTRAIN_LIB=checks selects the bounds-checked debug build of the same
+# library (libcryptotrain_checks.so, built by build.build_checks()).
+LIB_NAME = "libcryptotrain_checks.so" if os.environ.get("CRYPTOTRAIN_LIB") == "checks" else "libcryptotrain.so"
+LIB_PATH = os.path.join(_HERE, LIB_NAME)
 
 HE_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_PARAMS", -3: "PLAN_DOES_NOT_FIT", -4: "OOM",
@@ -86,8 +89,8 @@ class he_plan_info(ctypes.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libcryptotrain.so is not built (run __graft_entry__.build()); "
-                          "there is no fallback implementation")
+        raise ImportError("%s is not built (run __graft_entry__.build()); "
+                          "there is no fallback implementation" % LIB_NAME)
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
     pp = ctypes.POINTER(ctypes.c_void_p)
@@ -137,6 +140,9 @@ def _load():
         "he_batch_status": [vp, vp],
         "he_batch_set_wait_limit": [vp, ctypes.c_int64],
         "he_batch_test_hold_job": [vp, i32, i32],
+        "he_checks_enabled": [],
+        "he_checks_last_error": [ctypes.c_char_p, i32],
+        "he_checks_test_exclude": [vp, ctypes.c_int64],
         "he_server_create": [ctypes.POINTER(he_server_config), pp],
         "he_server_submit": [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(i64)],
         "he_server_poll": [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
@@ -183,7 +189,10 @@ def last_error(ctx=None) -> str:
 
 def _check(rc, ctx=None):
     if rc != HE_OK:
-        raise HEError(rc, last_error(ctx))
+        msg = last_error(ctx)
+        if not msg and LIB_NAME == "libcryptotrain_checks.so":
+            msg = he_checks_last_error()
+        raise HEError(rc, msg)
 
 
 def make_params(N, L=None, prime_bits=None, q=None, t=65537, base_log2=16, eta=21, max_ccmul_group=64, device=0,
@@ -442,6 +451,21 @@ def he_batch_set_wait_limit(b, polls):
 
 def he_batch_test_hold_job(b, job, hold):
     _bcheck(lib.he_batch_test_hold_job(b, job, int(hold)), b)
+
+
+def he_checks_enabled() -> bool:
+    return lib.he_checks_enabled() == 1
+
+
+def he_checks_last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib.he_checks_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def he_checks_test_exclude(t, nbytes):
+    """Leave [t.data_ptr(), + nbytes) out of the checked ranges (None: clear)."""
+    _check(lib.he_checks_test_exclude(_ptr(t) if t is not None else None, int(nbytes)))
 
 
 def he_batch_last_error(b) -> str:
