@@ -773,8 +773,14 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
             }
         MacJob mt = mac_job();
         TRY(upload_terms(c, Tt, mt));
-        mt.A = An; mt.B = Bn; mt.out = d; mt.out_stride = LKN; mt.n_out = nc * 3; mt.n_limbs = LK;
+        mt.A = An; mt.B = Bn; mt.out = d; mt.out_stride = LKN; mt.n_out = nc * 3; mt.n_limbs = L;
+        // two launches with the same term table: the limbs of Q, whose moduli
+        // may allow the lazy transform, and the auxiliary limbs of B (61-bit,
+        // never lazy), whose operand and output bases start L limbs on
         TRY(launch_mac_intt(c, mt, st));
+        MacJob mb = mt;
+        mb.A = An + LN; mb.B = Bn + LN; mb.out = d + LN; mb.n_limbs = K; mb.mod_base = L;
+        TRY(launch_mac_intt(c, mb, st));
         g_trace_role = "rescale";
         // 4. exact rescaling by t/q and digits of d2
         TRY(launch_scale_round(c, d, nc, dq, dig, st));
