@@ -20,8 +20,9 @@ Readings where the paper is silent or garbled:
       H_n W_n, kernel offset O = (C_n-1) H_n W_n + (h-1) W_n + h - 1.
   R3  correlated channel blocks: channel c at offset c S, kernel channel c at
       (C_n-1-c) S, S the smallest stride that keeps the cross-channel terms
-      off the requested outputs; C_n is the largest count for which the
-      requested outputs stay below N and no wrapped term reaches them.
+      off the requested outputs; C_n ranges over every count up to the
+      largest for which the requested outputs stay below N and no wrapped
+      term reaches them (fewer channels can leave room for output packing).
   R4  correlated windows are chosen over output tiles th x tw; a tile covering
       output rows [a0, a1) encodes input rows [a0-p, a1-p+h-1) clipped to the
       image; O uses the largest tile extent.
@@ -233,15 +234,22 @@ def plan_correlated(N, C, H, W, M, h, pad, depthwise=False) -> Plan:
             cmax = 1
             while cmax < C and _corr_fits(cmax + 1, S, geo, N):
                 cmax += 1
-            G = -(-C // cmax)
-            Cn = -(-C // G)
             T = len(tiles)
-            ranges = [((Cn - 1) * S + rlo, (Cn - 1) * S + rhi, 2 * (Cn - 1) * S + D1) for (rlo, rhi, D1) in geo]
-            Mn, Sout = _out_packing(M, N, ranges, Cn if depthwise and G > 1 else 0)
-            MG = -(-M // Mn)
-            key = (MG * (1 if depthwise else G) * T, G * T, G, -th, -tw)
-            if best is None or key < best[0]:
-                best = (key, (Cn, G, th, tw, O, S, tiles, Mn, Sout))
+            # every channel count up to the largest that fits (R3): fewer
+            # channels per polynomial can leave room for more kernels (R6)
+            seen = set()
+            for ct in range(cmax, 0, -1):
+                G = -(-C // ct)
+                if G in seen:
+                    continue
+                seen.add(G)
+                Cn = -(-C // G)
+                ranges = [((Cn - 1) * S + rlo, (Cn - 1) * S + rhi, 2 * (Cn - 1) * S + D1) for (rlo, rhi, D1) in geo]
+                Mn, Sout = _out_packing(M, N, ranges, Cn if depthwise and G > 1 else 0)
+                MG = -(-M // Mn)
+                key = (MG * (1 if depthwise else G) * T, G * T, G, -th, -tw)
+                if best is None or key < best[0]:
+                    best = (key, (Cn, G, th, tw, O, S, tiles, Mn, Sout))
     if best is None:
         raise ValueError("plan does not fit")
     Cn, G, th, tw, O, S, tiles, Mn, Sout = best[1]

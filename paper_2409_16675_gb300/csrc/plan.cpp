@@ -168,24 +168,31 @@ static bool corr_search(int N, const he_conv_shape &s, bool dw, he_plan_info &I,
             if (!corr_fits(1, S, g, N)) continue;
             int cmax = 1;
             while (cmax < s.C && corr_fits(cmax + 1, S, g, N)) cmax++;
-            const int G = (s.C + cmax - 1) / cmax;
-            const int Cn = (s.C + G - 1) / G;
-            std::vector<Span> sp;
-            for (const Geo &e : g)
-                sp.push_back({(Cn - 1) * S + e.rlo, (Cn - 1) * S + e.rhi, 2 * (long long)(Cn - 1) * S + e.D1});
-            int Mn;
-            long long Sout;
-            out_packing(s.M, N, sp, Mn, Sout, dw && G > 1 ? Cn : 0);
-            const long long MG = (s.M + Mn - 1) / Mn;
-            long long key[5] = {plan_products(dw, MG, G, (long long)tl.size()), (long long)G * (long long)tl.size(), G,
-                                -th, -tw};
-            if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
-                std::copy(key, key + 5, best);
-                found = true;
-                I.Cn = Cn; I.G = G; I.th = th; I.tw = tw; I.O = (int)O; I.S = (int)S;
-                I.Th = (Ho + th - 1) / th; I.Tw = (Wo + tw - 1) / tw;
-                I.Mn = Mn; I.Sout = (int)Sout;
-                tiles = tl;
+            // every channel count up to the largest that fits: fewer channels
+            // per polynomial can leave room for more kernels per polynomial
+            int last_G = -1;
+            for (int ct = cmax; ct >= 1; ct--) {
+                const int G = (s.C + ct - 1) / ct;
+                if (G == last_G) continue;
+                last_G = G;
+                const int Cn = (s.C + G - 1) / G;
+                std::vector<Span> sp;
+                for (const Geo &e : g)
+                    sp.push_back({(Cn - 1) * S + e.rlo, (Cn - 1) * S + e.rhi, 2 * (long long)(Cn - 1) * S + e.D1});
+                int Mn;
+                long long Sout;
+                out_packing(s.M, N, sp, Mn, Sout, dw && G > 1 ? Cn : 0);
+                const long long MG = (s.M + Mn - 1) / Mn;
+                long long key[5] = {plan_products(dw, MG, G, (long long)tl.size()), (long long)G * (long long)tl.size(),
+                                    G, -th, -tw};
+                if (!found || std::lexicographical_compare(key, key + 5, best, best + 5)) {
+                    std::copy(key, key + 5, best);
+                    found = true;
+                    I.Cn = Cn; I.G = G; I.th = th; I.tw = tw; I.O = (int)O; I.S = (int)S;
+                    I.Th = (Ho + th - 1) / th; I.Tw = (Wo + tw - 1) / tw;
+                    I.Mn = Mn; I.Sout = (int)Sout;
+                    tiles = tl;
+                }
             }
         }
     if (!found) return false;

@@ -179,3 +179,80 @@ def test_conventional_plan_is_the_bruteforce_minimum(N, C, H, W, h, pad):
     want = conv_bruteforce(N, C, H, W, h, pad, rng)
     p = packing.make_plan("conv", N, C, H, W, 1, h, pad)
     assert want is not None and p.G * p.T == want, (p.G, p.T, want)
+
+
+# ---------------------------------------------------------------- output packing (R14)
+def corr_outpack_feasible(N, C, H, W, h, pad, th, tw, Cn, S, Mn, Sout, x, ws):
+    """Mn kernels share one polynomial, kernel m at offset m*Sout: every
+    kernel's outputs decode correctly for every tile and channel group."""
+    Ho, Wo = H + 2 * pad - h + 1, W + 2 * pad - h + 1
+    tl = tiles_of(Ho, Wo, th, tw)
+    wins = [(max(0, a0 - pad), min(H, a1 - pad + h - 1), max(0, b0 - pad), min(W, b1 - pad + h - 1))
+            for (a0, a1, b0, b1) in tl]
+    O = max(max(r1 - r0, s1 - s0) for (r0, r1, s0, s1) in wins) + h - 1
+    for g0 in range(0, C, Cn):
+        chans = list(range(g0, min(C, g0 + Cn)))
+        kp = np.zeros(N, dtype=np.int64)
+        for m in range(Mn):
+            for ci, c in enumerate(chans):
+                for k in range(h):
+                    for l in range(h):
+                        pos = m * Sout + (Cn - 1 - ci) * S + (h - 1 - k) * O + (h - 1 - l)
+                        if pos >= N:
+                            return False
+                        kp[pos] = (kp[pos] + ws[m][c, k, l]) % P
+        parts = [conv_direct(x[chans], ws[m][chans], pad) for m in range(Mn)]
+        for (a0, a1, b0, b1), (r0, r1, s0, s1) in zip(tl, wins):
+            xp = np.zeros(N, dtype=np.int64)
+            for ci, c in enumerate(chans):
+                for i in range(r0, r1):
+                    for j in range(s0, s1):
+                        pos = ci * S + (i - r0) * O + (j - s0)
+                        if pos >= N:
+                            return False
+                        xp[pos] = (xp[pos] + x[c, i, j]) % P
+            prod = negacyclic(xp, kp, N)
+            for m in range(Mn):
+                for a in range(a0, a1):
+                    for b in range(b0, b1):
+                        pos = m * Sout + (Cn - 1) * S + (a - pad - r0 + h - 1) * O + (b - pad - s0 + h - 1)
+                        if pos >= N or (prod[pos] - parts[m][a, b]) % P:
+                            return False
+    return True
+
+
+def corr_outpack_bruteforce(N, C, H, W, M, h, pad, rng):
+    x = rng.integers(0, P, (C, H, W))
+    ws = [rng.integers(0, P, (C, h, h)) for _ in range(M)]
+    Ho, Wo = H + 2 * pad - h + 1, W + 2 * pad - h + 1
+    best = None
+    for th, tw in itertools.product(range(1, Ho + 1), range(1, Wo + 1)):
+        T = len(tiles_of(Ho, Wo, th, tw))
+        for Cn in range(1, C + 1):
+            G = -(-C // Cn)
+            if best is not None and G * T >= best:
+                continue
+            for S in range(1, N + 1):
+                if not corr_feasible(N, C, H, W, h, pad, th, tw, Cn, S, x, ws[0], None):
+                    continue
+                for Mn in range(M, 0, -1):
+                    cnt = -(-M // Mn) * G * T
+                    if best is not None and cnt >= best:
+                        continue
+                    if any(corr_outpack_feasible(N, C, H, W, h, pad, th, tw, Cn, S, Mn, So, x, ws)
+                           for So in range(1, N)):
+                        best = cnt
+    return best
+
+
+@pytest.mark.parametrize("N,C,H,W,h,pad", [(32, 1, 3, 3, 2, 1), (64, 2, 3, 4, 3, 1), (64, 1, 4, 4, 3, 0),
+                                            (128, 2, 4, 4, 3, 2)])
+def test_correlated_output_packing_is_the_bruteforce_minimum(N, C, H, W, h, pad):
+    """With M = 3 output channels: the oracle plan's M_G G T equals the
+    minimum over every correctly decoding layout with M_n kernels per
+    polynomial at any stride S_out (and any tile size, C_n and S)."""
+    M = 3
+    rng = np.random.default_rng(N * 41 + C * 13 + H + 100 * h + pad)
+    want = corr_outpack_bruteforce(N, C, H, W, M, h, pad, rng)
+    p = packing.make_plan("corr", N, C, H, W, M, h, pad)
+    assert want is not None and p.MG * p.G * p.T == want, (p.MG, p.G, p.T, want)
