@@ -125,6 +125,8 @@ typedef struct he_ctx_info {
     int32_t n_aux;       /* auxiliary primes of the CCMul basis */
     uint64_t aux[24];
     int32_t ppmul_ok;    /* 1 if t supports he_ppmul_* */
+    int32_t ks_primes;   /* small primes (< 2^30) of the relinearisation key switch, 0 when it
+                            runs over the limbs of q instead (see he_ccmul_precompute) */
 } he_ctx_info;
 
 /* Convolution shape (stride 1, square kernel, zero padding pad <= h-1). */
@@ -297,7 +299,11 @@ int he_cpmul_conv_noalloc(he_ctx *ctx, const he_plan *plan, int batch, const uin
  * base-2^base_log2 digits of d2.  ct_a [n_a][2][L][N], ct_b [n_b][2][L][N];
  * pair_a, pair_b: HOST int32 [n_pairs] indices; out [n_pairs/group][2][L][N].
  * Needs keys made with_relin.  group <= max_ccmul_group.  Outputs run in
- * chunks whose device scratch fits max_ccmul_scratch_bytes (he_params). */
+ * chunks whose device scratch fits max_ccmul_scratch_bytes (he_params).
+ * The sums sum_j D_j rlk_j are exact: where he_ctx_info.ks_primes > 0 they
+ * are taken modulo that many primes below 2^30 whose product exceeds four
+ * times their largest magnitude and brought to each limb by a CRT, otherwise
+ * modulo the limbs themselves; the output bits are the same either way. */
 int he_ccmul_precompute(he_ctx *ctx, const he_keys *keys, const uint64_t *ct_a, int n_a, const uint64_t *ct_b,
                         int n_b, const int32_t *pair_a, const int32_t *pair_b, int n_pairs, int group,
                         uint64_t *ct_out, cudaStream_t stream);

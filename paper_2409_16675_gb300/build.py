@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcryptotrain.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["params.cpp", "plan.cpp", "ntt.cu", "fused.cu", "exact.cu", "capi.cu", "batch.cu", "server.cu", "noalloc.cu"]
+SOURCES = ["params.cpp", "plan.cpp", "ntt.cu", "fused.cu", "exact.cu", "keyswitch.cu", "capi.cu", "batch.cu", "server.cu",
+           "noalloc.cu"]
 
 
 def nvcc() -> str:

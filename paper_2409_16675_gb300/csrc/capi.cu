@@ -240,6 +240,7 @@ int he_ctx_query(const he_ctx *c, he_ctx_info *info) {
     info->n_aux = c->K;
     for (int j = 0; j < c->K && j < 24; j++) info->aux[j] = c->aux[j];
     info->ppmul_ok = c->t_mod >= 0;
+    info->ks_primes = c->h_ks.np;
     return HE_OK;
 }
 
@@ -256,6 +257,16 @@ int he_last_error(const he_ctx *c, char *buf, int len) {
 }
 
 // ------------------------------------------------------------------ keys
+// The relinearisation key in NTT form modulo the context's small primes (for
+// the key switch over them), from its coefficient form.
+static int ks_key(he_ctx *c, he_keys *k, cudaStream_t st) {
+    const int np = c->h_ks.np;
+    if (!k->ell || np < 2) return HE_OK;
+    const size_t n = (size_t)k->ell * 2 * c->L * np * c->N;
+    if (he::dev_alloc((void **)&k->rlk32, n * 4) != cudaSuccess) return fail(c, HE_ERR_OOM, "key allocation");
+    return launch_ks_fwd(c, k->rlk, true, k->ell * 2 * c->L, k->rlk32, st);
+}
+
 int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStream_t st) {
     if (!c || !out) return HE_ERR_INVALID_ARG;
     *out = nullptr;
@@ -332,7 +343,7 @@ int he_keygen(he_ctx *c, uint64_t seed, int with_relin, he_keys **out, cudaStrea
         f.src = k->rlk; f.kind = SRC_RNS; f.src_stride = 2 * LN; f.dst = k->rlk_ntt; f.dst_stride = 2 * LN;
         f.n_polys = ell; f.n_limbs = L;
         TRY(launch_fwd(c, f, st));
-        return HE_OK;
+        return ks_key(c, k, st);
     };
     rc = run();
     if (rc) { he_keys_destroy(k); return rc; }
@@ -390,7 +401,8 @@ int he_keys_import(he_ctx *c, const int64_t *sk, const uint64_t *pk, const uint6
             f.src = k->rlk; f.dst = k->rlk_ntt; f.n_polys = 2 * ell;
             fj[nf++] = f;
         }
-        return launch_fwd_multi(c, fj, nf, st);
+        TRY(launch_fwd_multi(c, fj, nf, st));
+        return ks_key(c, k, st);
     };
     rc = run();
     if (rc) { he_keys_destroy(k); return rc; }
@@ -411,6 +423,7 @@ int he_keys_destroy(he_keys *k) {
     u64 *ps[] = {k->sk, k->s_ntt, k->pk, k->pk_ntt, k->rlk, k->rlk_ntt};
     for (u64 *p : ps)
         if (p) he::dev_free(p);
+    if (k->rlk32) he::dev_free(k->rlk32);
     delete k;
     return HE_OK;
 }
@@ -724,15 +737,20 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     const int N = c->N, L = c->L, K = c->K, LK = L + K, ell = c->ell;
     const size_t LN = (size_t)L * N, KN = (size_t)K * N, LKN = (size_t)LK * N;
     const int n_out = n_pairs / group;
+    // the key switch over the small primes when the context has them (and the
+    // keys their form of the relinearisation key), else over the limbs
+    const int np = c->h_ks.np;
+    const bool ks32 = np >= 2 && k->rlk32;
     // per-output scratch: tensor d (3 polys over Q u B), rescaled d0, d1, digits, digit NTTs
-    const size_t per_out = 3 * LKN * 8 + 2 * LN * 8 + (size_t)ell * N * 4 + (size_t)ell * LN * 8;
+    const size_t dign_words = ks32 ? ((size_t)ell * np * N + 1) / 2 : (size_t)ell * LN;
+    const size_t per_out = 3 * LKN * 8 + 2 * LN * 8 + (size_t)ell * N * 4 + dign_words * 8;
     // outputs are processed in chunks whose scratch fits the context's budget (default 4 GiB)
     const size_t chunk_budget =
         c->P.max_ccmul_scratch_bytes > 0 ? (size_t)c->P.max_ccmul_scratch_bytes : (size_t)4 << 30;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_out, chunk_budget / per_out));
     size_t need = Carver::round((size_t)(n_a + n_b) * 2 * KN * 8) + Carver::round((size_t)(n_a + n_b) * 2 * LKN * 8) +
                   Carver::round((size_t)chunk * 3 * LKN * 8) + Carver::round((size_t)chunk * 2 * LN * 8) +
-                  Carver::round((size_t)chunk * ell * N * 4) + Carver::round((size_t)chunk * ell * LN * 8) + 8192;
+                  Carver::round((size_t)chunk * ell * N * 4) + Carver::round((size_t)chunk * dign_words * 8) + 8192;
     TRY(ws_reserve(c, need));
     Carver cv(c->ws);
     u64 *aux_a = cv.take<u64>((size_t)n_a * 2 * KN);
@@ -742,7 +760,7 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     u64 *d = cv.take<u64>((size_t)chunk * 3 * LKN);
     u64 *dq = cv.take<u64>((size_t)chunk * 2 * LN);
     uint32_t *dig = cv.take<uint32_t>((size_t)chunk * ell * N);
-    u64 *dign = cv.take<u64>((size_t)chunk * ell * LN);
+    u64 *dign = cv.take<u64>((size_t)chunk * dign_words);
     TraceRole tr_("ccmul_in");
     // 1. exact base extension Q -> B of both operands
     TRY(launch_base_extend(c, ct_a, (long long)n_a * 2, aux_a, st));
@@ -784,6 +802,16 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
         g_trace_role = "rescale";
         // 4. exact rescaling by t/q and digits of d2
         TRY(launch_scale_round(c, d, nc, dq, dig, st));
+        if (ks32) {
+            // 5-6. key switch over the small primes: digits to the NTT domain
+            // mod each p_k, then per (output, limb, component) the sums, the
+            // inverse transforms and the CRT to q_i, added to (d0, d1)
+            g_trace_role = "relin_digits";
+            TRY(launch_ks_fwd(c, dig, false, nc * ell, (uint32_t *)dign, st));
+            g_trace_role = "relin";
+            TRY(launch_ks_mac(c, (const uint32_t *)dign, k->rlk32, dq, nc, ct_out + (size_t)o0 * 2 * LN, st));
+            continue;
+        }
         g_trace_role = "relin_digits";
         // 5. digits to the NTT domain over Q
         f = fwd_job();

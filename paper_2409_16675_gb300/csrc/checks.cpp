@@ -22,7 +22,7 @@
 #include "internal.h"
 
 // each unit's table and error word (HE_CHECKS_UNIT in ntt.cu, fused.cu,
-// exact.cu, noalloc.cu)
+// exact.cu, noalloc.cu, keyswitch.cu)
 int checks_put_ntt(const he::CheckTable *);
 int checks_take_ntt(he::CheckError *);
 int checks_put_fused(const he::CheckTable *);
@@ -31,6 +31,8 @@ int checks_put_exact(const he::CheckTable *);
 int checks_take_exact(he::CheckError *);
 int checks_put_noalloc(const he::CheckTable *);
 int checks_take_noalloc(he::CheckError *);
+int checks_put_keyswitch(const he::CheckTable *);
+int checks_take_keyswitch(he::CheckError *);
 
 namespace he {
 namespace {
@@ -83,14 +85,16 @@ void build_table(CheckTable *t) {
 }
 
 int put_all(const CheckTable *t) {
-    return checks_put_ntt(t) | checks_put_fused(t) | checks_put_exact(t) | checks_put_noalloc(t);
+    return checks_put_ntt(t) | checks_put_fused(t) | checks_put_exact(t) | checks_put_noalloc(t) |
+           checks_put_keyswitch(t);
 }
 
 // read (and clear) every unit's error word; the first violation's text
 unsigned take_all(std::string &text) {
     struct U { const char *name; int (*take)(CheckError *); } units[] = {
         {"ntt.cu / ntt_core.cuh", checks_take_ntt}, {"fused.cu", checks_take_fused},
-        {"exact.cu", checks_take_exact}, {"noalloc.cu", checks_take_noalloc}};
+        {"exact.cu", checks_take_exact}, {"noalloc.cu", checks_take_noalloc},
+        {"keyswitch.cu", checks_take_keyswitch}};
     unsigned total = 0;
     for (auto &u : units) {
         CheckError e = {0, 0, 0};

@@ -67,6 +67,39 @@ struct ConvDev {
     u64 c[MAXP];
 };
 
+// Relinearisation over small primes.  The key-switch sum of limb i,
+// E_i = sum_j D_j rlk_{j,i} (a product in Z[x]/(x^N + 1) of the digits
+// D_j < 2^base and the key residues rlk_{j,i} < q_i), has |E_i| below
+// ell N (2^base - 1)(q_i - 1).  It is computed exactly modulo np primes
+// p_k < 2^30 with P = prod p_k > 4 max|E_i|, in 32-bit arithmetic, and mapped
+// to q_i by a mixed-radix (Garner) CRT: y_0 = r_0, y_k = (((r_k - y_0)
+// p_0^-1 - y_1) p_1^-1 - ... - y_{k-1}) p_{k-1}^-1 mod p_k, E' = y_0 + p_0
+// (y_1 + p_1 (y_2 + ...)) in [0, P), and E = E' - P when y_{np-1} >
+// p_{np-1} / 2 (E' >= 3P/4 exactly when E < 0).
+constexpr int kKsMaxPrimes = 4;
+// Shared memory of the key-switch multiply-accumulate kernel: the exchange
+// buffer (one pad word per tile) and np - 1 parked residue polynomials; a
+// context uses the small primes only where this fits the per-block limit.
+constexpr int kKsSmemLimit = 232448;  // 227 KiB
+inline int ks_mac_smem(int N, int np) { return (N + (N >> kNttTileBits)) * 4 + (np - 1) * N * 4; }
+struct Mod32Dev {
+    uint32_t p, twop;
+    uint32_t pinv;               // -p^-1 mod 2^32 (Montgomery reduction of the 64-bit sums)
+    uint32_t ones;               // floor(2^32 / p): Shoup companion of 1
+    const uint2 *fw, *iw, *z;    // as in ModDev, (value, floor(value 2^32 / p)) pairs;
+                                 // z_e = psi^-e N^-1 2^32 (undoes the Montgomery 2^-32)
+};
+struct KsDev {
+    int np;                      // primes in use (0: the 64-bit path is used)
+    int fold;                    // products summed in 64 bits before a Montgomery fold
+    Mod32Dev m[kKsMaxPrimes];
+    uint32_t ginv[kKsMaxPrimes][kKsMaxPrimes], ginvs[kKsMaxPrimes][kKsMaxPrimes];  // p_m^-1 mod p_k (m < k)
+    uint32_t half_top;           // p_{np-1} / 2
+    int pad_;
+    u64 pq_s[HE_MAX_LIMBS][kKsMaxPrimes];  // floor(p_m 2^64 / q_i): Shoup companion of p_m (< q_i) mod q_i
+    u64 P_q[HE_MAX_LIMBS], P_qs[HE_MAX_LIMBS];  // P mod q_i and companion
+};
+
 // Everything the exact kernels need in one device block.
 struct ExactDev {
     CrtDev Q;                 // coefficient modulus basis
@@ -117,6 +150,8 @@ struct he_ctx {
     // host copies
     std::vector<he::ModDev> h_mods;
     he::ExactDev h_exact;
+    he::KsDev h_ks;                       // relinearisation over small primes (h_ks.np == 0: not used);
+                                          // passed to its kernels by value
     // workspace
     void *ws = nullptr;
     size_t ws_size = 0;
@@ -140,6 +175,7 @@ struct he_keys {
     u64 *pk_ntt = nullptr;   // [2][L][N]
     u64 *rlk = nullptr;      // [ell][2][L][N] coefficient form (or null)
     u64 *rlk_ntt = nullptr;  // [ell][2][L][N]
+    uint32_t *rlk32 = nullptr;  // [ell][2][L][np][N] NTT form mod the small primes (contexts with np > 0)
 };
 
 struct he_plan {
@@ -380,6 +416,19 @@ int launch_sample_multi(he_ctx *c, const SampleJob *jobs, int n, cudaStream_t st
 
 int launch_base_extend(he_ctx *c, const u64 *src, long long n_polys, u64 *dst_aux, cudaStream_t st);
 int launch_scale_round(he_ctx *c, const u64 *d, int n_out, u64 *dq, uint32_t *digits, cudaStream_t st);
+// Key switch over the small primes (keyswitch.cu, contexts with h_ks.np > 0).
+// Forward: n_polys sources (u32 digits < 2^base at src + p*N, or u64 residues
+// of limb p % L at src + p*N when u64_src) to NTT form mod every small
+// prime: dst + (p*np + k)*N.
+int launch_ks_fwd(he_ctx *c, const void *src, bool u64_src, int n_polys, uint32_t *dst, cudaStream_t st);
+// Multiply-accumulate: for output o < n_out, component comp and limb i,
+// out[(o*2 + comp)*L*N + i*N + x] = add[same] + E_i[x] mod q_i with
+// E_i = sum_j D_{o,j} rlk_{j,comp,i}, D in NTT form at dig + (o*ell + j)*np*N.
+int launch_ks_mac(he_ctx *c, const uint32_t *dig, const uint32_t *rlk32, const u64 *add, int n_out, u64 *out,
+                  cudaStream_t st);
+// Choose the small primes for a context (params.cpp; np = 0 when the sums do
+// not fit four of them or the kernel's shared memory) and upload their tables.
+int build_ks(he_ctx *c, std::string &err);
 int launch_decrypt_exact(he_ctx *c, const u64 *x, int n, u64 *m, cudaStream_t st);
 int launch_encode(he_ctx *c, const int32_t *map, int n_polys, int map_polys, const void *tensor, int dtype,
                   long long tensor_stride, int batch, long long out_batch_polys, u64 *out, cudaStream_t st);

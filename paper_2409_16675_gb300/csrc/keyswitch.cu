@@ -1,0 +1,370 @@
+// keyswitch.cu -- the relinearisation key switch over small primes (Section 2,
+// Motivation: CCMul needs relinearisation, Fig. 3(b)).
+//
+// For output o, component comp and limb i the key switch adds
+// E_i = sum_j D_j rlk_{j,comp,i} to the rescaled d_comp, where D_j < 2^base are
+// the digits of d2 and the product is in Z[x]/(x^N + 1).  Every coefficient
+// of E_i is an integer of magnitude below ell N (2^base - 1)(q_i - 1), so it is
+// fixed by its residues modulo a few primes p_k < 2^30 whose product P exceeds
+// four times that bound (three primes for N = 8192, four 50-bit limbs,
+// base 2^16).  The work then runs in the SM's native 32-bit arithmetic:
+//   k_ks_fwd   digits (and, once per key, the key residues) to the NTT domain
+//              modulo every p_k: ell * np transforms per output instead of
+//              ell * L over the 50-bit limbs;
+//   k_ks_mac   per (o, i, comp): for every p_k, sum_j of 32 x 32-bit products
+//              in 64-bit registers (one wide multiply-add per term), one
+//              Montgomery fold, the inverse transform mod p_k and the
+//              untwist; the residues of the first np - 1 primes wait in
+//              shared memory; then the mixed-radix (Garner) CRT gives E_i mod
+//              q_i, which is added to d_comp and stored.
+// The bits equal those of the key switch over the limbs (the sum is exact
+// either way); contexts whose sums need more than four primes, or whose
+// kernel would not fit shared memory, or with limbs below 2^31 keep that one.
+//
+// 32-bit arithmetic: Shoup products a w - floor(a w' / 2^32) p lie in [0, 2p)
+// for every 32-bit a (w' = floor(w 2^32 / p)); the butterflies keep Harvey's
+// bounds (inputs below 4p, X brought below 2p, outputs below 4p < 2^32).
+#include <atomic>
+#include <cstring>
+
+#include "ntt_core.cuh"
+
+namespace he {
+
+typedef uint32_t u32;
+
+__device__ __forceinline__ u32 shoup32(u32 a, u32 w, u32 ws, u32 p) { return a * w - __umulhi(a, ws) * p; }
+__device__ __forceinline__ u32 red32(u32 a, u32 p) { return a >= p ? a - p : a; }
+// a 32-bit value below 2^32 taken into [0, 2p) (Shoup product by 1)
+__device__ __forceinline__ u32 lift32(u32 a, const Mod32Dev &M) { return a - __umulhi(a, M.ones) * M.p; }
+
+// Montgomery fold of a 64-bit sum T: T 2^-32 mod p, in [0, p).  The high word
+// is first brought below p, so T' = h 2^32 + l < p 2^32 and T' + m p (m = l
+// (-p^-1) mod 2^32) is a multiple of 2^32 below 2p 2^32.
+__device__ __forceinline__ u32 mont32(u64 T, const Mod32Dev &M) {
+    u32 h = (u32)(T >> 32);
+    const u32 l = (u32)T;
+    if (h >= M.p) h = red32(lift32(h, M), M.p);
+    const u32 m = l * M.pinv;
+    const u64 s = ((((u64)h) << 32) | l) + (u64)m * M.p;
+    return red32((u32)(s >> 32), M.p);
+}
+
+// Forward pass (as fwd_pass in ntt_core.cuh, the same permuted factor order).
+template <int RB, int S>
+__device__ __forceinline__ void fwd_pass32(u32 (&v)[1 << RB], int tau, int lo, int s0, const Mod32Dev &M) {
+    constexpr int R = 1 << RB;
+    const u32 p = M.p, p2 = M.twop;
+#pragma unroll
+    for (int st = 0; st < S; st++) {
+        const int kb = S - 1 - st;
+        const int s = s0 + st;
+        const int gb = RB - 1 - kb;
+        const int base = (1 << s) + (tau >> lo);
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            if (k & (1 << kb)) continue;
+            const int widx = base + ((k >> (kb + 1)) << (s - gb));
+            const uint2 W = HE_LDG(M.fw + widx);
+            u32 X = v[k];
+            X = X >= p2 ? X - p2 : X;
+            const u32 T = shoup32(v[k | (1 << kb)], W.x, W.y, p);
+            v[k] = X + T;
+            v[k | (1 << kb)] = X - T + p2;
+        }
+    }
+}
+
+// Decimation-in-time pass of the inverse (as inv_pass in ntt_core.cuh).
+template <int RB, int S, int KB0>
+__device__ __forceinline__ void inv_pass32(u32 (&v)[1 << RB], int tau, int lo, int s0, const Mod32Dev &M) {
+    constexpr int R = 1 << RB;
+    const u32 p = M.p, p2 = M.twop;
+#pragma unroll
+    for (int st = 0; st < S; st++) {
+        const int kb = KB0 + st;
+        const int s = s0 + st;
+        const int base = (1 << s) + (tau & ((1 << lo) - 1));
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            if (k & (1 << kb)) continue;
+            const int widx = base + ((k & ((1 << kb) - 1)) << lo);
+            const uint2 W = HE_LDG(M.iw + widx);
+            u32 X = v[k];
+            X = X >= p2 ? X - p2 : X;
+            const u32 T = shoup32(v[k | (1 << kb)], W.x, W.y, p);
+            v[k] = X + T;
+            v[k | (1 << kb)] = X - T + p2;
+        }
+    }
+}
+
+template <int LOGN, int RB>
+__device__ __forceinline__ void exchange32(u32 *sm, u32 (&v)[1 << RB], int tau, int lo_from, int lo_to) {
+    const bool warp_local = warp_bits<LOGN, RB>(lo_from) == warp_bits<LOGN, RB>(lo_to);
+#pragma unroll
+    for (int k = 0; k < (1 << RB); k++) sm[padi<RB>(jidx<RB>(tau, k, lo_from))] = v[k];
+    if (warp_local) __syncwarp();
+    else __syncthreads();
+#pragma unroll
+    for (int k = 0; k < (1 << RB); k++) v[k] = sm[padi<RB>(jidx<RB>(tau, k, lo_to))];
+    if (warp_local) __syncwarp();
+    else __syncthreads();
+}
+
+// Forward transform of loaded values (below 4p) and store in register-tile
+// order (position k*T + tau), reduced into [0, p).
+template <int LOGN>
+__device__ __forceinline__ void fwd32_store(u32 (&v)[Cfg<LOGN>::R], u32 *sm, int tau, const Mod32Dev &M, u32 *d) {
+    constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL, RB = Cfg<LOGN>::RB, R = Cfg<LOGN>::R;
+    int lo = LOGN - RB;
+#pragma unroll
+    for (int pass = 0; pass < NP - 1; pass++) {
+        fwd_pass32<RB, RB>(v, tau, lo, RB * pass, M);
+        const int lo_next = pass == NP - 2 ? 0 : lo - RB;
+        exchange32<LOGN, RB>(sm, v, tau, lo, lo_next);
+        lo = lo_next;
+    }
+    fwd_pass32<RB, RL>(v, tau, 0, RB * (NP - 1), M);
+#pragma unroll
+    for (int k = 0; k < R; k++) HE_ST(d + k * T + tau, red32(red32(v[k], M.twop), M.p));
+}
+
+// Inverse transform (the window schedule of inv_transform in ntt_core.cuh);
+// leaves element k*T + tau of the natural order in v[k], below 4p.
+template <int LOGN>
+__device__ __forceinline__ void inv32(u32 (&v)[Cfg<LOGN>::R], u32 *sm, int tau, const Mod32Dev &M) {
+    constexpr int NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL, RB = Cfg<LOGN>::RB;
+    inv_pass32<RB, RB, 0>(v, tau, 0, 0, M);
+    if (LOGN == 13) {
+        exchange32<LOGN, RB>(sm, v, tau, 0, RB);
+        inv_pass32<RB, RB, 0>(v, tau, RB, RB, M);
+        exchange32<LOGN, RB>(sm, v, tau, RB, 2 * RB - 3);
+        inv_pass32<RB, 1, RB - 1>(v, tau, 2 * RB - 3, 2 * RB, M);
+        exchange32<LOGN, RB>(sm, v, tau, 2 * RB - 3, LOGN - RB);
+        inv_pass32<RB, RB, 0>(v, tau, LOGN - RB, LOGN - RB, M);
+        return;
+    }
+    int lo = 0;
+#pragma unroll
+    for (int pass = 1; pass < NP - 1; pass++) {
+        exchange32<LOGN, RB>(sm, v, tau, lo, RB * pass);
+        lo = RB * pass;
+        inv_pass32<RB, RB, 0>(v, tau, lo, RB * pass, M);
+    }
+    exchange32<LOGN, RB>(sm, v, tau, lo, LOGN - RB);
+    inv_pass32<RB, RL, RB - RL>(v, tau, LOGN - RB, RB * (NP - 1), M);
+}
+
+// ---------------------------------------------------------------- kernels
+// Forward transforms modulo every small prime: blockIdx.x = source polynomial
+// p, blockIdx.y = prime k; u32 sources are digits (< 2^32, taken below 2p),
+// u64 sources key residues (< 2^61, reduced mod p once per key).
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
+    k_ks_fwd(const void *__restrict__ src, int u64_src, u32 *__restrict__ dst, const __grid_constant__ KsDev ks) {
+    extern __shared__ u32 sm32[];
+    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
+    const int tau = threadIdx.x;
+    const int p = blockIdx.x, k = blockIdx.y;
+    const Mod32Dev M = ks.m[k];
+    u32 v[R];
+    if (u64_src) {
+        const u64 *s = (const u64 *)src + (long long)p * N + tau;
+#pragma unroll
+        for (int kk = 0; kk < R; kk++) v[kk] = (u32)(HE_LD(s + kk * T) % M.p);
+    } else {
+        const u32 *s = (const u32 *)src + (long long)p * N + tau;
+#pragma unroll
+        for (int kk = 0; kk < R; kk++) v[kk] = lift32(HE_LD(s + kk * T), M);
+    }
+    fwd32_store<LOGN>(v, sm32, tau, M, dst + ((long long)p * ks.np + k) * N);
+}
+
+struct KsMacArgs {
+    const u32 *dig;    // [n_out][ell][np][N] NTT form
+    const u32 *rlk32;  // [ell][2][L][np][N] NTT form
+    const u64 *add;    // [n_out][2][L][N] coefficient form (rescaled d0, d1)
+    u64 *out;          // [n_out][2][L][N]
+    int ell, L;
+};
+
+// One CTA per (output o, limb i, component comp): blockIdx.x = (o L + i) 2 +
+// comp, so the 2L CTAs that read one output's digits run side by side.
+// CH: coefficients per group of 64-bit sums.
+template <int LOGN, int CH>
+__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
+    k_ks_mac(const KsMacArgs a, const __grid_constant__ KsDev ks, const ModDev *__restrict__ mods) {
+    extern __shared__ u32 sm32[];
+    constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
+    u32 *park = sm32 + (N + N / R);  // residues of primes 0 .. np-2, [k][N], each thread its own words
+    const int tau = threadIdx.x;
+    const int comp = blockIdx.x & 1, oi = blockIdx.x >> 1;
+    const int L = a.L, ell = a.ell, np = ks.np;
+    const int o = oi / L, i = oi - o * L;
+    if (!HE_OBJ_OK(mods + i)) return;  // uniform over the CTA
+    const long long sA = (long long)np * N, sB = 2LL * L * np * N;
+    u32 v[R];
+#pragma unroll 1
+    for (int k = 0; k < np; k++) {
+        const Mod32Dev M = ks.m[k];
+        const u32 *A = a.dig + ((long long)o * ell * np + k) * N + tau;
+        const u32 *B = a.rlk32 + ((long long)(comp * L + i) * np + k) * N + tau;
+        // sum_j A_j B_j: one 32 x 32 -> 64-bit multiply-add per term, folded
+        // (Montgomery, times 2^-32) every ks.fold terms and at the end
+#pragma unroll
+        for (int part = 0; part < R / CH; part++) {
+            u64 acc[CH];
+            u32 tot[CH];
+#pragma unroll
+            for (int kk = 0; kk < CH; kk++) { acc[kk] = 0; tot[kk] = 0; }
+            int cnt = 0;
+#pragma unroll 1
+            for (int j = 0; j < ell; j++) {
+                const u32 *aj = A + j * sA + part * CH * T;
+                const u32 *bj = B + j * sB + part * CH * T;
+#pragma unroll
+                for (int kk = 0; kk < CH; kk++) acc[kk] += (u64)HE_LDG(aj + kk * T) * HE_LDG(bj + kk * T);
+                if (++cnt == ks.fold) {
+#pragma unroll
+                    for (int kk = 0; kk < CH; kk++) { tot[kk] = red32(tot[kk] + mont32(acc[kk], M), M.p); acc[kk] = 0; }
+                    cnt = 0;
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < CH; kk++) v[part * CH + kk] = red32(tot[kk] + mont32(acc[kk], M), M.p);
+        }
+        __syncthreads();  // no thread still reads the exchange buffer (previous prime's transform)
+        inv32<LOGN>(v, sm32, tau, M);
+        // untwist psi^-x N^-1 2^32: residue of E_i mod p_k at element x = kk T + tau
+#pragma unroll
+        for (int kk = 0; kk < R; kk++) {
+            const int x = kk * T + tau;
+            const uint2 z = HE_LDG(M.z + x);
+            const u32 r = red32(shoup32(v[kk], z.x, z.y, M.p), M.p);
+            if (k < np - 1) park[k * N + x] = r;
+            else v[kk] = r;
+        }
+    }
+    // Garner CRT of the np residues, E_i mod q_i, plus d_comp
+    const u64 q = mods[i].q, one_s = mods[i].one_s;
+    const long long off = ((long long)(o * 2 + comp) * L + i) * N;
+    const u64 *add = a.add + off;
+    u64 *out = a.out + off;
+#pragma unroll
+    for (int kk = 0; kk < R; kk++) {
+        const int x = kk * T + tau;
+        u32 y[kKsMaxPrimes], ytop = 0;
+#pragma unroll
+        for (int kp = 0; kp < kKsMaxPrimes; kp++) {
+            if (kp < np) {
+                const u32 p = ks.m[kp].p;
+                u32 t = kp < np - 1 ? park[kp * N + x] : v[kk];
+#pragma unroll
+                for (int m = 0; m < kp; m++) {
+                    const u32 ym = red32(y[m], p);  // y_m < p_m < 2p
+                    t = t >= ym ? t - ym : t + p - ym;
+                    t = red32(shoup32(t, ks.ginv[kp][m], ks.ginvs[kp][m], p), p);
+                }
+                y[kp] = t;
+                ytop = t;
+            }
+        }
+        // E' = y_0 + p_0 (y_1 + p_1 (... + p_{np-2} y_{np-1})) mod q_i: the
+        // innermost step is exact (below 2^60), the rest Shoup products
+        u64 e = 0;
+#pragma unroll
+        for (int m = kKsMaxPrimes - 2; m >= 0; m--) {
+            if (m > np - 2) continue;
+            if (m == np - 2) e = reduce64((u64)ytop * ks.m[m].p + y[m], q, one_s);
+            else e = addm(red1(shoup(e, ks.m[m].p, ks.pq_s[i][m], q), q), (u64)y[m], q);
+        }
+        if (ytop > ks.half_top) e = subm(e, ks.P_q[i], q);  // E < 0: E' - P
+        HE_ST(out + x, addm(e, HE_LD(add + x), q));
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+// True the first time a call site runs on the current device (kernel
+// attributes are per device).
+static bool ks_first_on_device(std::atomic<unsigned long long> &mask) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (mask.load(std::memory_order_acquire) & bit) return false;
+    mask.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
+
+
+template <int LOGN>
+static int ks_fwd_t(he_ctx *c, const void *src, bool u64_src, int n_polys, u32 *dst, cudaStream_t st) {
+    constexpr int N = Cfg<LOGN>::N;
+    const int smem = (N + N / Cfg<LOGN>::R) * 4;
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (ks_first_on_device(attr_mask))
+        cudaFuncSetAttribute(k_ks_fwd<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int np = c->h_ks.np;
+    const double bytes = (double)n_polys * N * ((u64_src ? 8.0 : 4.0) + 4.0 * np);
+    TraceScope ts(c, st, "ks_fwd", bytes, (double)n_polys * np * (N / 2) * LOGN);
+    k_ks_fwd<LOGN><<<dim3((unsigned)n_polys, (unsigned)np), Cfg<LOGN>::T, smem, st>>>(src, u64_src ? 1 : 0, dst,
+                                                                                     c->h_ks);
+    return cuda_check(c, cudaGetLastError(), "k_ks_fwd");
+}
+
+template <int LOGN>
+static int ks_mac_t(he_ctx *c, const u32 *dig, const u32 *rlk32, const u64 *add, int n_out, u64 *out,
+                    cudaStream_t st) {
+    constexpr int N = Cfg<LOGN>::N;
+    constexpr int CH = 8;
+    const int np = c->h_ks.np, L = c->L, ell = c->ell;
+    const int smem = ks_mac_smem(N, np);
+    static std::atomic<unsigned long long> attr_mask{0};
+    if (ks_first_on_device(attr_mask)) {
+        const int most = ks_mac_smem(N, kKsMaxPrimes);
+        cudaFuncSetAttribute(k_ks_mac<LOGN, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             most < kKsSmemLimit ? most : kKsSmemLimit);
+    }
+    const long long blocks = (long long)n_out * L * 2;
+    if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "key-switch launch too large");
+    // digits and key read once, addend read and output written once
+    const double bytes = 4.0 * N * np * ell * ((double)n_out + 2.0 * L) + 16.0 * N * (double)blocks;
+    // 32-bit modular products: terms, butterflies, untwist, Garner
+    const double mm = (double)blocks * N * (np * (ell + (LOGN / 2.0) + 1.0) + np * (np - 1) / 2.0);
+    TraceScope ts(c, st, "ks_mac", bytes, mm);
+    KsMacArgs a;
+    a.dig = dig; a.rlk32 = rlk32; a.add = add; a.out = out; a.ell = ell; a.L = L;
+    k_ks_mac<LOGN, CH><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(a, c->h_ks, c->d_mods);
+    return cuda_check(c, cudaGetLastError(), "k_ks_mac");
+}
+
+int launch_ks_fwd(he_ctx *c, const void *src, bool u64_src, int n_polys, uint32_t *dst, cudaStream_t st) {
+    if (n_polys <= 0) return HE_OK;
+    if (c->h_ks.np < 2) return fail(c, HE_ERR_INVALID_ARG, "no small-prime key switch in this context");
+    switch (c->logN) {
+    case 10: return ks_fwd_t<10>(c, src, u64_src, n_polys, dst, st);
+    case 11: return ks_fwd_t<11>(c, src, u64_src, n_polys, dst, st);
+    case 12: return ks_fwd_t<12>(c, src, u64_src, n_polys, dst, st);
+    case 13: return ks_fwd_t<13>(c, src, u64_src, n_polys, dst, st);
+    case 14: return ks_fwd_t<14>(c, src, u64_src, n_polys, dst, st);
+    }
+    return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
+}
+
+int launch_ks_mac(he_ctx *c, const uint32_t *dig, const uint32_t *rlk32, const u64 *add, int n_out, u64 *out,
+                  cudaStream_t st) {
+    if (n_out <= 0) return HE_OK;
+    if (c->h_ks.np < 2) return fail(c, HE_ERR_INVALID_ARG, "no small-prime key switch in this context");
+    switch (c->logN) {
+    case 10: return ks_mac_t<10>(c, dig, rlk32, add, n_out, out, st);
+    case 11: return ks_mac_t<11>(c, dig, rlk32, add, n_out, out, st);
+    case 12: return ks_mac_t<12>(c, dig, rlk32, add, n_out, out, st);
+    case 13: return ks_mac_t<13>(c, dig, rlk32, add, n_out, out, st);
+    case 14: return ks_mac_t<14>(c, dig, rlk32, add, n_out, out, st);
+    }
+    return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
+}
+
+}  // namespace he
+
+HE_CHECKS_UNIT(keyswitch)

@@ -427,6 +427,122 @@ int build_tables(he_ctx *c, std::string &err) {
         err = "upload tables";
         return HE_ERR_CUDA;
     }
+    return build_ks(c, err);
+}
+
+// Tables of one small prime p < 2^30 of the key switch: the same three tables
+// as add_modulus (forward factors in the register pass order, inverse
+// factors, untwist), as (value, floor(value 2^32 / p)) pairs of 32-bit words;
+// the untwist carries 2^32 for the Montgomery fold of the sums.
+static bool add_ks_prime(he_ctx *c, u64 p, Mod32Dev &M, std::string &err) {
+    const int N = c->N, logN = c->logN;
+    const u64 psi = root_2n(p, N);
+    if (!psi) { err = "no primitive 2N-th root"; return false; }
+    const u64 psiinv = invmod(psi, p), ninv = invmod((u64)N, p), r32 = ((u64)1 << 32) % p;
+    auto comp = [&](u64 w) { return (uint32_t)((w << 32) / p); };
+    std::vector<uint32_t> tab(6 * (size_t)N, 0);
+    uint32_t *fw = tab.data(), *iw = fw + 2 * N, *zt = iw + 2 * N;
+    std::vector<u64> pw(2 * N), ipw(2 * N);
+    pw[0] = ipw[0] = 1;
+    for (int e = 1; e < 2 * N; e++) { pw[e] = mulmod(pw[e - 1], psi, p); ipw[e] = mulmod(ipw[e - 1], psiinv, p); }
+    for (int k = 0; k < N; k++) {
+        const u64 z = mulmod(mulmod(ipw[k], ninv, p), r32, p);
+        zt[2 * k] = (uint32_t)z;
+        zt[2 * k + 1] = comp(z);
+    }
+    const int RB = kNttTileBits, NP = (logN + RB - 1) / RB, RL = logN - RB * (NP - 1);
+    for (int pass = 0; pass < NP; pass++) {
+        const int S = pass == NP - 1 ? RL : RB;
+        for (int st = 0; st < S; st++) {
+            const int s = RB * pass + st, gb = RB - 1 - (S - 1 - st);
+            for (int i = 0; i < (1 << s); i++) {
+                const int g = i & ((1 << gb) - 1), h = i >> gb;
+                const size_t pos = (size_t)(1 << s) + ((size_t)g << (s - gb)) + h;
+                const u64 w = pw[bitrev((1 << s) + i, logN)];
+                fw[2 * pos] = (uint32_t)w;
+                fw[2 * pos + 1] = comp(w);
+            }
+        }
+    }
+    for (int s = 0; s < logN; s++)
+        for (int k = 0; k < (1 << s); k++) {
+            const u64 w = ipw[((u64)k << (logN - s)) % (2 * (u64)N)];
+            const size_t i = (size_t)(1 << s) + k;
+            iw[2 * i] = (uint32_t)w;
+            iw[2 * i + 1] = comp(w);
+        }
+    void *d = nullptr;
+    if (he::dev_alloc(&d, tab.size() * 4) != cudaSuccess) { err = "cudaMalloc key-switch tables"; return false; }
+    c->allocs.push_back(d);
+    if (cudaMemcpy(d, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "upload key-switch tables";
+        return false;
+    }
+    M.p = (uint32_t)p;
+    M.twop = (uint32_t)(2 * p);
+    u64 x = p;  // p^-1 mod 2^64 (Newton), then -p^-1 mod 2^32
+    for (int it = 0; it < 5; it++) x *= 2 - p * x;
+    M.pinv = (uint32_t)(0 - x);
+    M.ones = (uint32_t)((((u64)1) << 32) / p);
+    M.fw = (const uint2 *)d;
+    M.iw = M.fw + N;
+    M.z = M.iw + N;
+    return true;
+}
+
+// The small primes of the relinearisation key switch: the largest primes
+// below 2^30 with p = 1 mod 2N, as many as make P = prod p_k exceed
+// 4 ell N (2^base - 1)(max q_i - 1), the bound on four times any |E_i|.  No
+// small primes (np = 0: the key switch runs over the limbs) when that takes
+// more than kKsMaxPrimes, when the kernel's shared memory would not fit, or
+// when a limb is below 2^31 (the CRT adds the residues y_k < 2^30 mod q_i).
+int build_ks(he_ctx *c, std::string &err) {
+    KsDev &K = c->h_ks;
+    memset(&K, 0, sizeof K);
+    const int N = c->N;
+    u64 qmax = 0;
+    for (u64 q : c->q) {
+        if (q < ((u64)1 << 31)) return HE_OK;
+        qmax = std::max(qmax, q);
+    }
+    const u64 dmax = c->P.base_log2 >= 32 ? 0xffffffffull : (((u64)1 << c->P.base_log2) - 1);
+    const Big bound = product({4, (u64)c->ell, (u64)N, dmax, qmax - 1});
+    std::vector<u64> used = c->q, ps;
+    used.insert(used.end(), c->aux.begin(), c->aux.end());
+    used.push_back(c->P.t);
+    while (ps.size() < 2 || product(ps).bits() - 1 < bound.bits()) {  // P >= 2^(bits(P) - 1)
+        if ((int)ps.size() == kKsMaxPrimes) return HE_OK;
+        const u64 p = next_prime_below(30, N, used);
+        if (!p || p < ((u64)1 << 29)) return HE_OK;
+        used.push_back(p);
+        ps.push_back(p);
+    }
+    const int np = (int)ps.size();
+    if (ks_mac_smem(N, np) > kKsSmemLimit) return HE_OK;
+    for (int k = 0; k < np; k++)
+        if (!add_ks_prime(c, ps[k], K.m[k], err)) return HE_ERR_CUDA;
+    // 64-bit sums of products below (p - 1)^2 fold before they could overflow
+    u128 f = ~(u64)0;
+    for (u64 p : ps) f = std::min<u128>(f, (u128)(~(u64)0) / ((u128)(p - 1) * (p - 1)));
+    K.fold = (int)std::min<u128>(f, 64);
+    for (int k = 0; k < np; k++)
+        for (int m = 0; m < k; m++) {
+            const u64 v = invmod(ps[m] % ps[k], ps[k]);
+            K.ginv[k][m] = (uint32_t)v;
+            K.ginvs[k][m] = (uint32_t)((v << 32) / ps[k]);
+        }
+    K.half_top = (uint32_t)(ps[np - 1] >> 1);
+    for (int i = 0; i < c->L; i++) {
+        const u64 q = c->q[i];
+        u64 P = 1;
+        for (int m = 0; m < np; m++) {
+            K.pq_s[i][m] = shoup_c(ps[m], q);
+            P = mulmod(P, ps[m], q);
+        }
+        K.P_q[i] = P;
+        K.P_qs[i] = shoup_c(P, q);
+    }
+    K.np = np;
     return HE_OK;
 }
 

@@ -47,7 +47,8 @@ class he_params(ctypes.Structure):
 class he_ctx_info(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int32), ("q", ctypes.c_uint64 * HE_MAX_LIMBS),
                 ("t", ctypes.c_uint64), ("ell", ctypes.c_int32), ("n_aux", ctypes.c_int32),
-                ("aux", ctypes.c_uint64 * 24), ("ppmul_ok", ctypes.c_int32)]
+                ("aux", ctypes.c_uint64 * 24), ("ppmul_ok", ctypes.c_int32),
+                ("ks_primes", ctypes.c_int32)]
 
 
 class he_conv_shape(ctypes.Structure):

@@ -18,6 +18,10 @@ RINGS = {
     "n1024": wl.RingSpec(1024, (40, 45), 65537),
     "n16384": wl.RingSpec(16384, (60, 60, 55), 65537),
     "n2048_t40": wl.RingSpec(2048, (50, 50, 50), 1099511480321),
+    # base-2^32 digits: four small primes in the key switch
+    "n8192_b32": wl.RingSpec(8192, (50, 50, 50, 50), 65537, 32),
+    # N = 16384 with three small primes (the 1024-thread kernels)
+    "n16384_np3": wl.RingSpec(16384, (50, 50), 65537),
 }
 _CTX = {}
 
@@ -243,9 +247,19 @@ def test_cpmul_conv_bits(name, families):
     pl.close()
 
 
-@pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2)])
+# small primes of the relinearisation key switch per ring (0: over the limbs;
+# n16384 would need four, whose parked residues exceed shared memory)
+KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 0, "n8192_b32": 4, "n16384_np3": 3}
+
+
+@pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2),
+                                        ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1)])
 def test_ccmul_bits(name, group):
+    """CCMul with relinearisation equals the oracle bit for bit on every key
+    switch: three and four small primes at N = 1024 to 16384, and over the
+    limbs where the small primes do not fit."""
     c = ctx_for(name)
+    assert nv.he_ctx_query(c.h).ks_primes == KS_PRIMES[name]
     P = oparams(c)
     k = layer.Keys(c, 8, True)
     ok = he.keygen(P, 8, True)
