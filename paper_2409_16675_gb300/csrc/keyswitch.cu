@@ -112,11 +112,17 @@ __device__ __forceinline__ void exchange32(u32 *sm, u32 (&v)[1 << RB], int tau, 
     else __syncthreads();
 }
 
-// Forward transform of loaded values (below 4p) and store in register-tile
-// order (position k*T + tau), reduced into [0, p).
+// NTT-domain order of the 32-bit forms: register k of thread tau after the
+// last forward pass (the register-tile element 16 tau + k of the transform)
+// sits at word 4 ((k / 4) T + tau) + k % 4, so each thread stores and loads
+// its coefficients four at a time (16-byte accesses, 512 contiguous bytes
+// per warp); the multiply-accumulate reads both operands in this order and
+// its inverse transform starts from the same register tile.
+// Forward transform of loaded values (below 4p) and store, reduced into [0, p).
 template <int LOGN>
 __device__ __forceinline__ void fwd32_store(u32 (&v)[Cfg<LOGN>::R], u32 *sm, int tau, const Mod32Dev &M, u32 *d) {
     constexpr int T = Cfg<LOGN>::T, NP = Cfg<LOGN>::NP, RL = Cfg<LOGN>::RL, RB = Cfg<LOGN>::RB, R = Cfg<LOGN>::R;
+    static_assert(R % 4 == 0, "four coefficients per 16-byte store");
     int lo = LOGN - RB;
 #pragma unroll
     for (int pass = 0; pass < NP - 1; pass++) {
@@ -126,8 +132,16 @@ __device__ __forceinline__ void fwd32_store(u32 (&v)[Cfg<LOGN>::R], u32 *sm, int
         lo = lo_next;
     }
     fwd_pass32<RB, RL>(v, tau, 0, RB * (NP - 1), M);
+    uint4 *d4 = (uint4 *)d + tau;
 #pragma unroll
-    for (int k = 0; k < R; k++) HE_ST(d + k * T + tau, red32(red32(v[k], M.twop), M.p));
+    for (int m = 0; m < R / 4; m++) {
+        uint4 w;
+        w.x = red32(red32(v[4 * m], M.twop), M.p);
+        w.y = red32(red32(v[4 * m + 1], M.twop), M.p);
+        w.z = red32(red32(v[4 * m + 2], M.twop), M.p);
+        w.w = red32(red32(v[4 * m + 3], M.twop), M.p);
+        HE_ST(d4 + m * T, w);
+    }
 }
 
 // Inverse transform (the window schedule of inv_transform in ntt_core.cuh);
@@ -154,6 +168,24 @@ __device__ __forceinline__ void inv32(u32 (&v)[Cfg<LOGN>::R], u32 *sm, int tau, 
     }
     exchange32<LOGN, RB>(sm, v, tau, lo, LOGN - RB);
     inv_pass32<RB, RL, RB - RL>(v, tau, LOGN - RB, RB * (NP - 1), M);
+}
+
+// One Garner digit: y_k = (((r_k - y_0) p_0^-1 - y_1) p_1^-1 - ...) p_{k-1}^-1
+// mod p_k over the first k digits (y_m < p_m < 2 p_k: one subtraction brings
+// each below p_k).
+__device__ __forceinline__ u32 garner_step(u32 r, u32 p, const u32 *ginv, const u32 *ginvs, u32 y0, u32 y1, u32 y2,
+                                           int k) {
+    const u32 ys[3] = {y0, y1, y2};
+    u32 t = r;
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        if (m < k) {
+            const u32 ym = red32(ys[m], p);
+            t = t >= ym ? t - ym : t + p - ym;
+            t = red32(shoup32(t, ginv[m], ginvs[m], p), p);
+        }
+    }
+    return t;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -203,15 +235,17 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const int L = a.L, ell = a.ell, np = ks.np;
     const int o = oi / L, i = oi - o * L;
     if (!HE_OBJ_OK(mods + i)) return;  // uniform over the CTA
-    const long long sA = (long long)np * N, sB = 2LL * L * np * N;
+    static_assert(CH % 4 == 0, "accumulator groups of whole 16-byte loads");
+    const long long sA = (long long)np * N / 4, sB = 2LL * L * np * N / 4;  // 16-byte words between terms
     u32 v[R];
 #pragma unroll 1
     for (int k = 0; k < np; k++) {
         const Mod32Dev M = ks.m[k];
-        const u32 *A = a.dig + ((long long)o * ell * np + k) * N + tau;
-        const u32 *B = a.rlk32 + ((long long)(comp * L + i) * np + k) * N + tau;
+        const uint4 *A = (const uint4 *)(a.dig + ((long long)o * ell * np + k) * N) + tau;
+        const uint4 *B = (const uint4 *)(a.rlk32 + ((long long)(comp * L + i) * np + k) * N) + tau;
         // sum_j A_j B_j: one 32 x 32 -> 64-bit multiply-add per term, folded
-        // (Montgomery, times 2^-32) every ks.fold terms and at the end
+        // (Montgomery, times 2^-32) every ks.fold terms and at the end; the
+        // term loop is unrolled by two so that two terms' loads are in flight
 #pragma unroll
         for (int part = 0; part < R / CH; part++) {
             u64 acc[CH];
@@ -219,12 +253,18 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
 #pragma unroll
             for (int kk = 0; kk < CH; kk++) { acc[kk] = 0; tot[kk] = 0; }
             int cnt = 0;
-#pragma unroll 1
+#pragma unroll 2
             for (int j = 0; j < ell; j++) {
-                const u32 *aj = A + j * sA + part * CH * T;
-                const u32 *bj = B + j * sB + part * CH * T;
+                const uint4 *aj = A + j * sA + part * (CH / 4) * T;
+                const uint4 *bj = B + j * sB + part * (CH / 4) * T;
 #pragma unroll
-                for (int kk = 0; kk < CH; kk++) acc[kk] += (u64)HE_LDG(aj + kk * T) * HE_LDG(bj + kk * T);
+                for (int g = 0; g < CH / 4; g++) {
+                    const uint4 x = HE_LDG(aj + g * T), y = HE_LDG(bj + g * T);
+                    acc[4 * g] += (u64)x.x * y.x;
+                    acc[4 * g + 1] += (u64)x.y * y.y;
+                    acc[4 * g + 2] += (u64)x.z * y.z;
+                    acc[4 * g + 3] += (u64)x.w * y.w;
+                }
                 if (++cnt == ks.fold) {
 #pragma unroll
                     for (int kk = 0; kk < CH; kk++) { tot[kk] = red32(tot[kk] + mont32(acc[kk], M), M.p); acc[kk] = 0; }
@@ -251,33 +291,33 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     const long long off = ((long long)(o * 2 + comp) * L + i) * N;
     const u64 *add = a.add + off;
     u64 *out = a.out + off;
+    static_assert(kKsMaxPrimes == 4, "the CRT below is written out for up to four primes");
+    const u32 p0 = ks.m[0].p, p1 = ks.m[1].p, p2 = ks.m[2].p, p3 = ks.m[3].p;
 #pragma unroll
     for (int kk = 0; kk < R; kk++) {
         const int x = kk * T + tau;
-        u32 y[kKsMaxPrimes], ytop = 0;
-#pragma unroll
-        for (int kp = 0; kp < kKsMaxPrimes; kp++) {
-            if (kp < np) {
-                const u32 p = ks.m[kp].p;
-                u32 t = kp < np - 1 ? park[kp * N + x] : v[kk];
-#pragma unroll
-                for (int m = 0; m < kp; m++) {
-                    const u32 ym = red32(y[m], p);  // y_m < p_m < 2p
-                    t = t >= ym ? t - ym : t + p - ym;
-                    t = red32(shoup32(t, ks.ginv[kp][m], ks.ginvs[kp][m], p), p);
-                }
-                y[kp] = t;
-                ytop = t;
-            }
-        }
-        // E' = y_0 + p_0 (y_1 + p_1 (... + p_{np-2} y_{np-1})) mod q_i: the
-        // innermost step is exact (below 2^60), the rest Shoup products
-        u64 e = 0;
-#pragma unroll
-        for (int m = kKsMaxPrimes - 2; m >= 0; m--) {
-            if (m > np - 2) continue;
-            if (m == np - 2) e = reduce64((u64)ytop * ks.m[m].p + y[m], q, one_s);
-            else e = addm(red1(shoup(e, ks.m[m].p, ks.pq_s[i][m], q), q), (u64)y[m], q);
+        // residues r_k (the last prime's in v) and the mixed-radix digits y_k
+        const u32 y0 = park[x];
+        const u32 y1 = garner_step(np > 2 ? park[N + x] : v[kk], p1, ks.ginv[1], ks.ginvs[1], y0, 0, 0, 1);
+        u32 y2 = 0, y3 = 0;
+        if (np > 2) y2 = garner_step(np > 3 ? park[2 * N + x] : v[kk], p2, ks.ginv[2], ks.ginvs[2], y0, y1, 0, 2);
+        if (np > 3) y3 = garner_step(v[kk], p3, ks.ginv[3], ks.ginvs[3], y0, y1, y2, 3);
+        // E' = y_0 + p_0 (y_1 + p_1 (y_2 + p_2 y_3)) mod q_i: the innermost
+        // step is exact (below 2^60), the rest Shoup products
+        u64 e;
+        u32 ytop;
+        if (np == 2) {
+            e = reduce64((u64)y1 * p0 + y0, q, one_s);
+            ytop = y1;
+        } else if (np == 3) {
+            e = reduce64((u64)y2 * p1 + y1, q, one_s);
+            e = addm(red1(shoup(e, p0, ks.pq_s[i][0], q), q), (u64)y0, q);
+            ytop = y2;
+        } else {
+            e = reduce64((u64)y3 * p2 + y2, q, one_s);
+            e = addm(red1(shoup(e, p1, ks.pq_s[i][1], q), q), (u64)y1, q);
+            e = addm(red1(shoup(e, p0, ks.pq_s[i][0], q), q), (u64)y0, q);
+            ytop = y3;
         }
         if (ytop > ks.half_top) e = subm(e, ks.P_q[i], q);  // E < 0: E' - P
         HE_ST(out + x, addm(e, HE_LD(add + x), q));
