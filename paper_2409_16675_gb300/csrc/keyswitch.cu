@@ -193,7 +193,7 @@ __device__ __forceinline__ u32 garner_step(u32 r, u32 p, const u32 *ginv, const 
 // p, blockIdx.y = prime k; u32 sources are digits (< 2^32, taken below 2p),
 // u64 sources key residues (< 2^61, reduced mod p once per key).
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
+__global__ void __launch_bounds__(Cfg<LOGN>::T, (LOGN >= 14 ? 1 : 3))
     k_ks_fwd(const void *__restrict__ src, int u64_src, u32 *__restrict__ dst, const __grid_constant__ KsDev ks) {
     extern __shared__ u32 sm32[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
