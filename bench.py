@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (read + write) per launch of the k_mac_intt family in this
 # workload, averaged over its launches in one ncu capture of this command
 # (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-MAC_INTT_TRAFFIC = 709.4e6
+MAC_INTT_TRAFFIC = 305.1e6
 
 METRIC = "Encrypted conv layers/s & NTT HBM GB/s (% of peak) vs plain launch; p50/p99 latency"
 UNIT = "layers/s"

@@ -86,12 +86,14 @@ struct Mod32Dev {
     uint32_t p, twop;
     uint32_t pinv;               // -p^-1 mod 2^32 (Montgomery reduction of the 64-bit sums)
     uint32_t ones;               // floor(2^32 / p): Shoup companion of 1
+    uint32_t r32;                // 2^32 mod p
+    uint32_t pad_;
     const uint2 *fw, *iw, *z;    // as in ModDev, (value, floor(value 2^32 / p)) pairs;
                                  // z_e = psi^-e N^-1 2^32 (undoes the Montgomery 2^-32)
 };
 struct KsDev {
     int np;                      // primes in use (0: the 64-bit path is used)
-    int fold;                    // products summed in 64 bits before a Montgomery fold
+    int fold;                    // products added to a 64-bit sum between exact folds
     Mod32Dev m[kKsMaxPrimes];
     uint32_t ginv[kKsMaxPrimes][kKsMaxPrimes], ginvs[kKsMaxPrimes][kKsMaxPrimes];  // p_m^-1 mod p_k (m < k)
     uint32_t half_top;           // p_{np-1} / 2

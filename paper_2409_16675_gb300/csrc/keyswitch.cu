@@ -38,7 +38,14 @@ __device__ __forceinline__ u32 red32(u32 a, u32 p) { return a >= p ? a - p : a; 
 // a 32-bit value below 2^32 taken into [0, 2p) (Shoup product by 1)
 __device__ __forceinline__ u32 lift32(u32 a, const Mod32Dev &M) { return a - __umulhi(a, M.ones) * M.p; }
 
-// Montgomery fold of a 64-bit sum T: T 2^-32 mod p, in [0, p).  The high word
+// Exact fold of a 64-bit sum T = h 2^32 + l: (h mod p)(2^32 mod p) + l, the
+// same residue, below (p - 1)^2 + 2^32.
+__device__ __forceinline__ u64 fold32(u64 T, const Mod32Dev &M) {
+    const u32 h = red32(lift32((u32)(T >> 32), M), M.p);
+    return (u64)h * M.r32 + (u32)T;
+}
+
+// Montgomery reduction of a 64-bit sum T: T 2^-32 mod p, in [0, p).  The high word
 // is first brought below p, so T' = h 2^32 + l < p 2^32 and T' + m p (m = l
 // (-p^-1) mod 2^32) is a multiple of 2^32 below 2p 2^32.
 __device__ __forceinline__ u32 mont32(u64 T, const Mod32Dev &M) {
@@ -189,16 +196,18 @@ __device__ __forceinline__ u32 garner_step(u32 r, u32 p, const u32 *ginv, const 
 }
 
 // ---------------------------------------------------------------- kernels
-// Forward transforms modulo every small prime: blockIdx.x = source polynomial
-// p, blockIdx.y = prime k; u32 sources are digits (< 2^32, taken below 2p),
-// u64 sources key residues (< 2^61, reduced mod p once per key).
+// Forward transforms modulo every small prime: blockIdx.x = p np + k for
+// source polynomial p and prime k, so the np CTAs reading one source run side
+// by side and all but the first find it in L2; u32 sources are digits
+// (< 2^32, taken below 2p), u64 sources key residues (< 2^61, reduced mod p
+// once per key).
 template <int LOGN>
 __global__ void __launch_bounds__(Cfg<LOGN>::T, (LOGN >= 14 ? 1 : 3))
     k_ks_fwd(const void *__restrict__ src, int u64_src, u32 *__restrict__ dst, const __grid_constant__ KsDev ks) {
     extern __shared__ u32 sm32[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
     const int tau = threadIdx.x;
-    const int p = blockIdx.x, k = blockIdx.y;
+    const int p = (int)blockIdx.x / ks.np, k = (int)blockIdx.x - p * ks.np;
     const Mod32Dev M = ks.m[k];
     u32 v[R];
     if (u64_src) {
@@ -244,14 +253,14 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
         const uint4 *A = (const uint4 *)(a.dig + ((long long)o * ell * np + k) * N) + tau;
         const uint4 *B = (const uint4 *)(a.rlk32 + ((long long)(comp * L + i) * np + k) * N) + tau;
         // sum_j A_j B_j: one 32 x 32 -> 64-bit multiply-add per term, folded
-        // (Montgomery, times 2^-32) every ks.fold terms and at the end; the
-        // term loop is unrolled by two so that two terms' loads are in flight
+        // exactly every ks.fold terms (ell is below it at the usual digit
+        // bases) and Montgomery-reduced (times 2^-32) at the end; the term
+        // loop is unrolled by two so that two terms' loads are in flight
 #pragma unroll
         for (int part = 0; part < R / CH; part++) {
             u64 acc[CH];
-            u32 tot[CH];
 #pragma unroll
-            for (int kk = 0; kk < CH; kk++) { acc[kk] = 0; tot[kk] = 0; }
+            for (int kk = 0; kk < CH; kk++) acc[kk] = 0;
             int cnt = 0;
 #pragma unroll 2
             for (int j = 0; j < ell; j++) {
@@ -267,12 +276,12 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
                 }
                 if (++cnt == ks.fold) {
 #pragma unroll
-                    for (int kk = 0; kk < CH; kk++) { tot[kk] = red32(tot[kk] + mont32(acc[kk], M), M.p); acc[kk] = 0; }
+                    for (int kk = 0; kk < CH; kk++) acc[kk] = fold32(acc[kk], M);
                     cnt = 0;
                 }
             }
 #pragma unroll
-            for (int kk = 0; kk < CH; kk++) v[part * CH + kk] = red32(tot[kk] + mont32(acc[kk], M), M.p);
+            for (int kk = 0; kk < CH; kk++) v[part * CH + kk] = mont32(acc[kk], M);
         }
         __syncthreads();  // no thread still reads the exchange buffer (previous prime's transform)
         inv32<LOGN>(v, sm32, tau, M);
@@ -347,8 +356,8 @@ static int ks_fwd_t(he_ctx *c, const void *src, bool u64_src, int n_polys, u32 *
     const int np = c->h_ks.np;
     const double bytes = (double)n_polys * N * ((u64_src ? 8.0 : 4.0) + 4.0 * np);
     TraceScope ts(c, st, "ks_fwd", bytes, (double)n_polys * np * (N / 2) * LOGN);
-    k_ks_fwd<LOGN><<<dim3((unsigned)n_polys, (unsigned)np), Cfg<LOGN>::T, smem, st>>>(src, u64_src ? 1 : 0, dst,
-                                                                                     c->h_ks);
+    if ((long long)n_polys * np > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "key-switch launch too large");
+    k_ks_fwd<LOGN><<<(unsigned)(n_polys * np), Cfg<LOGN>::T, smem, st>>>(src, u64_src ? 1 : 0, dst, c->h_ks);
     return cuda_check(c, cudaGetLastError(), "k_ks_fwd");
 }
 

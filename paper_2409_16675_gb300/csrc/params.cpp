@@ -484,6 +484,7 @@ static bool add_ks_prime(he_ctx *c, u64 p, Mod32Dev &M, std::string &err) {
     for (int it = 0; it < 5; it++) x *= 2 - p * x;
     M.pinv = (uint32_t)(0 - x);
     M.ones = (uint32_t)((((u64)1) << 32) / p);
+    M.r32 = (uint32_t)r32;
     M.fw = (const uint2 *)d;
     M.iw = M.fw + N;
     M.z = M.iw + N;
@@ -521,9 +522,14 @@ int build_ks(he_ctx *c, std::string &err) {
     if (ks_mac_smem(N, np) > kKsSmemLimit) return HE_OK;
     for (int k = 0; k < np; k++)
         if (!add_ks_prime(c, ps[k], K.m[k], err)) return HE_ERR_CUDA;
-    // 64-bit sums of products below (p - 1)^2 fold before they could overflow
+    // a 64-bit sum of products below (p - 1)^2 is folded to (h mod p)(2^32
+    // mod p) + l < (p - 1)^2 + 2^32 every `fold` products, so it stays below
+    // 2^64 with fold more products added
     u128 f = ~(u64)0;
-    for (u64 p : ps) f = std::min<u128>(f, (u128)(~(u64)0) / ((u128)(p - 1) * (p - 1)));
+    for (u64 p : ps) {
+        const u128 sq = (u128)(p - 1) * (p - 1);
+        f = std::min<u128>(f, ((u128)(~(u64)0) - sq - ((u128)1 << 32)) / sq);
+    }
     K.fold = (int)std::min<u128>(f, 64);
     for (int k = 0; k < np; k++)
         for (int m = 0; m < k; m++) {

@@ -22,6 +22,8 @@ RINGS = {
     "n8192_b32": wl.RingSpec(8192, (50, 50, 50, 50), 65537, 32),
     # N = 16384 with three small primes (the 1024-thread kernels)
     "n16384_np3": wl.RingSpec(16384, (50, 50), 65537),
+    # 16 digits: the key switch's 64-bit sums are folded once (every 14 terms)
+    "n4096_l5": wl.RingSpec(4096, (50, 50, 50, 50, 50), 65537),
 }
 _CTX = {}
 
@@ -249,11 +251,12 @@ def test_cpmul_conv_bits(name, families):
 
 # small primes of the relinearisation key switch per ring (0: over the limbs;
 # n16384 would need four, whose parked residues exceed shared memory)
-KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 0, "n8192_b32": 4, "n16384_np3": 3}
+KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 0, "n8192_b32": 4, "n16384_np3": 3,
+             "n4096_l5": 3}
 
 
 @pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2),
-                                        ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1)])
+                                        ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1), ("n4096_l5", 2)])
 def test_ccmul_bits(name, group):
     """CCMul with relinearisation equals the oracle bit for bit on every key
     switch: three and four small primes at N = 1024 to 16384, and over the
