@@ -81,21 +81,25 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 10 ms while running."""
+    """nvidia-smi clock / throttle samples every period_ms (10 ms by default)
+    while running.  The serving sweep samples every 100 ms: its windows last
+    seconds, and each query takes driver locks that the request server's
+    worker also needs."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=10):
         self.index = index
+        self.period_ms = period_ms
         self.samples = []
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "10"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -723,7 +727,7 @@ def serve_measure(rates, seconds, warmup_s, budget_gb):
 
     sweep = []
     gpu = int(os.environ.get("LOCAL_RANK", "0"))
-    with ClockSampler(gpu) as clk:
+    with ClockSampler(gpu, 100) as clk:
         for ri, rate in enumerate(rates):
             times, who = wl.poisson_arrivals(wl.MASTER_SEED + 50 + ri, rate, warmup_s + seconds, len(clients))
             inflight = [[] for _ in clients]          # (request id, slot)
