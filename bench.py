@@ -472,14 +472,19 @@ def run_gpu(args):
     # (the 32-bit multiplies of one 64-bit Shoup modular product); achieved =
     # algorithmic modular products (butterflies, untwist/scaling products, MAC
     # terms) per second over the kernel's event-timed launches.
+    # The key-switch families (ks_*) count 32-bit modular products: a Shoup
+    # product there is one high-half multiply (half rate, two lane slots) and
+    # two low multiplies, so their peak is the same lane rate / 4.
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = sms * 64 * mhz * 1e6 / 10 / 1e12
+    per_product = 4 if name.startswith("ks_") else 10
+    alu_peak = sms * 64 * mhz * 1e6 / per_product / 1e12
     alu = mm / (tot_ms / 1000.0) / 1e12
-    roof = {"kernel": name, "bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tmodmul/s",
+    roof = {"kernel": name, "bound": "alu", "achieved": alu, "peak": alu_peak,
+            "unit": "Tmodmul32/s" if per_product == 4 else "Tmodmul/s",
             "frac": alu / alu_peak,
-            "peak_source": "derived: %d SMs x 64 IMAD lanes/cycle x %.0f MHz / 10 IMAD per 64-bit modular product"
-                           % (sms, mhz),
+            "peak_source": "derived: %d SMs x 64 IMAD lanes/cycle x %.0f MHz / %d IMAD per %d-bit modular product"
+                           % (sms, mhz, per_product, 32 if per_product == 4 else 64),
             "traffic": MAC_INTT_TRAFFIC if name == "mac_intt" else None,
             "launches": launches, "avg_launch_us": 1000.0 * tot_ms / launches,
             "timed_region": "the same K steps again with a CUDA event pair around every launch: %.3f ms per step"
@@ -489,7 +494,8 @@ def run_gpu(args):
     total_ms = sum(u[1] for u in trace.values())
     kernels = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms,
                    "GB/s": v[2] / (v[1] / 1000.0) / 1e9 if v[1] else None,
-                   "Tmodmul/s": v[3] / (v[1] / 1000.0) / 1e12 if v[1] else None}
+                   ("Tmodmul32/s" if k.startswith("ks_") else "Tmodmul/s"):
+                       v[3] / (v[1] / 1000.0) / 1e12 if v[1] else None}
                for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}
     families = {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms} for k, v in fam.items()}
     launches_total = sum(v[0] for v in trace.values())
