@@ -743,14 +743,16 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     const bool ks32 = np >= 2 && k->rlk32;
     // per-output scratch: tensor d (3 polys over Q u B), rescaled d0, d1, digits, digit NTTs
     const size_t dign_words = ks32 ? ((size_t)ell * np * N + 1) / 2 : (size_t)ell * LN;
-    const size_t per_out = 3 * LKN * 8 + 2 * LN * 8 + (size_t)ell * N * 4 + dign_words * 8;
+    const size_t park_words = ks32 ? ((size_t)2 * L * (np - 1) * N + 1) / 2 : 0;  // key switch's parked residues
+    const size_t per_out = 3 * LKN * 8 + 2 * LN * 8 + (size_t)ell * N * 4 + dign_words * 8 + park_words * 8;
     // outputs are processed in chunks whose scratch fits the context's budget (default 4 GiB)
     const size_t chunk_budget =
         c->P.max_ccmul_scratch_bytes > 0 ? (size_t)c->P.max_ccmul_scratch_bytes : (size_t)4 << 30;
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_out, chunk_budget / per_out));
     size_t need = Carver::round((size_t)(n_a + n_b) * 2 * KN * 8) + Carver::round((size_t)(n_a + n_b) * 2 * LKN * 8) +
                   Carver::round((size_t)chunk * 3 * LKN * 8) + Carver::round((size_t)chunk * 2 * LN * 8) +
-                  Carver::round((size_t)chunk * ell * N * 4) + Carver::round((size_t)chunk * dign_words * 8) + 8192;
+                  Carver::round((size_t)chunk * ell * N * 4) + Carver::round((size_t)chunk * dign_words * 8) +
+                  Carver::round((size_t)chunk * park_words * 8) + 8192;
     TRY(ws_reserve(c, need));
     Carver cv(c->ws);
     u64 *aux_a = cv.take<u64>((size_t)n_a * 2 * KN);
@@ -761,6 +763,7 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
     u64 *dq = cv.take<u64>((size_t)chunk * 2 * LN);
     uint32_t *dig = cv.take<uint32_t>((size_t)chunk * ell * N);
     u64 *dign = cv.take<u64>((size_t)chunk * dign_words);
+    u64 *park = cv.take<u64>((size_t)chunk * park_words);
     TraceRole tr_("ccmul_in");
     // 1. exact base extension Q -> B of both operands
     TRY(launch_base_extend(c, ct_a, (long long)n_a * 2, aux_a, st));
@@ -809,7 +812,8 @@ int he_ccmul_precompute(he_ctx *c, const he_keys *k, const uint64_t *ct_a, int n
             g_trace_role = "relin_digits";
             TRY(launch_ks_fwd(c, dig, false, nc * ell, (uint32_t *)dign, st));
             g_trace_role = "relin";
-            TRY(launch_ks_mac(c, (const uint32_t *)dign, k->rlk32, dq, nc, ct_out + (size_t)o0 * 2 * LN, st));
+            TRY(launch_ks_mac(c, (const uint32_t *)dign, k->rlk32, dq, nc, ct_out + (size_t)o0 * 2 * LN,
+                              (uint32_t *)park, st));
             continue;
         }
         g_trace_role = "relin_digits";

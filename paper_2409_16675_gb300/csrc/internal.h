@@ -77,11 +77,6 @@ struct ConvDev {
 // (y_1 + p_1 (y_2 + ...)) in [0, P), and E = E' - P when y_{np-1} >
 // p_{np-1} / 2 (E' >= 3P/4 exactly when E < 0).
 constexpr int kKsMaxPrimes = 4;
-// Shared memory of the key-switch multiply-accumulate kernel: the exchange
-// buffer (one pad word per tile) and np - 1 parked residue polynomials; a
-// context uses the small primes only where this fits the per-block limit.
-constexpr int kKsSmemLimit = 232448;  // 227 KiB
-inline int ks_mac_smem(int N, int np) { return (N + (N >> kNttTileBits)) * 4 + (np - 1) * N * 4; }
 struct Mod32Dev {
     uint32_t p, twop;
     uint32_t pinv;               // -p^-1 mod 2^32 (Montgomery reduction of the 64-bit sums)
@@ -426,8 +421,9 @@ int launch_ks_fwd(he_ctx *c, const void *src, bool u64_src, int n_polys, uint32_
 // Multiply-accumulate: for output o < n_out, component comp and limb i,
 // out[(o*2 + comp)*L*N + i*N + x] = add[same] + E_i[x] mod q_i with
 // E_i = sum_j D_{o,j} rlk_{j,comp,i}, D in NTT form at dig + (o*ell + j)*np*N.
+// park: device scratch of n_out*L*2*(np-1)*N words.
 int launch_ks_mac(he_ctx *c, const uint32_t *dig, const uint32_t *rlk32, const u64 *add, int n_out, u64 *out,
-                  cudaStream_t st);
+                  uint32_t *park, cudaStream_t st);
 // Choose the small primes for a context (params.cpp; np = 0 when the sums do
 // not fit four of them or the kernel's shared memory) and upload their tables.
 int build_ks(he_ctx *c, std::string &err);

@@ -14,9 +14,11 @@
 //   k_ks_mac   per (o, i, comp): for every p_k, sum_j of 32 x 32-bit products
 //              in 64-bit registers (one wide multiply-add per term), one
 //              Montgomery fold, the inverse transform mod p_k and the
-//              untwist; the residues of the first np - 1 primes wait in
-//              shared memory; then the mixed-radix (Garner) CRT gives E_i mod
-//              q_i, which is added to d_comp and stored.
+//              untwist; the residues of the first np - 1 primes wait in a
+//              global scratch that stays in L2 (each thread rereads its own
+//              words), so shared memory holds only the exchange buffer and
+//              three CTAs fit on an SM; then the mixed-radix (Garner) CRT gives
+//              E_i mod q_i, which is added to d_comp and stored.
 // The bits equal those of the key switch over the limbs (the sum is exact
 // either way); contexts whose sums need more than four primes, or whose
 // kernel would not fit shared memory, or with limbs below 2^31 keep that one.
@@ -227,18 +229,21 @@ struct KsMacArgs {
     const u32 *rlk32;  // [ell][2][L][np][N] NTT form
     const u64 *add;    // [n_out][2][L][N] coefficient form (rescaled d0, d1)
     u64 *out;          // [n_out][2][L][N]
+    u32 *park;         // [n_out * L * 2][np - 1][N] residues of the first np - 1 primes
     int ell, L;
 };
 
 // One CTA per (output o, limb i, component comp): blockIdx.x = (o L + i) 2 +
 // comp, so the 2L CTAs that read one output's digits run side by side.
-// CH: coefficients per group of 64-bit sums.
+// CH: coefficients per group of 64-bit sums.  Three resident CTAs per SM
+// (40 registers) below N = 16384.
 template <int LOGN, int CH>
-__global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
+__global__ void __launch_bounds__(Cfg<LOGN>::T, (LOGN >= 14 ? 1 : 3))
     k_ks_mac(const KsMacArgs a, const __grid_constant__ KsDev ks, const ModDev *__restrict__ mods) {
     extern __shared__ u32 sm32[];
     constexpr int N = Cfg<LOGN>::N, T = Cfg<LOGN>::T, R = Cfg<LOGN>::R;
-    u32 *park = sm32 + (N + N / R);  // residues of primes 0 .. np-2, [k][N], each thread its own words
+    // residues of primes 0 .. np-2, [k][N]; each thread rereads only its own words
+    u32 *park = a.park + (long long)blockIdx.x * (ks.np - 1) * N;
     const int tau = threadIdx.x;
     const int comp = blockIdx.x & 1, oi = blockIdx.x >> 1;
     const int L = a.L, ell = a.ell, np = ks.np;
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
             const int x = kk * T + tau;
             const uint2 z = HE_LDG(M.z + x);
             const u32 r = red32(shoup32(v[kk], z.x, z.y, M.p), M.p);
-            if (k < np - 1) park[k * N + x] = r;
+            if (k < np - 1) HE_ST(park + k * N + x, r);
             else v[kk] = r;
         }
     }
@@ -306,10 +311,11 @@ __global__ void __launch_bounds__(Cfg<LOGN>::T, Cfg<LOGN>::MINB)
     for (int kk = 0; kk < R; kk++) {
         const int x = kk * T + tau;
         // residues r_k (the last prime's in v) and the mixed-radix digits y_k
-        const u32 y0 = park[x];
-        const u32 y1 = garner_step(np > 2 ? park[N + x] : v[kk], p1, ks.ginv[1], ks.ginvs[1], y0, 0, 0, 1);
+        const u32 y0 = HE_LD(park + x);
+        const u32 y1 = garner_step(np > 2 ? HE_LD(park + N + x) : v[kk], p1, ks.ginv[1], ks.ginvs[1], y0, 0, 0, 1);
         u32 y2 = 0, y3 = 0;
-        if (np > 2) y2 = garner_step(np > 3 ? park[2 * N + x] : v[kk], p2, ks.ginv[2], ks.ginvs[2], y0, y1, 0, 2);
+        if (np > 2)
+            y2 = garner_step(np > 3 ? HE_LD(park + 2 * N + x) : v[kk], p2, ks.ginv[2], ks.ginvs[2], y0, y1, 0, 2);
         if (np > 3) y3 = garner_step(v[kk], p3, ks.ginv[3], ks.ginvs[3], y0, y1, y2, 3);
         // E' = y_0 + p_0 (y_1 + p_1 (y_2 + p_2 y_3)) mod q_i: the innermost
         // step is exact (below 2^60), the rest Shoup products
@@ -362,18 +368,15 @@ static int ks_fwd_t(he_ctx *c, const void *src, bool u64_src, int n_polys, u32 *
 }
 
 template <int LOGN>
-static int ks_mac_t(he_ctx *c, const u32 *dig, const u32 *rlk32, const u64 *add, int n_out, u64 *out,
+static int ks_mac_t(he_ctx *c, const u32 *dig, const u32 *rlk32, const u64 *add, int n_out, u64 *out, u32 *park,
                     cudaStream_t st) {
     constexpr int N = Cfg<LOGN>::N;
-    constexpr int CH = 8;
+    constexpr int CH = 4;
     const int np = c->h_ks.np, L = c->L, ell = c->ell;
-    const int smem = ks_mac_smem(N, np);
+    const int smem = (N + N / Cfg<LOGN>::R) * 4;
     static std::atomic<unsigned long long> attr_mask{0};
-    if (ks_first_on_device(attr_mask)) {
-        const int most = ks_mac_smem(N, kKsMaxPrimes);
-        cudaFuncSetAttribute(k_ks_mac<LOGN, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             most < kKsSmemLimit ? most : kKsSmemLimit);
-    }
+    if (ks_first_on_device(attr_mask))
+        cudaFuncSetAttribute(k_ks_mac<LOGN, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const long long blocks = (long long)n_out * L * 2;
     if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "key-switch launch too large");
     // digits and key read once, addend read and output written once
@@ -382,7 +385,7 @@ static int ks_mac_t(he_ctx *c, const u32 *dig, const u32 *rlk32, const u64 *add,
     const double mm = (double)blocks * N * (np * (ell + (LOGN / 2.0) + 1.0) + np * (np - 1) / 2.0);
     TraceScope ts(c, st, "ks_mac", bytes, mm);
     KsMacArgs a;
-    a.dig = dig; a.rlk32 = rlk32; a.add = add; a.out = out; a.ell = ell; a.L = L;
+    a.dig = dig; a.rlk32 = rlk32; a.add = add; a.out = out; a.park = park; a.ell = ell; a.L = L;
     k_ks_mac<LOGN, CH><<<(unsigned)blocks, Cfg<LOGN>::T, smem, st>>>(a, c->h_ks, c->d_mods);
     return cuda_check(c, cudaGetLastError(), "k_ks_mac");
 }
@@ -401,15 +404,15 @@ int launch_ks_fwd(he_ctx *c, const void *src, bool u64_src, int n_polys, uint32_
 }
 
 int launch_ks_mac(he_ctx *c, const uint32_t *dig, const uint32_t *rlk32, const u64 *add, int n_out, u64 *out,
-                  cudaStream_t st) {
+                  uint32_t *park, cudaStream_t st) {
     if (n_out <= 0) return HE_OK;
     if (c->h_ks.np < 2) return fail(c, HE_ERR_INVALID_ARG, "no small-prime key switch in this context");
     switch (c->logN) {
-    case 10: return ks_mac_t<10>(c, dig, rlk32, add, n_out, out, st);
-    case 11: return ks_mac_t<11>(c, dig, rlk32, add, n_out, out, st);
-    case 12: return ks_mac_t<12>(c, dig, rlk32, add, n_out, out, st);
-    case 13: return ks_mac_t<13>(c, dig, rlk32, add, n_out, out, st);
-    case 14: return ks_mac_t<14>(c, dig, rlk32, add, n_out, out, st);
+    case 10: return ks_mac_t<10>(c, dig, rlk32, add, n_out, out, park, st);
+    case 11: return ks_mac_t<11>(c, dig, rlk32, add, n_out, out, park, st);
+    case 12: return ks_mac_t<12>(c, dig, rlk32, add, n_out, out, park, st);
+    case 13: return ks_mac_t<13>(c, dig, rlk32, add, n_out, out, park, st);
+    case 14: return ks_mac_t<14>(c, dig, rlk32, add, n_out, out, park, st);
     }
     return fail(c, HE_ERR_UNSUPPORTED_PARAMS, "unsupported N");
 }

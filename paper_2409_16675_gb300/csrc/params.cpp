@@ -495,8 +495,8 @@ static bool add_ks_prime(he_ctx *c, u64 p, Mod32Dev &M, std::string &err) {
 // below 2^30 with p = 1 mod 2N, as many as make P = prod p_k exceed
 // 4 ell N (2^base - 1)(max q_i - 1), the bound on four times any |E_i|.  No
 // small primes (np = 0: the key switch runs over the limbs) when that takes
-// more than kKsMaxPrimes, when the kernel's shared memory would not fit, or
-// when a limb is below 2^31 (the CRT adds the residues y_k < 2^30 mod q_i).
+// more than kKsMaxPrimes, or when a limb is below 2^31 (the CRT adds the
+// residues y_k < 2^30 mod q_i).
 int build_ks(he_ctx *c, std::string &err) {
     KsDev &K = c->h_ks;
     memset(&K, 0, sizeof K);
@@ -519,7 +519,6 @@ int build_ks(he_ctx *c, std::string &err) {
         ps.push_back(p);
     }
     const int np = (int)ps.size();
-    if (ks_mac_smem(N, np) > kKsSmemLimit) return HE_OK;
     for (int k = 0; k < np; k++)
         if (!add_ks_prime(c, ps[k], K.m[k], err)) return HE_ERR_CUDA;
     // a 64-bit sum of products below (p - 1)^2 is folded to (h mod p)(2^32

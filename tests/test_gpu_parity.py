@@ -24,6 +24,8 @@ RINGS = {
     "n16384_np3": wl.RingSpec(16384, (50, 50), 65537),
     # 16 digits: the key switch's 64-bit sums are folded once (every 14 terms)
     "n4096_l5": wl.RingSpec(4096, (50, 50, 50, 50, 50), 65537),
+    # a limb below 2^31: the key switch runs over the limbs
+    "n4096_q30": wl.RingSpec(4096, (30, 50, 50), 65537),
 }
 _CTX = {}
 
@@ -249,18 +251,19 @@ def test_cpmul_conv_bits(name, families):
     pl.close()
 
 
-# small primes of the relinearisation key switch per ring (0: over the limbs;
-# n16384 would need four, whose parked residues exceed shared memory)
-KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 0, "n8192_b32": 4, "n16384_np3": 3,
-             "n4096_l5": 3}
+# small primes of the relinearisation key switch per ring (0: over the limbs,
+# which a limb below 2^31 forces)
+KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 4, "n8192_b32": 4, "n16384_np3": 3,
+             "n4096_l5": 3, "n4096_q30": 0}
 
 
 @pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2),
-                                        ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1), ("n4096_l5", 2)])
+                                        ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1), ("n4096_l5", 2),
+                                        ("n4096_q30", 1)])
 def test_ccmul_bits(name, group):
     """CCMul with relinearisation equals the oracle bit for bit on every key
-    switch: three and four small primes at N = 1024 to 16384, and over the
-    limbs where the small primes do not fit."""
+    switch: three and four small primes at N = 1024 to 16384 (a sum folded
+    once at 16 digits), and over the limbs where a limb is below 2^31."""
     c = ctx_for(name)
     assert nv.he_ctx_query(c.h).ks_primes == KS_PRIMES[name]
     P = oparams(c)
