@@ -234,6 +234,15 @@ int he_conv_plan(he_ctx *ctx, const he_conv_shape *shape, int encoding, he_plan 
  * polynomial products per image (MG * G * T, Section 3.3 and Fig. 8) for any
  * shape.  Errors as he_conv_plan; INVALID_ARG also for N not a power of two. */
 int he_plan_search(int N, const he_conv_shape *shape, int encoding, he_plan_info *info);
+/* he_ks_primes: the small primes of the relinearisation key switch that a
+ * context with these parameters uses (host only, no device memory; Section 2,
+ * CCMul and Fig. 3(b)): the largest primes p < 2^30 with p = 1 mod 2N, as
+ * many (2 to 4) as make their product exceed 4 ell N (2^base_log2 - 1)
+ * (max q_i - 1), four times the largest |sum_j D_j rlk_{j,i}|.  *np = 0 when
+ * a limb is below 2^31 (the key switch then runs over the limbs).  primes:
+ * caller array of at least 4 entries.  Errors as he_setup for N, L,
+ * prime_bits, q and base_log2. */
+int he_ks_primes(const he_params *params, uint64_t *primes, int32_t *np);
 int he_plan_destroy(he_plan *plan);
 int he_plan_query(const he_plan *plan, he_plan_info *info);
 

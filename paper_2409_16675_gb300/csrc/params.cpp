@@ -251,6 +251,56 @@ static u64 next_prime_below(int bits, int N, const std::vector<u64> &used) {
     return 0;
 }
 
+// Limb primes of a parameter set: the explicit q[] (checked), or for each
+// prime_bits[i] the largest unused prime below 2^bits with q = 1 mod 2N.
+static int limb_primes(const he_params &P, int N, std::vector<u64> &out, std::string &err) {
+    out.clear();
+    const bool explicit_q = P.q[0] != 0;
+    for (int i = 0; i < P.L; i++) {
+        u64 q = explicit_q ? P.q[i] : 0;
+        if (explicit_q) {
+            if (!is_prime(q) || q % (2 * (u64)N) != 1 || q >= ((u64)1 << 61) ||
+                std::find(out.begin(), out.end(), q) != out.end()) {
+                err = "explicit q must be distinct primes < 2^61 with q = 1 mod 2N";
+                return HE_ERR_UNSUPPORTED_PARAMS;
+            }
+        } else {
+            if (P.prime_bits[i] < 20 || P.prime_bits[i] > 61) { err = "prime_bits out of [20, 61]"; return HE_ERR_UNSUPPORTED_PARAMS; }
+            q = next_prime_below(P.prime_bits[i], N, out);
+            if (!q) { err = "no prime of that size"; return HE_ERR_UNSUPPORTED_PARAMS; }
+        }
+        out.push_back(q);
+    }
+    return HE_OK;
+}
+
+// The small primes of the relinearisation key switch for limbs q, plaintext
+// modulus t, degree N and ell digits of base_log2 bits: the largest primes
+// below 2^30 with p = 1 mod 2N (none of them a limb or t), as many as make
+// P = prod p_k exceed 4 ell N (2^base - 1)(max q_i - 1), the bound on four
+// times any |E_i|.  Empty (the key switch runs over the limbs) when that
+// takes more than kKsMaxPrimes or when a limb is below 2^31 (the CRT adds the
+// residues y_k < 2^30 mod q_i).
+static std::vector<u64> ks_select(const std::vector<u64> &q, u64 t, int N, int ell, int base_log2) {
+    u64 qmax = 0;
+    for (u64 qi : q) {
+        if (qi < ((u64)1 << 31)) return {};
+        qmax = std::max(qmax, qi);
+    }
+    const u64 dmax = base_log2 >= 32 ? 0xffffffffull : (((u64)1 << base_log2) - 1);
+    const Big bound = product({4, (u64)ell, (u64)N, dmax, qmax - 1});
+    std::vector<u64> used = q, ps;
+    used.push_back(t);
+    while (ps.size() < 2 || product(ps).bits() - 1 < bound.bits()) {  // P >= 2^(bits(P) - 1)
+        if ((int)ps.size() == kKsMaxPrimes) return {};
+        const u64 p = next_prime_below(30, N, used);
+        if (!p || p < ((u64)1 << 29)) return {};
+        used.push_back(p);
+        ps.push_back(p);
+    }
+    return ps;
+}
+
 int build_tables(he_ctx *c, std::string &err) {
     he_params &P = c->P;
     const int N = P.N;
@@ -270,24 +320,11 @@ int build_tables(he_ctx *c, std::string &err) {
     while ((1 << c->logN) < N) c->logN++;
     c->L = P.L;
     // limb primes
-    c->q.clear();
-    const bool explicit_q = P.q[0] != 0;
-    for (int i = 0; i < P.L; i++) {
-        u64 q = explicit_q ? P.q[i] : 0;
-        if (explicit_q) {
-            if (!is_prime(q) || q % (2 * (u64)N) != 1 || q >= ((u64)1 << 61) ||
-                std::find(c->q.begin(), c->q.end(), q) != c->q.end()) {
-                err = "explicit q must be distinct primes < 2^61 with q = 1 mod 2N";
-                return HE_ERR_UNSUPPORTED_PARAMS;
-            }
-        } else {
-            if (P.prime_bits[i] < 20 || P.prime_bits[i] > 61) { err = "prime_bits out of [20, 61]"; return HE_ERR_UNSUPPORTED_PARAMS; }
-            q = next_prime_below(P.prime_bits[i], N, c->q);
-            if (!q) { err = "no prime of that size"; return HE_ERR_UNSUPPORTED_PARAMS; }
-        }
-        c->q.push_back(q);
-        P.q[i] = q;
+    {
+        const int rc = limb_primes(P, N, c->q, err);
+        if (rc) return rc;
     }
+    for (int i = 0; i < P.L; i++) P.q[i] = c->q[i];
     for (u64 q : c->q)
         if (std::__gcd(q, (u64)P.t) != 1) { err = "t must be coprime to q"; return HE_ERR_UNSUPPORTED_PARAMS; }
     Big Q = product(c->q);
@@ -491,33 +528,13 @@ static bool add_ks_prime(he_ctx *c, u64 p, Mod32Dev &M, std::string &err) {
     return true;
 }
 
-// The small primes of the relinearisation key switch: the largest primes
-// below 2^30 with p = 1 mod 2N, as many as make P = prod p_k exceed
-// 4 ell N (2^base - 1)(max q_i - 1), the bound on four times any |E_i|.  No
-// small primes (np = 0: the key switch runs over the limbs) when that takes
-// more than kKsMaxPrimes, or when a limb is below 2^31 (the CRT adds the
-// residues y_k < 2^30 mod q_i).
+// Tables and CRT constants of the context's key-switch primes (ks_select;
+// np = 0 when it chooses none).
 int build_ks(he_ctx *c, std::string &err) {
     KsDev &K = c->h_ks;
     memset(&K, 0, sizeof K);
-    const int N = c->N;
-    u64 qmax = 0;
-    for (u64 q : c->q) {
-        if (q < ((u64)1 << 31)) return HE_OK;
-        qmax = std::max(qmax, q);
-    }
-    const u64 dmax = c->P.base_log2 >= 32 ? 0xffffffffull : (((u64)1 << c->P.base_log2) - 1);
-    const Big bound = product({4, (u64)c->ell, (u64)N, dmax, qmax - 1});
-    std::vector<u64> used = c->q, ps;
-    used.insert(used.end(), c->aux.begin(), c->aux.end());
-    used.push_back(c->P.t);
-    while (ps.size() < 2 || product(ps).bits() - 1 < bound.bits()) {  // P >= 2^(bits(P) - 1)
-        if ((int)ps.size() == kKsMaxPrimes) return HE_OK;
-        const u64 p = next_prime_below(30, N, used);
-        if (!p || p < ((u64)1 << 29)) return HE_OK;
-        used.push_back(p);
-        ps.push_back(p);
-    }
+    const std::vector<u64> ps = ks_select(c->q, c->P.t, c->N, c->ell, c->P.base_log2);
+    if (ps.empty()) return HE_OK;
     const int np = (int)ps.size();
     for (int k = 0; k < np; k++)
         if (!add_ks_prime(c, ps[k], K.m[k], err)) return HE_ERR_CUDA;
@@ -564,3 +581,22 @@ std::vector<u64> relin_multipliers(const he_ctx *c) {
 }
 
 }  // namespace he
+
+extern "C" int he_ks_primes(const he_params *params, uint64_t *primes, int32_t *np) {
+    if (!params || !primes || !np) return HE_ERR_INVALID_ARG;
+    *np = 0;
+    const int N = params->N;
+    if (N < 1024 || N > 16384 || (N & (N - 1))) return HE_ERR_UNSUPPORTED_PARAMS;
+    if (params->L < 1 || params->L > HE_MAX_LIMBS) return HE_ERR_INVALID_ARG;
+    const int base = params->base_log2 ? params->base_log2 : 16;
+    if (base < 1 || base > 32) return HE_ERR_INVALID_ARG;
+    std::vector<u64> q;
+    std::string err;
+    const int rc = he::limb_primes(*params, N, q, err);
+    if (rc) return rc;
+    const int ell = (he::product(q).bits() + base - 1) / base;
+    const std::vector<u64> ps = he::ks_select(q, params->t, N, ell, base);
+    for (size_t k = 0; k < ps.size(); k++) primes[k] = ps[k];
+    *np = (int32_t)ps.size();
+    return HE_OK;
+}

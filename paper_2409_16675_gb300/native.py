@@ -111,6 +111,7 @@ def _load():
         "he_plan_destroy": [vp],
         "he_plan_query": [vp, ctypes.POINTER(he_plan_info)],
         "he_plan_search": [i32, ctypes.POINTER(he_conv_shape), i32, ctypes.POINTER(he_plan_info)],
+        "he_ks_primes": [ctypes.POINTER(he_params), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(i32)],
         "he_encode_conventional": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_encode_correlated": [vp, vp, i32, vp, i32, i32, vp, vp],
         "he_cpmul_conv": [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp],
@@ -304,6 +305,15 @@ def he_plan_search(N, C, H, W, M, h, pad, encoding) -> "he_plan_info":
     info = he_plan_info()
     _check(lib.he_plan_search(N, ctypes.byref(s), encoding, ctypes.byref(info)))
     return info
+
+
+def he_ks_primes(params) -> list:
+    """Small primes of the relinearisation key switch for these parameters
+    (host only); [] when the key switch runs over the limbs."""
+    arr = (ctypes.c_uint64 * 4)()
+    n = ctypes.c_int32()
+    _check(lib.he_ks_primes(ctypes.byref(params), arr, ctypes.byref(n)))
+    return [int(arr[k]) for k in range(n.value)]
 
 
 def he_plan_destroy(plan):
