@@ -20,8 +20,8 @@
 //              three CTAs fit on an SM; then the mixed-radix (Garner) CRT gives
 //              E_i mod q_i, which is added to d_comp and stored.
 // The bits equal those of the key switch over the limbs (the sum is exact
-// either way); contexts whose sums need more than four primes, or whose
-// kernel would not fit shared memory, or with limbs below 2^31 keep that one.
+// either way); contexts with a limb below 2^31 keep that one (four primes
+// cover the sums of every other supported parameter set).
 //
 // 32-bit arithmetic: Shoup products a w - floor(a w' / 2^32) p lie in [0, 2p)
 // for every 32-bit a (w' = floor(w 2^32 / p)); the butterflies keep Harvey's

@@ -280,6 +280,32 @@ def test_ccmul_bits(name, group):
     k.close()
 
 
+@pytest.mark.parametrize("name", ["n8192", "n8192_b32", "n16384"])
+def test_ccmul_key_switch_near_its_bound(name):
+    """With a relinearisation key whose every coefficient is q_i - 1 (imported
+    on both sides), coefficient N - 1 of sum_j D_j rlk_j is (q_i - 1) times
+    the sum of all digits and coefficient 0 about minus that: with random
+    ciphertexts about half the worst-case magnitude, of both signs.  The key
+    switch over three or four small primes still equals the oracle bit for
+    bit."""
+    c = ctx_for(name)
+    P = oparams(c)
+    ok = he.keygen(P, 21, True)
+    rlk = np.empty_like(ok.rlk)
+    for i, qi in enumerate(c.q):
+        rlk[:, :, i, :] = qi - 1
+    keys = he.Keys(ok.sk, ok.pk, rlk)
+    kh = nv.he_keys_import(c.h, cuda(ok.sk), cuda(ok.pk), cuda(rlk))
+    rng = np.random.default_rng(23)
+    a = he.encrypt(P, ok, rng.integers(0, c.t, (2, c.N), dtype=np.uint64), 24)
+    b = he.encrypt(P, ok, rng.integers(0, c.t, (2, c.N), dtype=np.uint64), 25)
+    pairs = [(0, 1), (1, 0)]
+    out = c.ct(2)
+    nv.he_ccmul_precompute(c.h, kh, cuda(a), 2, cuda(b), 2, pairs, 1, out)
+    assert np.array_equal(to_np(out), he.ccmul(P, keys, a, b, pairs, 1))
+    nv.he_keys_destroy(kh)
+
+
 def test_ccmul_in_chunks_gives_the_same_bits():
     """A CCMul-Precompute whose scratch exceeds the context's budget runs in
     chunks of outputs; a budget of one output per chunk gives the bits of the
