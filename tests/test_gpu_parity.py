@@ -26,6 +26,10 @@ RINGS = {
     "n4096_l5": wl.RingSpec(4096, (50, 50, 50, 50, 50), 65537),
     # a limb below 2^31: the key switch runs over the limbs
     "n4096_q30": wl.RingSpec(4096, (30, 50, 50), 65537),
+    # base-2^8 digits of a 64-bit q: two small primes suffice
+    "n1024_np2": wl.RingSpec(1024, (32, 32), 65537, 8),
+    # four small primes and 15 digits: the sums are folded at the last term
+    "n1024_b32_l9": wl.RingSpec(1024, (50,) * 9, 65537, 32),
 }
 _CTX = {}
 
@@ -254,16 +258,17 @@ def test_cpmul_conv_bits(name, families):
 # small primes of the relinearisation key switch per ring (0: over the limbs,
 # which a limb below 2^31 forces)
 KS_PRIMES = {"n1024": 3, "n4096": 3, "n8192": 3, "n2048_t40": 3, "n16384": 4, "n8192_b32": 4, "n16384_np3": 3,
-             "n4096_l5": 3, "n4096_q30": 0}
+             "n4096_l5": 3, "n4096_q30": 0, "n1024_np2": 2, "n1024_b32_l9": 4}
 
 
 @pytest.mark.parametrize("name,group", [("n1024", 1), ("n1024", 3), ("n4096", 2), ("n8192", 1), ("n2048_t40", 2),
                                         ("n16384", 1), ("n8192_b32", 2), ("n16384_np3", 1), ("n4096_l5", 2),
-                                        ("n4096_q30", 1)])
+                                        ("n4096_q30", 1), ("n1024_np2", 2), ("n1024_b32_l9", 1)])
 def test_ccmul_bits(name, group):
     """CCMul with relinearisation equals the oracle bit for bit on every key
-    switch: three and four small primes at N = 1024 to 16384 (a sum folded
-    once at 16 digits), and over the limbs where a limb is below 2^31."""
+    switch: two, three and four small primes at N = 1024 to 16384 (sums
+    folded at 15 and 16 digits), and over the limbs where a limb is below
+    2^31."""
     c = ctx_for(name)
     assert nv.he_ctx_query(c.h).ks_primes == KS_PRIMES[name]
     P = oparams(c)

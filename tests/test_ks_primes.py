@@ -31,6 +31,8 @@ CASES = [  # (N, prime bits, t, base_log2, expected number of primes)
     (8192, (31, 40), 65537, 16, 0),
     (16384, (61,) * 16, 65537, 32, 4),               # the largest bound
     (1024, (61,) * 16, 65537, 1, 3),                 # 976 one-bit digits
+    (1024, (32, 32), 65537, 8, 2),                   # two primes suffice
+    (1024, (50,) * 9, 65537, 32, 4),
 ]
 
 
