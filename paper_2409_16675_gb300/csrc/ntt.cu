@@ -265,7 +265,13 @@ static int mac_t(he_ctx *c, const MacJob *jobs, int n, cudaStream_t st) {
         blocks += b;
         const double lb = 8.0 * N * j.n_limbs;  // one polynomial over all limbs
         bytes += lb * (j.n_out + j.n_dist_a + j.n_dist_b + (j.add ? j.n_out : 0));
-        mm += (double)b * ((N / 2) * LOGN + 3.0 * N) + (double)j.n_terms * N * j.n_limbs;
+        // modular products the kernel computes per output limb polynomial:
+        // the inverse transform's butterflies, one Montgomery reduction ending
+        // each coefficient's sum, the untwist, one product per term, and in
+        // the epilogue Delta*m (outputs with a message) and g*s^2 (keygen)
+        const double with_msg = (j.msg && j.msg_div > 0) ? (double)((j.n_out + j.msg_div - 1) / j.msg_div) : 0.0;
+        mm += (double)b * ((N / 2) * LOGN + 2.0 * N) + (double)j.n_terms * N * j.n_limbs +
+              with_msg * j.n_limbs * N + (j.s2 ? (double)b * N : 0.0);
     }
     if (blocks == 0) return HE_OK;
     if (blocks > 0x7fffffffLL) return fail(c, HE_ERR_INVALID_ARG, "multiply-accumulate launch too large");
